@@ -1,0 +1,244 @@
+/*
+ * gb300bfs.h -- C ABI of the GB300 Graph500 library (kernel 1 + kernel 2).
+ *
+ * The library implements the data-parallel part of the Graph500 pipeline that
+ * arXiv 2012.13548 ("Graph500 from OCaml-Multicore Perspective") builds on a
+ * CPU: Sec. 2.1 (Kronecker edge list), Sec. 2.2 (kernel 1: graph construction
+ * as CSR) and Sec. 2.3 (kernel 2: level-synchronous BFS producing a parent and
+ * a level array), plus a batched multi-source BFS and a serving loop.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a gb_status; no C++ exception crosses the ABI.
+ *     On failure gb_last_error() returns a message (thread-local, valid until
+ *     the next call on the same thread).
+ *   - "device" pointers are CUDA global-memory pointers of the current device;
+ *     "host" pointers are ordinary CPU memory.  The caller owns every array it
+ *     passes.  The library owns gb_graph and gb_server objects.
+ *   - Work is stream-ordered on the gb_stream given (a cudaStream_t; NULL is
+ *     the legacy default stream).  Outputs are valid once that stream has
+ *     synchronised.  Calls that must return a size computed on the device
+ *     (graph_build_csr) synchronise the stream themselves and say so.
+ *   - Errors detected inside a kernel (an edge endpoint out of range, a
+ *     bounded device-side wait that ran out) are recorded in a per-device
+ *     status word; gb_device_status() synchronises a stream and returns and
+ *     clears it.  No kernel traps or asserts.
+ *   - Vertex ids are 0-based int64 at the ABI; inside a graph they are stored
+ *     as int32 columns, so a graph has at most 2^30 vertices (SCALE <= 30).
+ */
+#ifndef GB300BFS_H
+#define GB300BFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+/* A CUDA stream (cudaStream_t); NULL means the legacy default stream. */
+typedef struct CUstream_st *gb_stream;
+
+/* Opaque, library-owned, device-resident CSR graph (Sec. 2.2). */
+typedef struct gb_graph gb_graph;
+
+/* Opaque serving loop (resident graphs + admitted queries). */
+typedef struct gb_server gb_server;
+
+typedef enum gb_status {
+    GB_OK = 0,
+    GB_ERR_INVALID = -1,       /* a bad argument (NULL pointer, bad size, bad k) */
+    GB_ERR_NOMEM = -2,         /* a device or host allocation failed */
+    GB_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    GB_ERR_TIMEOUT = -4,       /* a bounded device-side wait ran out */
+    GB_ERR_RANGE = -5,         /* a vertex id outside [0, n) */
+    GB_ERR_BUSY = -6,          /* no free slot or memory right now; retry later */
+    GB_ERR_UNIMPLEMENTED = -7
+} gb_status;
+
+/* Message for the last failure on this thread ("" if none). */
+const char *gb_last_error(void);
+
+/* ABI version of this header (incremented on incompatible change). */
+int gb_abi_version(void);
+
+/* Synchronise `s`, then return and clear the device status word: GB_OK, or
+ * the first GB_ERR_RANGE / GB_ERR_TIMEOUT a kernel recorded since the last
+ * call. */
+gb_status gb_device_status(gb_stream s);
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.1: Kronecker edge list.                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Generate m = edgefactor * 2^scale edge tuples into `edges` (device,
+ * int64 [2][m] structure-of-arrays: row 0 = start vertex, row 1 = end
+ * vertex; caller-allocated, 16 * m bytes).  Sec. 2.1: #V = 2^scale,
+ * #E = #V * edgefactor; duplicates and self-loops are kept; the vertex
+ * numbers are permuted and then the tuples are shuffled.
+ * Tuple e draws, for each bit level k < scale, two SplitMix64 values
+ * r1, r2 at counters 2(e*scale+k) and 2(e*scale+k)+1 of seed_gen and sets the
+ * row/column bits from the quadrant probabilities a, b, c, d = 1-a-b-c
+ * (thresholds floor(p * 2^53) against r >> 11).  The permutation ranks
+ * vertices by (SplitMix64(seed_perm, v), v); the shuffle puts at position j
+ * the tuple of rank j under (SplitMix64(seed_shuf, e), e).
+ * Requires 1 <= scale <= 30, edgefactor >= 1, m <= 2^32.  Allocates
+ * temporary device memory on `s` (about 24 * m bytes). */
+gb_status kron_generate(int scale, int edgefactor, double a, double b, double c,
+                        uint64_t seed_gen, uint64_t seed_perm, uint64_t seed_shuf,
+                        int64_t *edges, gb_stream s);
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.2: kernel 1, graph construction (CSR).                             */
+/* ------------------------------------------------------------------------ */
+
+/* Build the undirected CSR of `edges` (device int64 [2][m] as produced by
+ * kron_generate; read only, may be freed after the call returns) over
+ * n = 2^scale vertices.  Row u holds, ascending, every v != u such that
+ * (u,v) or (v,u) is a tuple: the graph is symmetrised, self-loops and
+ * duplicate edges are dropped (Sec. 2.1 "may be ignored in the subsequent
+ * kernels").  Offsets are int64 [n+1]: an empty row repeats the previous
+ * offset and off[n] = nnz (Sec. 2.2).  Columns are int32 [nnz].
+ * Synchronises `s` (the column count is needed on the host).  Returns
+ * GB_ERR_RANGE if an endpoint is outside [0, 2^scale).  *out receives a
+ * library-owned graph; free it with graph_free. */
+gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph **out,
+                          gb_stream s);
+
+/* Wrap a caller-built CSR (device arrays off int64 [n+1], col int32 [nnz]):
+ * the arrays are copied into library-owned memory.  The rows must be sorted
+ * ascending, free of self-loops and duplicates, and symmetric; only
+ * 0 <= col < n and monotone offsets are checked (on the host after a copy).
+ * Synchronises `s`. */
+gb_status graph_from_csr(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
+                         gb_graph **out, gb_stream s);
+
+gb_status graph_free(gb_graph *g);
+
+/* Vertex and column counts of g (host outputs). */
+gb_status graph_info(const gb_graph *g, int64_t *n, int64_t *nnz);
+
+/* Borrowed device pointers to g's offsets and columns (valid until
+ * graph_free). */
+gb_status graph_csr_view(const gb_graph *g, const int64_t **off, const int32_t **col);
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.3: kernel 2, breadth-first search.                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Options for the BFS entry points (process-wide; applied to later calls).
+ *   canonical_parents  0: parent(v) is whichever level-(l-1) neighbour
+ *                      claimed v first (any valid Graph500 tree);
+ *                      1: parent(v) is the smallest-id neighbour one level
+ *                      up (a unique tree, Sec. 2.3.1: the tree follows from
+ *                      the level array).
+ *   alpha, beta        direction switch: top-down -> bottom-up when the
+ *                      frontier's edges exceed (unexplored edges)/alpha;
+ *                      bottom-up -> top-down when the frontier shrinks below
+ *                      n/beta vertices (Beamer et al., SC 2012).
+ *   big_degree         frontier vertices of larger degree are split over the
+ *                      whole grid in top-down steps.
+ *   ms_alpha, ms_beta  the same switch for the multi-source BFS.
+ *   timeout_ms         limit of every device-side wait (grid barriers, the
+ *                      radix-sort look-back); on expiry the kernel records
+ *                      GB_ERR_TIMEOUT and returns. */
+typedef struct gb_bfs_options {
+    int canonical_parents;
+    double alpha;
+    double beta;
+    int big_degree;
+    double ms_alpha;
+    double ms_beta;
+    double timeout_ms;
+} gb_bfs_options;
+
+gb_status bfs_get_options(gb_bfs_options *out);
+gb_status bfs_set_options(const gb_bfs_options *opt);
+
+/* Single-source BFS from `root` (Sec. 2.3.2, Algorithm "Parallel BFS", run
+ * direction-optimised).  parent and level are caller-allocated device int32
+ * [n].  On return (after `s` syncs) level[v] is the hop distance from root or
+ * -1, parent[root] = root, parent[v] is a neighbour of v with level one less,
+ * and parent[v] = -1 for every unreached v.  GB_ERR_RANGE if root is outside
+ * [0, n).  One persistent cooperative kernel runs all levels; temporary
+ * device memory (about 4.2 * n bytes) is taken from the stream-ordered
+ * pool. */
+gb_status bfs(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level, gb_stream s);
+
+/* Multi-source BFS: k (1..64) roots (host array) in one persistent launch,
+ * one bit per root in per-vertex masks.  parents and levels are device int32
+ * [k][n] (row i belongs to roots[i]); row i equals what bfs() returns for
+ * roots[i] (canonical parents in canonical mode, any valid tree otherwise).
+ * Roots may repeat. */
+gb_status bfs_batch(const gb_graph *g, const int64_t *roots, int k, int32_t *parents,
+                    int32_t *levels, gb_stream s);
+
+/* BFS over a batch of ng graphs of different sizes in one launch: r (1..8)
+ * roots per graph, roots a host int64 [ng][r] array.  parents[i] and
+ * levels[i] (host arrays of ng device pointers) point to int32 [r][n_i]
+ * outputs for graph i.  Each result equals the standalone bfs() result. */
+gb_status bfs_multi_graph(const gb_graph *const *gs, int ng, const int64_t *roots, int r,
+                          int32_t *const *parents, int32_t *const *levels, gb_stream s);
+
+/* Counters of the last bfs/bfs_batch/bfs_multi_graph call on this thread;
+ * synchronises the stream of that call.
+ *   nlevels          number of BFS levels (max level + 1)
+ *   edges_examined   adjacency entries read (top-down: frontier degrees;
+ *                    bottom-up: neighbours tested before the first hit)
+ *   vertices_touched frontier vertices expanded plus unvisited vertices
+ *                    tested
+ *   reached          vertices with level >= 0 (summed over roots)
+ *   td_levels, bu_levels  levels run top-down / bottom-up */
+typedef struct gb_bfs_stats {
+    int64_t nlevels;
+    int64_t edges_examined;
+    int64_t vertices_touched;
+    int64_t reached;
+    int64_t td_levels;
+    int64_t bu_levels;
+} gb_bfs_stats;
+
+gb_status bfs_last_stats(gb_bfs_stats *out);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: resident graphs, BFS queries admitted as they arrive.            */
+/* ------------------------------------------------------------------------ */
+
+/* Create a server over ng resident graphs (borrowed; they must outlive the
+ * server).  Up to 64 queries per graph run together as bits of one
+ * multi-source BFS; a query is admitted at the next level boundary once a
+ * bit is free and its output buffers (8 * n_graph bytes) fit within
+ * mem_budget bytes of device memory.  The server runs its own host thread
+ * and one CUDA stream per graph. */
+gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb_server **out);
+
+/* Queue a query (graph index, root).  *ticket identifies it.  Never blocks;
+ * GB_ERR_RANGE for a bad graph or root. */
+gb_status server_submit(gb_server *srv, int graph_id, int64_t root, int64_t *ticket);
+
+/* Poll a query.  Returns GB_OK with *parent/*level set to borrowed device
+ * pointers (int32 [n_graph]) once it is done, GB_ERR_BUSY while it is
+ * queued or running.  The buffers stay valid until server_release. */
+gb_status server_poll(gb_server *srv, int64_t ticket, const int32_t **parent,
+                      const int32_t **level);
+
+/* Return a finished query's buffers to the server. */
+gb_status server_release(gb_server *srv, int64_t ticket);
+
+/* Replay an open-loop arrival trace: query i arrives t_arrival_s[i] seconds
+ * after the call starts (ascending), on graph graph_id[i] from root[i].
+ * Blocks until all are done.  latency_ms[i] receives arrival-to-done time
+ * (host array, caller-allocated).  Buffers are released as queries
+ * finish unless keep_results is nonzero, in which case the caller polls and
+ * releases them. */
+gb_status server_run_trace(gb_server *srv, int64_t nq, const double *t_arrival_s,
+                           const int32_t *graph_id, const int64_t *root, int keep_results,
+                           double *latency_ms);
+
+gb_status server_destroy(gb_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300BFS_H */
