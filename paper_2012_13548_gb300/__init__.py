@@ -1,0 +1,9 @@
+"""GB300-native Graph500 kernels 1 and 2 (arXiv 2012.13548, Sec. 2).
+
+The compute path is the CUDA library built from ``csrc/`` (sm_103a); this
+package only loads it (``binding``) and holds the seeded input recipes
+(``workloads``).
+"""
+from .binding import (GbError, Graph, bfs, bfs_batch, bfs_get_options, bfs_last_stats,  # noqa: F401
+                      bfs_multi_graph, bfs_set_options, gb_device_status, graph_build_csr,
+                      graph_from_csr, kron_generate, lib)

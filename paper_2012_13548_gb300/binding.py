@@ -1,0 +1,273 @@
+"""Python binding of the C ABI in ``include/gb300bfs.h``.
+
+Argument marshalling only: every function checks its tensors, passes their
+device pointers and the current CUDA stream to the library and raises
+``GbError`` on a non-zero status.  There is no fallback: if the CUDA library
+has not been built, importing a function raises.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgb300bfs.so")
+
+GB_OK, GB_ERR_INVALID, GB_ERR_NOMEM, GB_ERR_CUDA = 0, -1, -2, -3
+GB_ERR_TIMEOUT, GB_ERR_RANGE, GB_ERR_BUSY, GB_ERR_UNIMPLEMENTED = -4, -5, -6, -7
+_NAMES = {0: "GB_OK", -1: "GB_ERR_INVALID", -2: "GB_ERR_NOMEM", -3: "GB_ERR_CUDA",
+          -4: "GB_ERR_TIMEOUT", -5: "GB_ERR_RANGE", -6: "GB_ERR_BUSY", -7: "GB_ERR_UNIMPLEMENTED"}
+
+
+class GbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class gb_bfs_options(ctypes.Structure):
+    _fields_ = [("canonical_parents", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("big_degree", ctypes.c_int),
+                ("ms_alpha", ctypes.c_double), ("ms_beta", ctypes.c_double),
+                ("timeout_ms", ctypes.c_double)]
+
+
+class gb_bfs_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in
+                ("nlevels", "edges_examined", "vertices_touched", "reached", "td_levels",
+                 "bu_levels")]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "CUDA library %s is missing: run __graft_entry__.build() (nvcc, sm_103a) first"
+                % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        sigs = {
+            "gb_last_error": (ctypes.c_char_p, []),
+            "gb_abi_version": (ctypes.c_int, []),
+            "gb_device_status": (ctypes.c_int, [_vp]),
+            "kron_generate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                             ctypes.c_uint64, ctypes.c_uint64, _vp, _vp]),
+            "graph_build_csr": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.POINTER(_vp), _vp]),
+            "graph_from_csr": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.POINTER(_vp), _vp]),
+            "graph_free": (ctypes.c_int, [_vp]),
+            "graph_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+            "graph_csr_view": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+            "bfs_get_options": (ctypes.c_int, [ctypes.POINTER(gb_bfs_options)]),
+            "bfs_set_options": (ctypes.c_int, [ctypes.POINTER(gb_bfs_options)]),
+            "bfs": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp]),
+            "bfs_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.c_int, _vp, _vp, _vp]),
+            "bfs_multi_graph": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int,
+                                               ctypes.POINTER(_i64), ctypes.c_int,
+                                               ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
+            "bfs_last_stats": (ctypes.c_int, [ctypes.POINTER(gb_bfs_stats)]),
+            "server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t,
+                                             ctypes.POINTER(_vp)]),
+            "server_submit": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.POINTER(_i64)]),
+            "server_poll": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+            "server_release": (ctypes.c_int, [_vp, _i64]),
+            "server_run_trace": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp, ctypes.c_int, _vp]),
+            "server_destroy": (ctypes.c_int, [_vp]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C-ABI functions this binding wraps."""
+    return ["gb_last_error", "gb_abi_version", "gb_device_status", "kron_generate",
+            "graph_build_csr", "graph_from_csr", "graph_free", "graph_info", "graph_csr_view",
+            "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
+            "bfs_last_stats", "server_create", "server_submit", "server_poll", "server_release",
+            "server_run_trace", "server_destroy"]
+
+
+def _check(rc):
+    if rc != GB_OK:
+        raise GbError(rc, lib().gb_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _DevArray:
+    """A borrowed device array exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+        self._owner = owner
+
+
+class Graph:
+    """A library-owned device CSR graph (Sec. 2.2)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+        n, nnz = _i64(), _i64()
+        _check(lib().graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz)))
+        self.n, self.nnz = n.value, nnz.value
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("graph has been freed")
+        return self._h
+
+    def csr(self):
+        """Borrowed (off int64 [n+1], col int32 [nnz]) CUDA tensors; valid until free()."""
+        off, col = _vp(), _vp()
+        _check(lib().graph_csr_view(self.handle, ctypes.byref(off), ctypes.byref(col)))
+        dev = torch.cuda.current_device()
+        o = torch.as_tensor(_DevArray(off.value, (self.n + 1,), "<i8", self), device="cuda:%d" % dev)
+        c = torch.as_tensor(_DevArray(col.value, (self.nnz,), "<i4", self), device="cuda:%d" % dev)
+        return o, c
+
+    def free(self):
+        if self._h:
+            _check(lib().graph_free(self._h))
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.graph_free(self._h)
+        except Exception:
+            pass
+
+
+def gb_device_status(stream=None):
+    """Synchronise the stream and raise if a kernel recorded an error."""
+    _check(lib().gb_device_status(_stream(stream)))
+
+
+def kron_generate(scale, edgefactor, a, b, c, seed_gen, seed_perm, seed_shuf, edges=None,
+                  stream=None):
+    """Kronecker edge list (Sec. 2.1) as an int64 [2, m] CUDA tensor."""
+    m = (1 << scale) * edgefactor
+    if edges is None:
+        edges = torch.empty((2, m), dtype=torch.int64, device="cuda")
+    if tuple(edges.shape) != (2, m):
+        raise ValueError("edges must have shape (2, %d)" % m)
+    _check(lib().kron_generate(scale, edgefactor, a, b, c, seed_gen & (2**64 - 1),
+                               seed_perm & (2**64 - 1), seed_shuf & (2**64 - 1),
+                               _dev(edges, torch.int64, "edges"), _stream(stream)))
+    return edges
+
+
+def graph_build_csr(edges, scale, stream=None):
+    """Kernel 1 (Sec. 2.2): the undirected CSR of an int64 [2, m] edge list."""
+    if edges.dim() != 2 or edges.shape[0] != 2:
+        raise ValueError("edges must have shape (2, m)")
+    h = _vp()
+    _check(lib().graph_build_csr(_dev(edges, torch.int64, "edges"), edges.shape[1], scale,
+                                 ctypes.byref(h), _stream(stream)))
+    return Graph(h.value)
+
+
+def graph_from_csr(off, col, stream=None):
+    """Wrap a caller CSR (copied into library memory)."""
+    h = _vp()
+    _check(lib().graph_from_csr(_dev(off, torch.int64, "off"),
+                                _dev(col, torch.int32, "col") if col.numel() else ctypes.c_void_p(None),
+                                off.numel() - 1, col.numel(), ctypes.byref(h), _stream(stream)))
+    return Graph(h.value)
+
+
+def bfs_get_options():
+    o = gb_bfs_options()
+    _check(lib().bfs_get_options(ctypes.byref(o)))
+    return {f: getattr(o, f) for f, _ in gb_bfs_options._fields_}
+
+
+def bfs_set_options(**kw):
+    """Update any of canonical_parents, alpha, beta, big_degree, ms_alpha, ms_beta, timeout_ms."""
+    cur = bfs_get_options()
+    unknown = set(kw) - set(cur)
+    if unknown:
+        raise KeyError("unknown options %s" % sorted(unknown))
+    cur.update(kw)
+    o = gb_bfs_options(**cur)
+    _check(lib().bfs_set_options(ctypes.byref(o)))
+
+
+def bfs(graph, root, parent=None, level=None, stream=None):
+    """Kernel 2 (Sec. 2.3): (parent, level) int32 [n] CUDA tensors from `root`."""
+    if parent is None:
+        parent = torch.empty(graph.n, dtype=torch.int32, device="cuda")
+    if level is None:
+        level = torch.empty(graph.n, dtype=torch.int32, device="cuda")
+    if parent.numel() != graph.n or level.numel() != graph.n:
+        raise ValueError("outputs must have n = %d entries" % graph.n)
+    _check(lib().bfs(graph.handle, int(root), _dev(parent, torch.int32, "parent"),
+                     _dev(level, torch.int32, "level"), _stream(stream)))
+    return parent, level
+
+
+def bfs_batch(graph, roots, parents=None, levels=None, stream=None):
+    """Multi-source BFS: (parents, levels) int32 [k, n], row i for roots[i]."""
+    roots = [int(r) for r in roots]
+    k = len(roots)
+    if parents is None:
+        parents = torch.empty((k, graph.n), dtype=torch.int32, device="cuda")
+    if levels is None:
+        levels = torch.empty((k, graph.n), dtype=torch.int32, device="cuda")
+    if parents.numel() != k * graph.n or levels.numel() != k * graph.n:
+        raise ValueError("outputs must have k*n entries")
+    arr = (_i64 * max(k, 1))(*roots)
+    _check(lib().bfs_batch(graph.handle, arr, k, _dev(parents, torch.int32, "parents"),
+                           _dev(levels, torch.int32, "levels"), _stream(stream)))
+    return parents, levels
+
+
+def bfs_multi_graph(graphs, roots, parents=None, levels=None, stream=None):
+    """BFS of r roots on each of ng graphs in one launch.  roots: [ng][r] ints.
+    Returns lists of (parents [r, n_i], levels [r, n_i])."""
+    ng = len(graphs)
+    r = len(roots[0]) if ng else 0
+    if any(len(x) != r for x in roots):
+        raise ValueError("every graph needs the same number of roots")
+    if parents is None:
+        parents = [torch.empty((r, g.n), dtype=torch.int32, device="cuda") for g in graphs]
+    if levels is None:
+        levels = [torch.empty((r, g.n), dtype=torch.int32, device="cuda") for g in graphs]
+    gh = (_vp * ng)(*[g.handle.value for g in graphs])
+    rr = (_i64 * (ng * r))(*[int(x) for row in roots for x in row])
+    pp = (_vp * ng)(*[_dev(p, torch.int32, "parents").value for p in parents])
+    ll = (_vp * ng)(*[_dev(x, torch.int32, "levels").value for x in levels])
+    _check(lib().bfs_multi_graph(gh, ng, rr, r, pp, ll, _stream(stream)))
+    return parents, levels
+
+
+def bfs_last_stats():
+    """Counters of this thread's last BFS call (synchronises its stream)."""
+    s = gb_bfs_stats()
+    _check(lib().bfs_last_stats(ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in gb_bfs_stats._fields_}

@@ -1,0 +1,419 @@
+// C ABI of the library (include/gb300bfs.h): argument checks, error
+// reporting, the per-device context and the graph objects.  Every compute
+// step runs in the CUDA kernels of gen.cu, sort.cu, csr.cu, bfs.cu and
+// msbfs.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gb300bfs.h"
+#include "internal.h"
+
+namespace gb {
+
+namespace {
+thread_local std::string t_err;
+std::mutex g_ctx_mu;
+std::vector<Context *> g_ctx;  // indexed by device
+
+gb_bfs_options g_opt = {
+    0,       // canonical_parents
+    14.0,    // alpha
+    24.0,    // beta
+    256,     // big_degree
+    16.0,    // ms_alpha
+    32.0,    // ms_beta
+    5000.0,  // timeout_ms
+};
+
+// last-call statistics of this thread
+struct StatsSlot {
+    int device = -1;
+    BfsDevStats *dev = nullptr;
+    cudaStream_t stream = nullptr;
+    bool valid = false;
+};
+thread_local StatsSlot t_stats;
+
+gb_status check_graph(const gb_graph *g)
+{
+    if (!g || !g->off) {
+        set_error("NULL or freed graph");
+        return GB_ERR_INVALID;
+    }
+    return GB_OK;
+}
+
+}  // namespace
+
+void set_error(const std::string &msg) { t_err = msg; }
+const std::string &last_error() { return t_err; }
+
+gb_status cuda_fail(cudaError_t e, const char *what)
+{
+    t_err = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return GB_ERR_NOMEM;
+    return GB_ERR_CUDA;
+}
+
+gb_bfs_options &options() { return g_opt; }
+
+uint64_t timeout_ns()
+{
+    double ms = g_opt.timeout_ms > 0 ? g_opt.timeout_ms : 5000.0;
+    return (uint64_t)(ms * 1e6);
+}
+
+Context *context()
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "cudaGetDevice");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    if ((int)g_ctx.size() <= dev) g_ctx.resize(dev + 1, nullptr);
+    if (g_ctx[dev]) return g_ctx[dev];
+    Context *c = new (std::nothrow) Context();
+    if (!c) {
+        t_err = "out of host memory";
+        return nullptr;
+    }
+    c->device = dev;
+    if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev)) !=
+            cudaSuccess ||
+        (e = cudaMalloc((void **)&c->status, sizeof(DevStatus))) != cudaSuccess ||
+        (e = cudaMemset(c->status, 0, sizeof(DevStatus))) != cudaSuccess) {
+        cuda_fail(e, "library context");
+        delete c;
+        return nullptr;
+    }
+    // keep freed stream-ordered memory in the pool between calls
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    c->bfs_blocks = bfs_pick_blocks(c->num_sms);
+    c->ms_blocks = msbfs_pick_blocks(c->num_sms);
+    g_ctx[dev] = c;
+    return c;
+}
+
+BfsDevStats *stats_buffer()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (t_stats.dev && t_stats.device == dev) return t_stats.dev;
+    if (t_stats.dev) {
+        int old = 0;
+        cudaGetDevice(&old);
+        cudaSetDevice(t_stats.device);
+        cudaFree(t_stats.dev);
+        cudaSetDevice(old);
+        t_stats.dev = nullptr;
+    }
+    if (cudaMalloc((void **)&t_stats.dev, sizeof(BfsDevStats)) != cudaSuccess) return nullptr;
+    t_stats.device = dev;
+    t_stats.valid = false;
+    return t_stats.dev;
+}
+
+void note_stats_call(BfsDevStats *dev_stats, cudaStream_t s)
+{
+    (void)dev_stats;
+    t_stats.stream = s;
+    t_stats.valid = true;
+}
+
+}  // namespace gb
+
+using namespace gb;
+
+namespace {
+
+cudaStream_t as_stream(gb_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <typename F>
+gb_status guarded(F &&f)
+{
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        set_error("out of host memory");
+        return GB_ERR_NOMEM;
+    } catch (...) {
+        set_error("internal error");
+        return GB_ERR_INVALID;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gb_last_error(void) { return last_error().c_str(); }
+
+int gb_abi_version(void) { return 1; }
+
+gb_status gb_device_status(gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        Context *ctx = context();
+        if (!ctx) return GB_ERR_CUDA;
+        GB_CUDA(cudaStreamSynchronize(as_stream(s)));
+        DevStatus h;
+        GB_CUDA(cudaMemcpy(&h, ctx->status, sizeof(h), cudaMemcpyDeviceToHost));
+        if (h.code != 0) {
+            GB_CUDA(cudaMemset(ctx->status, 0, sizeof(DevStatus)));
+            set_error("device status " + std::to_string(h.code) + " at site " +
+                      std::to_string(h.where) + " (detail " + std::to_string(h.detail) + ")");
+            return (gb_status)h.code;
+        }
+        return GB_OK;
+    });
+}
+
+gb_status kron_generate(int scale, int edgefactor, double a, double b, double c, uint64_t seed_gen,
+                        uint64_t seed_perm, uint64_t seed_shuf, int64_t *edges, gb_stream s)
+{
+    return guarded([&]() {
+        if (!(a >= 0 && b >= 0 && c >= 0 && a + b + c <= 1.0 + 1e-12)) {
+            set_error("kron_generate: initiator probabilities must be >= 0 with a+b+c <= 1");
+            return GB_ERR_INVALID;
+        }
+        return kron_generate_impl(scale, edgefactor, a, b, c, seed_gen, seed_perm, seed_shuf,
+                                  edges, as_stream(s));
+    });
+}
+
+gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph **out, gb_stream s)
+{
+    return guarded([&]() {
+        if (!out || scale < 1 || scale > 30 || m < 0 || (m > 0 && !edges)) {
+            set_error("graph_build_csr: need out != NULL, 1 <= scale <= 30, m >= 0");
+            return GB_ERR_INVALID;
+        }
+        *out = nullptr;
+        gb_graph *g = new gb_graph();
+        gb_status rc = build_csr(edges, m, scale, g, as_stream(s));
+        if (rc != GB_OK) {
+            if (g->off) cudaFree(g->off);
+            if (g->col) cudaFree(g->col);
+            delete g;
+            return rc;
+        }
+        *out = g;
+        return GB_OK;
+    });
+}
+
+gb_status graph_from_csr(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
+                         gb_graph **out, gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        if (!out || !off || n < 1 || n > (int64_t(1) << 30) || nnz < 0 || (nnz > 0 && !col)) {
+            set_error("graph_from_csr: need out, off != NULL, 1 <= n <= 2^30, nnz >= 0");
+            return GB_ERR_INVALID;
+        }
+        *out = nullptr;
+        Context *ctx = context();
+        if (!ctx) return GB_ERR_CUDA;
+        cudaStream_t st = as_stream(s);
+        std::vector<int64_t> hoff(n + 1);
+        std::vector<int32_t> hcol(nnz);
+        GB_CUDA(cudaMemcpyAsync(hoff.data(), off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        if (nnz) GB_CUDA(cudaMemcpyAsync(hcol.data(), col, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        if (hoff[0] != 0 || hoff[n] != nnz) {
+            set_error("graph_from_csr: off[0] must be 0 and off[n] must equal nnz");
+            return GB_ERR_INVALID;
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (hoff[i + 1] < hoff[i]) {
+                set_error("graph_from_csr: offsets must be non-decreasing");
+                return GB_ERR_INVALID;
+            }
+        for (int64_t j = 0; j < nnz; ++j)
+            if (hcol[j] < 0 || hcol[j] >= n) {
+                set_error("graph_from_csr: a column is outside [0, n)");
+                return GB_ERR_RANGE;
+            }
+        gb_graph *g = new gb_graph();
+        g->n = n;
+        g->nnz = nnz;
+        g->scale = -1;
+        g->device = ctx->device;
+        cudaError_t e;
+        if ((e = cudaMalloc(&g->off, (n + 1) * sizeof(int64_t))) != cudaSuccess ||
+            (e = cudaMalloc(&g->col, std::max<int64_t>(nnz, 4) * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMemcpyAsync(g->off, off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (nnz && (e = cudaMemcpyAsync(g->col, col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st)) != cudaSuccess) ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            cudaFree(g->off);
+            cudaFree(g->col);
+            delete g;
+            return cuda_fail(e, "graph_from_csr");
+        }
+        *out = g;
+        return GB_OK;
+    });
+}
+
+gb_status graph_free(gb_graph *g)
+{
+    return guarded([&]() -> gb_status {
+        if (!g) return GB_OK;
+        cudaDeviceSynchronize();
+        if (g->off) cudaFree(g->off);
+        if (g->col) cudaFree(g->col);
+        g->off = nullptr;
+        g->col = nullptr;
+        delete g;
+        return GB_OK;
+    });
+}
+
+gb_status graph_info(const gb_graph *g, int64_t *n, int64_t *nnz)
+{
+    gb_status rc = check_graph(g);
+    if (rc != GB_OK) return rc;
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    return GB_OK;
+}
+
+gb_status graph_csr_view(const gb_graph *g, const int64_t **off, const int32_t **col)
+{
+    gb_status rc = check_graph(g);
+    if (rc != GB_OK) return rc;
+    if (off) *off = g->off;
+    if (col) *col = g->col;
+    return GB_OK;
+}
+
+gb_status bfs_get_options(gb_bfs_options *out)
+{
+    if (!out) {
+        set_error("bfs_get_options: NULL");
+        return GB_ERR_INVALID;
+    }
+    *out = options();
+    return GB_OK;
+}
+
+gb_status bfs_set_options(const gb_bfs_options *opt)
+{
+    if (!opt || !(opt->alpha > 0) || !(opt->beta > 0) || opt->big_degree < 1 ||
+        !(opt->ms_alpha > 0) || !(opt->ms_beta > 0) || !(opt->timeout_ms > 0)) {
+        set_error("bfs_set_options: alpha, beta, ms_alpha, ms_beta, timeout_ms must be > 0 and big_degree >= 1");
+        return GB_ERR_INVALID;
+    }
+    options() = *opt;
+    return GB_OK;
+}
+
+gb_status bfs(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level, gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        gb_status rc = check_graph(g);
+        if (rc != GB_OK) return rc;
+        if (!parent || !level) {
+            set_error("bfs: NULL output");
+            return GB_ERR_INVALID;
+        }
+        if (root < 0 || root >= g->n) {
+            set_error("bfs: root outside [0, n)");
+            return GB_ERR_RANGE;
+        }
+        BfsDevStats *st = stats_buffer();
+        if (!st) return cuda_fail(cudaErrorMemoryAllocation, "bfs stats buffer");
+        rc = bfs_impl(g, root, parent, level, st, as_stream(s));
+        if (rc == GB_OK) note_stats_call(st, as_stream(s));
+        return rc;
+    });
+}
+
+gb_status bfs_batch(const gb_graph *g, const int64_t *roots, int k, int32_t *parents,
+                    int32_t *levels, gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        gb_status rc = check_graph(g);
+        if (rc != GB_OK) return rc;
+        if (!roots || !parents || !levels || k < 1 || k > 64) {
+            set_error("bfs_batch: need roots/outputs != NULL and 1 <= k <= 64");
+            return GB_ERR_INVALID;
+        }
+        for (int i = 0; i < k; ++i)
+            if (roots[i] < 0 || roots[i] >= g->n) {
+                set_error("bfs_batch: a root is outside [0, n)");
+                return GB_ERR_RANGE;
+            }
+        BfsDevStats *st = stats_buffer();
+        if (!st) return cuda_fail(cudaErrorMemoryAllocation, "bfs stats buffer");
+        rc = msbfs_impl(g, roots, k, parents, levels, st, as_stream(s));
+        if (rc == GB_OK) note_stats_call(st, as_stream(s));
+        return rc;
+    });
+}
+
+gb_status bfs_multi_graph(const gb_graph *const *gs, int ng, const int64_t *roots, int r,
+                          int32_t *const *parents, int32_t *const *levels, gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        if (!gs || !roots || !parents || !levels || ng < 1 || ng > 64 || r < 1 || r > 8) {
+            set_error("bfs_multi_graph: need arrays != NULL, 1 <= ng <= 64, 1 <= r <= 8");
+            return GB_ERR_INVALID;
+        }
+        for (int i = 0; i < ng; ++i) {
+            gb_status rc = check_graph(gs[i]);
+            if (rc != GB_OK) return rc;
+            if (!parents[i] || !levels[i]) {
+                set_error("bfs_multi_graph: NULL output pointer");
+                return GB_ERR_INVALID;
+            }
+            for (int j = 0; j < r; ++j)
+                if (roots[(size_t)i * r + j] < 0 || roots[(size_t)i * r + j] >= gs[i]->n) {
+                    set_error("bfs_multi_graph: a root is outside [0, n_i)");
+                    return GB_ERR_RANGE;
+                }
+        }
+        BfsDevStats *st = stats_buffer();
+        if (!st) return cuda_fail(cudaErrorMemoryAllocation, "bfs stats buffer");
+        gb_status rc = multigraph_impl(gs, ng, roots, r, parents, levels, st, as_stream(s));
+        if (rc == GB_OK) note_stats_call(st, as_stream(s));
+        return rc;
+    });
+}
+
+gb_status bfs_last_stats(gb_bfs_stats *out)
+{
+    return guarded([&]() -> gb_status {
+        if (!out) {
+            set_error("bfs_last_stats: NULL");
+            return GB_ERR_INVALID;
+        }
+        if (!t_stats.valid || !t_stats.dev) {
+            set_error("bfs_last_stats: no BFS call on this thread yet");
+            return GB_ERR_INVALID;
+        }
+        BfsDevStats h;
+        GB_CUDA(cudaStreamSynchronize(t_stats.stream));
+        GB_CUDA(cudaMemcpy(&h, t_stats.dev, sizeof(h), cudaMemcpyDeviceToHost));
+        out->nlevels = (int64_t)h.nlevels;
+        out->edges_examined = (int64_t)h.edges_examined;
+        out->vertices_touched = (int64_t)h.vertices_touched;
+        out->reached = (int64_t)h.reached;
+        out->td_levels = (int64_t)h.td_levels;
+        out->bu_levels = (int64_t)h.bu_levels;
+        return GB_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,478 @@
+// Kernel 2 (Sec. 2.3): level-synchronous, direction-optimising BFS.
+//
+// One persistent cooperative kernel runs the whole search; levels are
+// separated by a software grid barrier (bounded waits), which is the level
+// synchronisation of Sec. 2.3.2 ("process an entire level in one step in
+// parallel", and the failure case without it).  Per level the kernel runs one
+// of two steps, chosen identically by every block from global counters:
+//
+//  top-down (Algorithm "Parallel BFS", Sec. 2.3.2): for every frontier vertex
+//    and every neighbour in parallel, an unvisited neighbour is claimed with
+//    an atomic OR on the visited bitmap; the winner writes parent and level
+//    and appends the vertex to the next queue with one atomic per warp.
+//    Frontier vertices of degree <= big_degree are expanded 32 at a time by a
+//    warp that gathers their adjacency lists as one contiguous stream of
+//    edges; larger ones are cut into 256-edge chunks spread over all warps.
+//  bottom-up (Beamer, Asanovic, Patterson, SC 2012): every unvisited vertex
+//    scans its sorted adjacency list and stops at the first neighbour in the
+//    frontier bitmap, which is therefore the smallest-id parent.
+//
+// The switch follows Beamer: top-down -> bottom-up when the frontier's edges
+// exceed (edges of unvisited vertices) / alpha, back when the frontier is
+// shrinking and smaller than n / beta.  Both steps leave the next frontier as
+// a queue and as a bitmap, so switching costs nothing.  In canonical mode the
+// parents of vertices claimed top-down are recomputed at the next level as
+// their smallest-id neighbour in the previous frontier, which makes the tree
+// the unique one the oracle derives from the level array (Sec. 2.3.1).
+//
+// Memory layout of one search: visited bitmap and a ring of four frontier
+// bitmaps (n/8 bytes each, L2-resident at SCALE 26: 8 MB), one int32 queue of
+// n entries holding every level's frontier back to back (the BFS order), a
+// list of big frontier vertices with their chunk bases, and four level
+// control records (ring).
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+
+namespace gb {
+namespace {
+
+constexpr int BFS_THREADS = 512;
+constexpr int BIG_CHUNK = 256;      // edges per chunk of a big frontier vertex
+constexpr int BU_SERIAL_MAX = 32;   // bottom-up: larger rows are scanned by the whole warp
+constexpr int SITE_BFS_BAR = 20;
+constexpr int SITE_BFS_LEVELS = 21;
+
+struct LevelCtl {
+    unsigned long long qcnt;  // vertices appended to the next queue
+    unsigned long long mf;    // sum of their degrees
+    unsigned long long big;   // (count << 32) | chunks of big vertices appended
+    unsigned long long pad;
+};
+
+struct BigEnt {
+    int32_t u;
+    uint32_t cbase;
+};
+
+struct WsHeader {
+    GridBarrier bar;
+    unsigned done;
+    unsigned pad0;
+    LevelCtl ctl[4];
+    unsigned long long acc[6];  // edges, touched, reached, nlevels, td, bu
+};
+
+struct BfsArgs {
+    const int64_t *off;
+    const int32_t *col;
+    int64_t n;
+    int64_t nnz;
+    int32_t root;
+    int32_t *parent;
+    int32_t *level;
+    unsigned *vis;
+    unsigned *fb;  // 4 bitmaps of nw words
+    int64_t nw;
+    int32_t *queue;
+    BigEnt *bigq;
+    WsHeader *hdr;
+    DevStatus *st;
+    BfsDevStats *stats;
+    float alpha;
+    float beta;
+    int big_deg;
+    int canonical;
+    uint64_t timeout_ns;
+};
+
+// The big list is written by other blocks during the previous level: read it
+// from L2, never from a possibly stale L1 line.
+__device__ __forceinline__ BigEnt load_big(const BigEnt *q, int64_t i)
+{
+    const unsigned long long r = __ldcg(reinterpret_cast<const unsigned long long *>(q) + i);
+    BigEnt b;
+    b.u = (int32_t)(r & 0xffffffffull);
+    b.cbase = (uint32_t)(r >> 32);
+    return b;
+}
+
+__device__ __forceinline__ unsigned nchunks(int64_t deg)
+{
+    return (unsigned)((deg + BIG_CHUNK - 1) / BIG_CHUNK);
+}
+
+// Warp-collective: append the lanes with `won` to the next frontier (queue,
+// degree sum and, for big degrees, the chunk list).
+__device__ __forceinline__ void append_next(bool won, int32_t v, int64_t dv, const BfsArgs &a,
+                                            LevelCtl *nxt, int64_t qnext_base, int64_t bnext_base)
+{
+    const unsigned bal = __ballot_sync(kFull, won);
+    if (bal == 0) return;
+    const unsigned lane = lane_id();
+    const int leader = __ffs(bal) - 1;
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(&nxt->qcnt, (unsigned long long)__popc(bal));
+    base = __shfl_sync(kFull, base, leader);
+    unsigned long long dsum = warp_sum((unsigned long long)(won ? dv : 0));
+    if (won) {
+        __stcg(&a.queue[qnext_base + (int64_t)base + __popc(bal & lanemask_lt())], v);
+        if (dv > a.big_deg) {
+            const unsigned long long p =
+                atomicAdd(&nxt->big, (1ull << 32) | (unsigned long long)nchunks(dv));
+            const unsigned long long packed =
+                (unsigned long long)(uint32_t)v | ((p & 0xffffffffull) << 32);
+            __stcg(reinterpret_cast<unsigned long long *>(a.bigq) + bnext_base + (int64_t)(p >> 32),
+                   packed);
+        }
+    }
+    if ((int)lane == leader) atomicAdd(&nxt->mf, dsum);
+}
+
+// Warp-collective top-down visit of edge (src -> v) for the lanes with `valid`.
+__device__ __forceinline__ void td_visit(bool valid, int32_t src, int32_t v, int l,
+                                         const BfsArgs &a, unsigned *Fn, LevelCtl *nxt,
+                                         int64_t qnext_base, int64_t bnext_base)
+{
+    bool won = false;
+    int64_t dv = 0;
+    if (valid) {
+        const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
+        if (!(ldcg_u32(&a.vis[w]) & bit)) {
+            const unsigned old = atomicOr(&a.vis[w], bit);
+            if (!(old & bit)) {
+                won = true;
+                a.parent[v] = src;
+                a.level[v] = l + 1;
+                atomicOr(&Fn[w], bit);
+                dv = a.off[v + 1] - a.off[v];
+            }
+        }
+    }
+    append_next(won, v, dv, a, nxt, qnext_base, bnext_base);
+}
+
+__global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
+{
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+    const unsigned lane = lane_id();
+    const int64_t gwarp = gtid >> 5;
+    const int64_t nwarps = gthreads >> 5;
+    const int64_t n = a.n, nw = a.nw;
+    WsHeader *h = a.hdr;
+    const int32_t root = a.root;
+
+    // ---- init: outputs to -1, bitmaps cleared, the root placed
+    for (int64_t v = gtid; v < n; v += gthreads) {
+        a.parent[v] = v == root ? root : -1;
+        a.level[v] = v == root ? 0 : -1;
+    }
+    for (int64_t w = gtid; w < nw; w += gthreads) {
+        const unsigned tail = (w == nw - 1 && (n & 31)) ? ~((1u << (n & 31)) - 1u) : 0u;
+        const unsigned rb = (w == (root >> 5)) ? 1u << (root & 31) : 0u;
+        a.vis[w] = tail | rb;  // ids >= n count as visited
+        a.fb[w] = rb;
+        a.fb[nw + w] = 0;
+        a.fb[2 * nw + w] = 0;
+        a.fb[3 * nw + w] = 0;
+    }
+    if (gtid == 0) {
+        const int64_t dr = a.off[root + 1] - a.off[root];
+        a.queue[0] = root;
+        h->ctl[0].qcnt = 1;
+        h->ctl[0].mf = (unsigned long long)dr;
+        if (dr > a.big_deg) {
+            h->ctl[0].big = (1ull << 32) | nchunks(dr);
+            BigEnt be;
+            be.u = root;
+            be.cbase = 0;
+            a.bigq[0] = be;
+        }
+    }
+    if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_BFS_BAR)) return;
+
+    int64_t qbase = 0, bbase = 0, prev_qn = 0;
+    double mu = (double)a.nnz;
+    bool td = true, prev_td = true;
+    unsigned long long my_edges = 0, my_touched = 0;
+    int l = 0;
+    for (;; ++l) {
+        LevelCtl *cur = &h->ctl[l & 3];
+        const int64_t qn = (int64_t)ldcg_u64(&cur->qcnt);
+        if (qn == 0) break;
+        if (l > n) {
+            if (gtid == 0) record_error(a.st, GB_ERR_TIMEOUT, SITE_BFS_LEVELS, l);
+            break;
+        }
+        const double mf = (double)ldcg_u64(&cur->mf);
+        const unsigned long long bigp = ldcg_u64(&cur->big);
+        const int64_t nb = (int64_t)(bigp >> 32);
+        const int64_t nc = (int64_t)(bigp & 0xffffffffull);
+        mu -= mf;
+        if (l > 0) {
+            if (td) {
+                if (mf > mu / a.alpha) td = false;
+            } else if (qn < prev_qn && (double)qn < (double)n / a.beta) {
+                td = true;
+            }
+        }
+        unsigned *F = a.fb + (size_t)(l & 3) * nw;
+        unsigned *Fn = a.fb + (size_t)((l + 1) & 3) * nw;
+        unsigned *Fz = a.fb + (size_t)((l + 2) & 3) * nw;
+        unsigned *Fp = a.fb + (size_t)((l + 3) & 3) * nw;
+        LevelCtl *nxt = &h->ctl[(l + 1) & 3];
+        const int64_t qnext_base = qbase + qn;
+        const int64_t bnext_base = bbase + nb;
+
+        // Clear the bitmap and control record that level l+1 will fill.
+        for (int64_t w = gtid; w < nw; w += gthreads) Fz[w] = 0;
+        if (gtid == 0) {
+            LevelCtl z = {0, 0, 0, 0};
+            h->ctl[(l + 2) & 3] = z;
+        }
+
+        // Canonical parents of vertices claimed top-down at level l-1.
+        if (a.canonical && l > 0 && prev_td) {
+            for (int64_t i = gtid; i < qn; i += gthreads) {
+                const int32_t u = ldcg_i32(&a.queue[qbase + i]);
+                const int64_t e = a.off[u + 1];
+                for (int64_t j = a.off[u]; j < e; ++j) {
+                    const int32_t v = a.col[j];
+                    if ((ldcg_u32(&Fp[v >> 5]) >> (v & 31)) & 1u) {
+                        a.parent[u] = v;
+                        break;
+                    }
+                }
+            }
+        }
+
+        if (td) {
+            // (a) chunks of big frontier vertices, a contiguous range per warp
+            if (nc > 0) {
+                const int64_t per = (nc + nwarps - 1) / nwarps;
+                const int64_t c0 = gwarp * per;
+                const int64_t c1 = c0 + per < nc ? c0 + per : nc;
+                if (c0 < c1) {
+                    int64_t lo = 0, hi = nb;  // largest i with cbase(i) <= c0
+                    while (hi - lo > 1) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        if ((int64_t)load_big(a.bigq, bbase + mid).cbase <= c0) lo = mid;
+                        else hi = mid;
+                    }
+                    int64_t ow = lo;
+                    BigEnt be = load_big(a.bigq, bbase + ow);
+                    for (int64_t c = c0; c < c1; ++c) {
+                        while (ow + 1 < nb && (int64_t)load_big(a.bigq, bbase + ow + 1).cbase <= c) {
+                            ++ow;
+                            be = load_big(a.bigq, bbase + ow);
+                        }
+                        const int64_t s = a.off[be.u] + (c - (int64_t)be.cbase) * BIG_CHUNK;
+                        const int64_t eu = a.off[be.u + 1];
+                        const int64_t e = s + BIG_CHUNK < eu ? s + BIG_CHUNK : eu;
+                        if (lane == 0) my_edges += (unsigned long long)(e - s);
+                        for (int64_t b = s; b < e; b += 32) {
+                            const int64_t j = b + lane;
+                            const bool valid = j < e;
+                            const int32_t v = valid ? a.col[j] : 0;
+                            td_visit(valid, be.u, v, l, a, Fn, nxt, qnext_base, bnext_base);
+                        }
+                    }
+                }
+            }
+            // (b) the other frontier vertices, 32 per warp, edges gathered as one stream
+            for (int64_t i0 = gwarp * 32; i0 < qn; i0 += nwarps * 32) {
+                const int64_t i = i0 + lane;
+                int32_t u = 0;
+                int64_t s = 0, d = 0;
+                if (i < qn) {
+                    u = ldcg_i32(&a.queue[qbase + i]);
+                    s = a.off[u];
+                    d = a.off[u + 1] - s;
+                    if (d > a.big_deg) d = 0;
+                }
+                const int64_t incl = warp_inclusive_scan(d);
+                const int64_t total = __shfl_sync(kFull, incl, 31);
+                const int64_t excl = incl - d;
+                my_edges += d;
+                my_touched += (i < qn);
+                for (int64_t b = 0; b < total; b += 32) {
+                    const int64_t k = b + lane;
+                    int owner = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int cand = owner + step;
+                        const int64_t ex = __shfl_sync(kFull, excl, cand);
+                        if (ex <= k) owner = cand;
+                    }
+                    const int32_t src = __shfl_sync(kFull, u, owner);
+                    const int64_t so = __shfl_sync(kFull, s, owner);
+                    const int64_t eo = __shfl_sync(kFull, excl, owner);
+                    const bool valid = k < total;
+                    const int32_t v = valid ? a.col[so + (k - eo)] : 0;
+                    td_visit(valid, src, v, l, a, Fn, nxt, qnext_base, bnext_base);
+                }
+            }
+        } else {
+            // bottom-up: warp w owns the 32 vertices of visited word w
+            for (int64_t w = gwarp; w < nw; w += nwarps) {
+                const unsigned vw = ldcg_u32(&a.vis[w]);
+                if (vw == kFull) continue;
+                const int64_t u = w * 32 + lane;
+                const bool cand = !((vw >> lane) & 1u);
+                int64_t s = 0, e = 0;
+                if (cand) {
+                    s = a.off[u];
+                    e = a.off[u + 1];
+                }
+                const int64_t deg = e - s;
+                int32_t found = -1;
+                if (cand && deg <= BU_SERIAL_MAX) {
+                    int64_t j = s;
+                    for (; j < e; ++j) {
+                        const int32_t v = a.col[j];
+                        if ((ldcg_u32(&F[v >> 5]) >> (v & 31)) & 1u) {
+                            found = v;
+                            break;
+                        }
+                    }
+                    my_edges += (found >= 0) ? (j - s + 1) : deg;
+                }
+                my_touched += cand;
+                unsigned bigm = __ballot_sync(kFull, cand && deg > BU_SERIAL_MAX);
+                while (bigm) {
+                    const int jl = __ffs(bigm) - 1;
+                    bigm &= bigm - 1;
+                    const int64_t sj = __shfl_sync(kFull, s, jl);
+                    const int64_t ej = __shfl_sync(kFull, e, jl);
+                    int32_t fj = -1;
+                    int64_t scanned = 0;
+                    for (int64_t b = sj; b < ej; b += 32) {
+                        const int64_t j = b + lane;
+                        int32_t v = 0;
+                        bool hit = false;
+                        if (j < ej) {
+                            v = a.col[j];
+                            hit = (ldcg_u32(&F[v >> 5]) >> (v & 31)) & 1u;
+                        }
+                        const unsigned hb = __ballot_sync(kFull, hit);
+                        if (hb) {
+                            const int fl = __ffs(hb) - 1;
+                            fj = __shfl_sync(kFull, v, fl);
+                            scanned += fl + 1;
+                            break;
+                        }
+                        scanned += (ej - b < 32 ? ej - b : 32);
+                    }
+                    if ((int)lane == jl) {
+                        found = fj;
+                        my_edges += scanned;
+                    }
+                }
+                const bool won = found >= 0;
+                if (won) {
+                    a.parent[u] = found;
+                    a.level[u] = l + 1;
+                }
+                const unsigned nm = __ballot_sync(kFull, won);
+                if (nm && lane == 0) {
+                    __stcg(&a.vis[w], vw | nm);
+                    __stcg(&Fn[w], nm);
+                }
+                append_next(won, (int32_t)u, deg, a, nxt, qnext_base, bnext_base);
+            }
+        }
+        prev_td = td;
+        prev_qn = qn;
+        qbase += qn;
+        bbase += nb;
+        if (gtid == 0) atomicAdd(&h->acc[td ? 4 : 5], 1ull);
+        if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_BFS_BAR)) return;
+    }
+
+    // ---- statistics: block partial sums, the last block publishes them
+    my_edges = warp_sum(my_edges);
+    my_touched = warp_sum(my_touched);
+    if (lane == 0) {
+        if (my_edges) atomicAdd(&h->acc[0], my_edges);
+        if (my_touched) atomicAdd(&h->acc[1], my_touched);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&h->done, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            BfsDevStats s;
+            s.nlevels = (unsigned long long)l;
+            s.edges_examined = ldcg_u64(&h->acc[0]);
+            s.vertices_touched = ldcg_u64(&h->acc[1]);
+            s.reached = (unsigned long long)qbase;
+            s.td_levels = ldcg_u64(&h->acc[4]);
+            s.bu_levels = ldcg_u64(&h->acc[5]);
+            *a.stats = s;
+        }
+    }
+}
+
+}  // namespace
+
+int bfs_pick_blocks(int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_kernel, BFS_THREADS, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return num_sms * std::min(per_sm, 2);
+}
+
+gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level,
+                   BfsDevStats *stats, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    const gb_bfs_options &o = options();
+    const int64_t n = g->n;
+    const int64_t nw = (n + 31) / 32;
+    const int big_deg = std::max(o.big_degree, 1);
+    const int64_t bigcap = g->nnz / (big_deg + 1) + 2;
+    // one allocation: header | visited | 4 frontier bitmaps | queue | big list
+    const size_t off_vis = (sizeof(WsHeader) + 255) & ~size_t(255);
+    const size_t off_fb = off_vis + ((nw * 4 + 255) & ~size_t(255));
+    const size_t off_q = off_fb + ((4 * nw * 4 + 255) & ~size_t(255));
+    const size_t off_big = off_q + ((n * 4 + 255) & ~size_t(255));
+    const size_t total = off_big + bigcap * sizeof(BigEnt);
+    unsigned char *ws = nullptr;
+    GB_CUDA(cudaMallocAsync((void **)&ws, total, s));
+    GB_CUDA(cudaMemsetAsync(ws, 0, sizeof(WsHeader), s));
+    BfsArgs a;
+    a.off = g->off;
+    a.col = g->col;
+    a.n = n;
+    a.nnz = g->nnz;
+    a.root = (int32_t)root;
+    a.parent = parent;
+    a.level = level;
+    a.hdr = reinterpret_cast<WsHeader *>(ws);
+    a.vis = reinterpret_cast<unsigned *>(ws + off_vis);
+    a.fb = reinterpret_cast<unsigned *>(ws + off_fb);
+    a.nw = nw;
+    a.queue = reinterpret_cast<int32_t *>(ws + off_q);
+    a.bigq = reinterpret_cast<BigEnt *>(ws + off_big);
+    a.st = ctx->status;
+    a.stats = stats;
+    a.alpha = (float)o.alpha;
+    a.beta = (float)o.beta;
+    a.big_deg = big_deg;
+    a.canonical = o.canonical_parents;
+    a.timeout_ns = timeout_ns();
+    void *args[] = {&a};
+    GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfs_kernel, dim3(ctx->bfs_blocks),
+                                        dim3(BFS_THREADS), args, 0, s));
+    GB_CUDA(cudaFreeAsync(ws, s));
+    return GB_OK;
+}
+
+}  // namespace gb

@@ -1,0 +1,141 @@
+// Shared device helpers of the GB300 Graph500 library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gb300bfs.h"
+#include "internal.h"
+
+namespace gb {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Device status word: the first error a kernel records wins; nothing traps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void record_error(DevStatus *st, int code, int where, long long detail)
+{
+    if (atomicCAS(&st->code, 0, code) == 0) {
+        st->where = where;
+        st->detail = detail;
+    }
+}
+
+__device__ __forceinline__ int status_code(const DevStatus *st)
+{
+    return *(volatile const int *)&st->code;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
+{
+    return *(volatile const unsigned *)p;
+}
+
+// ---------------------------------------------------------------------------
+// Software grid barrier for cooperative (all-blocks-resident) launches.
+// Sense by generation counter; every wait is bounded by `timeout_ns` of the
+// global timer, after which the block records GB_ERR_TIMEOUT and the barrier
+// returns false in every block (blocks also leave early once any block has
+// recorded an error).
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, DevStatus *st, uint64_t timeout_ns,
+                                          int site)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned g = ld_acquire_u32(&b->gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&b->count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            st_release_u32(&b->gen, g + 1u);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (ld_acquire_u32(&b->gen) == g) {
+                if (status_code(st) != 0) { ok = 0; break; }
+                if ((++spins & 31u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
+                    record_error(st, GB_ERR_TIMEOUT, site, (long long)blockIdx.x);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && status_code(st) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// inclusive prefix sum across the warp
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v)
+{
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(kFull, v, o);
+        if (lane >= (unsigned)o) v += t;
+    }
+    return v;
+}
+
+// Loads that bypass L1: data written by other blocks of the same kernel.
+__device__ __forceinline__ unsigned ldcg_u32(const unsigned *p) { return __ldcg(p); }
+__device__ __forceinline__ int ldcg_i32(const int *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ldcg_u64(const unsigned long long *p)
+{
+    return __ldcg(p);
+}
+
+}  // namespace gb

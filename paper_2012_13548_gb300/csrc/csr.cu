@@ -1,0 +1,212 @@
+// Kernel 1 (Sec. 2.2): the undirected CSR graph from the Kronecker tuples.
+//
+//   1. symmetrise: tuple (u,v) becomes keys (u << S | v) and (v << S | u),
+//      S = scale, so one key holds an ordered pair in 2*S contiguous bits;
+//   2. radix sort of the keys (ceil(2S/8) passes) -- the "sorted array" the
+//      paper's CSR needs (Sec. 2.2, Sec. 4.2);
+//   3. a key is kept if it is not a self-loop (u == v) and differs from its
+//      predecessor (duplicates, Sec. 2.1 "may be ignored"); a count pass and a
+//      scan of the per-tile counts give each kept key its column slot;
+//   4. the write pass stores the columns and, at every change of row between
+//      neighbouring keys, the offsets of all rows in between: an empty row
+//      repeats the previous offset and off[n] = nnz (Sec. 2.2).
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+
+namespace gb {
+namespace {
+
+constexpr int FIN_THREADS = 256;
+constexpr int FIN_ITEMS = 16;
+constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;  // 4096 keys
+constexpr int SITE_K1_RANGE = 10;
+
+__global__ void k1_sym_kernel(const int64_t *__restrict__ edges, int64_t m, int scale,
+                              ulonglong2 *__restrict__ keys, DevStatus *st)
+{
+    const int64_t n = int64_t(1) << scale;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        int64_t u = edges[e];
+        int64_t v = edges[m + e];
+        if (u < 0 || u >= n || v < 0 || v >= n) {
+            record_error(st, GB_ERR_RANGE, SITE_K1_RANGE, (long long)e);
+            u = v = 0;  // a self-loop: dropped below
+        }
+        keys[e] = make_ulonglong2(((uint64_t)u << scale) | (uint64_t)v,
+                                  ((uint64_t)v << scale) | (uint64_t)u);
+    }
+}
+
+__device__ __forceinline__ bool k1_keep(const uint64_t *keys, int64_t i, uint64_t k, int scale,
+                                        uint64_t vmask)
+{
+    if ((k >> scale) == (k & vmask)) return false;  // self-loop
+    return i == 0 || keys[i - 1] != k;              // first of a run of duplicates
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) k1_count_kernel(const uint64_t *__restrict__ keys,
+                                                               int64_t nk, int scale,
+                                                               unsigned *__restrict__ tile_cnt)
+{
+    __shared__ unsigned s_w[FIN_THREADS / 32];
+    const uint64_t vmask = (uint64_t(1) << scale) - 1;
+    const int64_t t0 = (int64_t)blockIdx.x * FIN_TILE;
+    unsigned c = 0;
+#pragma unroll 4
+    for (int j = 0; j < FIN_ITEMS; ++j) {
+        const int64_t i = t0 + j * FIN_THREADS + threadIdx.x;
+        if (i < nk) c += k1_keep(keys, i, keys[i], scale, vmask);
+    }
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < FIN_THREADS / 32; ++w) t += s_w[w];
+        tile_cnt[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of the tile counts (one block; each thread a contiguous run).
+__global__ void __launch_bounds__(1024) k1_scan_tiles_kernel(const unsigned *__restrict__ cnt,
+                                                             int64_t ntiles,
+                                                             unsigned long long *__restrict__ base)
+{
+    __shared__ unsigned long long s_w[32];
+    const int tid = threadIdx.x;
+    const int64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = (int64_t)tid * per;
+    const int64_t b = b0 < ntiles ? b0 : ntiles;
+    const int64_t e = b + per < ntiles ? b + per : ntiles;
+    unsigned long long sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += cnt[i];
+    unsigned long long incl = warp_inclusive_scan(sum);
+    if ((tid & 31) == 31) s_w[tid >> 5] = incl;
+    __syncthreads();
+    if (tid < 32) {
+        unsigned long long w = s_w[tid];
+        unsigned long long wi = warp_inclusive_scan(w);
+        s_w[tid] = wi - w;
+    }
+    __syncthreads();
+    unsigned long long run = s_w[tid >> 5] + incl - sum;
+    for (int64_t i = b; i < e; ++i) {
+        base[i] = run;
+        run += cnt[i];
+    }
+    if (tid == blockDim.x - 1) base[ntiles] = run;
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) k1_write_kernel(
+    const uint64_t *__restrict__ keys, int64_t nk, int scale,
+    const unsigned long long *__restrict__ tile_base, int64_t n, int64_t *__restrict__ off,
+    int32_t *__restrict__ col, int64_t nnz, DevStatus *st)
+{
+    __shared__ unsigned s_w[FIN_THREADS / 32];
+    const uint64_t vmask = (uint64_t(1) << scale) - 1;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    // blocked: thread t owns keys [t0 + t*ITEMS, t0 + (t+1)*ITEMS)
+    const int64_t i0 = (int64_t)blockIdx.x * FIN_TILE + (int64_t)threadIdx.x * FIN_ITEMS;
+    uint64_t k[FIN_ITEMS];
+    unsigned keep = 0, c = 0;
+#pragma unroll
+    for (int j = 0; j < FIN_ITEMS; ++j) {
+        const int64_t i = i0 + j;
+        k[j] = i < nk ? keys[i] : 0;
+        const bool kp = i < nk && k1_keep(keys, i, k[j], scale, vmask);
+        keep |= (unsigned)kp << j;
+        c += kp;
+    }
+    const unsigned incl = warp_inclusive_scan(c);
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    unsigned woff = 0;
+    for (int w = 0; w < warp; ++w) woff += s_w[w];
+    int64_t pos = (int64_t)tile_base[blockIdx.x] + woff + incl - c;
+#pragma unroll
+    for (int j = 0; j < FIN_ITEMS; ++j) {
+        const int64_t i = i0 + j;
+        if (i >= nk) break;
+        const int64_t r = (int64_t)(k[j] >> scale);
+        const int64_t rp = i == 0 ? -1 : (int64_t)(keys[i - 1] >> scale);
+        for (int64_t x = rp + 1; x <= r; ++x) off[x] = pos;  // rows rp+1..r start here
+        if ((keep >> j) & 1u) {
+            if (pos < nnz) col[pos] = (int32_t)(k[j] & vmask);
+            else record_error(st, GB_ERR_RANGE, 11, pos);
+            ++pos;
+        }
+        if (i == nk - 1)
+            for (int64_t x = r + 1; x <= n; ++x) off[x] = pos;  // trailing empty rows, off[n]
+    }
+}
+
+}  // namespace
+
+gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    const int64_t n = int64_t(1) << scale;
+    const int64_t nk = 2 * m;
+    g->n = n;
+    g->scale = scale;
+    g->device = ctx->device;
+    GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
+    if (nk == 0) {
+        g->nnz = 0;
+        GB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(int64_t)));
+        GB_CUDA(cudaMalloc(&g->col, 16));
+        GB_CUDA(cudaMemsetAsync(g->off, 0, (n + 1) * sizeof(int64_t), s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        return GB_OK;
+    }
+    uint64_t *k0 = nullptr, *k1 = nullptr, *ks = nullptr;
+    GB_CUDA(alloc_async(&k0, (size_t)nk, s));
+    GB_CUDA(alloc_async(&k1, (size_t)nk, s));
+    k1_sym_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(edges, m, scale,
+                                                   reinterpret_cast<ulonglong2 *>(k0), ctx->status);
+    GB_CUDA(cudaGetLastError());
+    gb_status rc = radix_sort(k0, k1, nullptr, nullptr, nk, 0, 2 * scale, &ks, nullptr, s);
+    if (rc != GB_OK) return rc;
+    const int64_t ntiles = (nk + FIN_TILE - 1) / FIN_TILE;
+    unsigned *tcnt = nullptr;
+    unsigned long long *tbase = nullptr;
+    GB_CUDA(alloc_async(&tcnt, (size_t)ntiles, s));
+    GB_CUDA(alloc_async(&tbase, (size_t)ntiles + 1, s));
+    k1_count_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tcnt);
+    k1_scan_tiles_kernel<<<1, 1024, 0, s>>>(tcnt, ntiles, tbase);
+    GB_CUDA(cudaGetLastError());
+    unsigned long long nnz = 0;
+    DevStatus hst;
+    GB_CUDA(cudaMemcpyAsync(&nnz, tbase + ntiles, sizeof(nnz), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&hst, ctx->status, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (hst.code != 0) {
+        GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
+        cudaFreeAsync(k0, s);
+        cudaFreeAsync(k1, s);
+        cudaFreeAsync(tcnt, s);
+        cudaFreeAsync(tbase, s);
+        cudaStreamSynchronize(s);
+        set_error(hst.code == GB_ERR_RANGE ? "graph_build_csr: an edge endpoint is outside [0, 2^scale)"
+                                           : "graph_build_csr: device error during the build");
+        return (gb_status)hst.code;
+    }
+    g->nnz = (int64_t)nnz;
+    GB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(int64_t)));
+    GB_CUDA(cudaMalloc(&g->col, std::max<int64_t>(g->nnz, 4) * sizeof(int32_t)));
+    k1_write_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tbase, n, g->off, g->col,
+                                                             g->nnz, ctx->status);
+    GB_CUDA(cudaGetLastError());
+    GB_CUDA(cudaFreeAsync(k0, s));
+    GB_CUDA(cudaFreeAsync(k1, s));
+    GB_CUDA(cudaFreeAsync(tcnt, s));
+    GB_CUDA(cudaFreeAsync(tbase, s));
+    return GB_OK;
+}
+
+}  // namespace gb

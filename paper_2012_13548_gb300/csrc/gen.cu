@@ -1,0 +1,139 @@
+// Kronecker edge-list generator on the device (Sec. 2.1).
+//
+// #V = 2^scale, #E = edgefactor * #V.  Tuple e makes `scale` independent
+// quadrant choices, one per bit level, from two SplitMix64 draws (Steele, Lea,
+// Flood 2014) at counters 2(e*scale+k) and 2(e*scale+k)+1; a 53-bit draw is
+// compared with integer thresholds floor(p * 2^53) so that the row bit is set
+// with probability C+D and the column bit with B/(A+B) or D/(C+D).  Vertex
+// numbers are then permuted (rank under (SplitMix64(seed_perm, v), v)) and the
+// tuples shuffled (position j takes the tuple of rank j under
+// (SplitMix64(seed_shuf, e), e)), both by the device radix sort.  Duplicates
+// and self-loops stay in the list, as Sec. 2.1 requires.
+#include "common.cuh"
+#include "internal.h"
+
+namespace gb {
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void gen_hash_iota_kernel(int64_t count, uint64_t seed, uint64_t *__restrict__ keys,
+                                     uint32_t *__restrict__ ids)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        keys[i] = splitmix64(seed, (uint64_t)i);
+        ids[i] = (uint32_t)i;
+    }
+}
+
+// pi[v] = rank of v: the sorted id list read as rank -> vertex, inverted.
+__global__ void gen_perm_scatter_kernel(const uint32_t *__restrict__ sorted_ids, int64_t n,
+                                        int32_t *__restrict__ pi, DevStatus *st)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const uint32_t v = sorted_ids[r];
+        if (v < n) pi[v] = (int32_t)r;
+        else record_error(st, GB_ERR_RANGE, 40, r);
+    }
+}
+
+// Output position j: tuple order[j], generated from its counters and relabelled.
+__global__ void __launch_bounds__(256) gen_edges_kernel(int scale, int64_t m, uint64_t t_ab,
+                                                        uint64_t t_a, uint64_t t_c,
+                                                        uint64_t seed_gen,
+                                                        const uint32_t *__restrict__ order,
+                                                        const int32_t *__restrict__ pi,
+                                                        int64_t *__restrict__ edges, DevStatus *st)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const uint64_t e = order[j];
+        if (e >= (uint64_t)m) {
+            record_error(st, GB_ERR_RANGE, 41, j);
+            continue;
+        }
+        uint32_t u = 0, v = 0;
+        uint64_t ctr = 2ull * e * (uint64_t)scale;
+        for (int k = 0; k < scale; ++k, ctr += 2) {
+            const uint64_t x1 = splitmix64(seed_gen, ctr) >> 11;
+            const uint64_t x2 = splitmix64(seed_gen, ctr + 1) >> 11;
+            const uint32_t ii = x1 >= t_ab;
+            const uint32_t jj = x2 >= (ii ? t_c : t_a);
+            u |= ii << k;
+            v |= jj << k;
+        }
+        edges[j] = pi[u];
+        edges[m + j] = pi[v];
+    }
+}
+
+uint64_t threshold53(double p)
+{
+    const double two53 = 9007199254740992.0;
+    if (!(p > 0.0)) return 0;  // also catches NaN from an empty quadrant pair
+    return (uint64_t)(p * two53);
+}
+
+}  // namespace
+
+gb_status kron_generate_impl(int scale, int edgefactor, double a, double b, double c,
+                             uint64_t seed_gen, uint64_t seed_perm, uint64_t seed_shuf,
+                             int64_t *edges, cudaStream_t s)
+{
+    if (scale < 1 || scale > 30 || edgefactor < 1 || !edges) {
+        set_error("kron_generate: need 1 <= scale <= 30, edgefactor >= 1, edges != NULL");
+        return GB_ERR_INVALID;
+    }
+    const int64_t n = int64_t(1) << scale;
+    const int64_t m = n * edgefactor;
+    if (m > (int64_t(1) << 32)) {
+        set_error("kron_generate: more than 2^32 tuples");
+        return GB_ERR_RANGE;
+    }
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    const double d = 1.0 - a - b - c;
+    const uint64_t t_ab = threshold53(a + b);
+    const uint64_t t_a = threshold53(a / (a + b));
+    const uint64_t t_c = threshold53(c / (c + d));
+
+    const int blocks = ctx->num_sms * 8;
+    // Vertex permutation.
+    uint64_t *k0 = nullptr, *k1 = nullptr, *ks = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr, *vs = nullptr;
+    int32_t *pi = nullptr;
+    GB_CUDA(alloc_async(&k0, (size_t)m, s));
+    GB_CUDA(alloc_async(&k1, (size_t)m, s));
+    GB_CUDA(alloc_async(&v0, (size_t)m, s));
+    GB_CUDA(alloc_async(&v1, (size_t)m, s));
+    GB_CUDA(alloc_async(&pi, (size_t)n, s));
+    gen_hash_iota_kernel<<<blocks, 256, 0, s>>>(n, seed_perm, k0, v0);
+    GB_CUDA(cudaGetLastError());
+    gb_status rc = radix_sort(k0, k1, v0, v1, n, 0, 64, &ks, &vs, s);
+    if (rc != GB_OK) return rc;
+    gen_perm_scatter_kernel<<<blocks, 256, 0, s>>>(vs, n, pi, ctx->status);
+    // Edge shuffle order.
+    gen_hash_iota_kernel<<<blocks, 256, 0, s>>>(m, seed_shuf, k0, v0);
+    GB_CUDA(cudaGetLastError());
+    rc = radix_sort(k0, k1, v0, v1, m, 0, 64, &ks, &vs, s);
+    if (rc != GB_OK) return rc;
+    gen_edges_kernel<<<blocks, 256, 0, s>>>(scale, m, t_ab, t_a, t_c, seed_gen, vs, pi, edges,
+                                            ctx->status);
+    GB_CUDA(cudaGetLastError());
+    GB_CUDA(cudaFreeAsync(k0, s));
+    GB_CUDA(cudaFreeAsync(k1, s));
+    GB_CUDA(cudaFreeAsync(v0, s));
+    GB_CUDA(cudaFreeAsync(v1, s));
+    GB_CUDA(cudaFreeAsync(pi, s));
+    return GB_OK;
+}
+
+}  // namespace gb

@@ -1,0 +1,118 @@
+// Host-side declarations shared between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gb300bfs.h"
+
+namespace gb {
+
+// Device status word: the first error a kernel records wins; nothing traps.
+struct DevStatus {
+    int code;         // 0 or a gb_status
+    int where;        // kernel-specific site id
+    long long detail; // e.g. the offending index
+};
+
+// Per-device library context: the device status word and device limits.
+struct Context {
+    int device = -1;
+    int num_sms = 0;
+    DevStatus *status = nullptr;  // device memory
+    int bfs_blocks = 0;           // cooperative grid of the BFS kernel
+    int ms_blocks = 0;            // cooperative grid of the multi-source kernel
+};
+
+// Context of the current device (created on first use).  Returns nullptr and
+// sets the thread's error on failure.
+Context *context();
+
+// Thread-local error message.
+void set_error(const std::string &msg);
+const std::string &last_error();
+
+// Map a CUDA error to a status, recording `what`.
+gb_status cuda_fail(cudaError_t e, const char *what);
+
+#define GB_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e__ = (call);                              \
+        if (e__ != cudaSuccess) return ::gb::cuda_fail(e__, #call); \
+    } while (0)
+
+// Process-wide BFS options.
+gb_bfs_options &options();
+uint64_t timeout_ns();
+
+// Stream-ordered temporaries.
+template <typename T>
+inline cudaError_t alloc_async(T **p, size_t count, cudaStream_t s)
+{
+    return cudaMallocAsync((void **)p, count * sizeof(T) + (count == 0 ? 16 : 0), s);
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort (sort.cu): ascending LSD sort of uint64 keys by bits
+// [begin_bit, end_bit), optionally carrying uint32 values.  keys/keys_alt
+// (and vals/vals_alt) are two caller buffers of n entries; *keys_out and
+// *vals_out receive whichever buffer holds the result.
+// ---------------------------------------------------------------------------
+gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
+                     int64_t n, int begin_bit, int end_bit, uint64_t **keys_out,
+                     uint32_t **vals_out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Graph object.
+// ---------------------------------------------------------------------------
+}  // namespace gb
+
+struct gb_graph {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int scale = -1;          // -1 if built from a caller CSR of arbitrary n
+    int64_t *off = nullptr;  // device [n+1]
+    int32_t *col = nullptr;  // device [nnz]
+    int device = -1;
+};
+
+namespace gb {
+
+// Kernel 1 pieces (csr.cu).
+gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s);
+
+// Kronecker generator (gen.cu).
+gb_status kron_generate_impl(int scale, int edgefactor, double a, double b, double c,
+                             uint64_t seed_gen, uint64_t seed_perm, uint64_t seed_shuf,
+                             int64_t *edges, cudaStream_t s);
+
+// Per-call statistics written by the BFS kernels (device layout).
+struct BfsDevStats {
+    unsigned long long nlevels;
+    unsigned long long edges_examined;
+    unsigned long long vertices_touched;
+    unsigned long long reached;
+    unsigned long long td_levels;
+    unsigned long long bu_levels;
+};
+
+// Single-source BFS (bfs.cu).
+gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level,
+                   BfsDevStats *stats, cudaStream_t s);
+int bfs_pick_blocks(int num_sms);
+
+// Multi-source BFS over one graph or a batch of graphs (msbfs.cu).
+gb_status msbfs_impl(const gb_graph *g, const int64_t *roots, int k, int32_t *parents,
+                     int32_t *levels, BfsDevStats *stats, cudaStream_t s);
+gb_status multigraph_impl(const gb_graph *const *gs, int ng, const int64_t *roots, int r,
+                          int32_t *const *parents, int32_t *const *levels,
+                          BfsDevStats *stats, cudaStream_t s);
+int msbfs_pick_blocks(int num_sms);
+
+// Last-call statistics bookkeeping (api.cpp).
+void note_stats_call(BfsDevStats *dev_stats, cudaStream_t s);
+BfsDevStats *stats_buffer();
+
+}  // namespace gb

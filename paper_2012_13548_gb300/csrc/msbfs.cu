@@ -1,0 +1,677 @@
+// Batched kernel 2: multi-source BFS with per-vertex bitmask frontiers.
+//
+// Bit b of a vertex mask belongs to root b.  A level of every search is one
+// level of Algorithm "Parallel BFS" (Sec. 2.3.2) applied to all bits at once
+// (the multi-source traversal of Then et al., VLDB 2014): the frontier of
+// vertex v is M_l[v] (bits whose level at v is l), seen[v] holds the bits
+// with level <= l.  Bits are independent, so every row of the result equals
+// the single-source result of its root.
+//
+//  top-down level: (1) every active vertex v ORs M_l[v] & ~seen[u] into
+//    M_{l+1}[u] for its neighbours u (one atomic per edge that adds bits);
+//    the first writer of a vertex appends it to the next active list;
+//    (2) after a grid barrier each new vertex scans its sorted adjacency list
+//    for, per new bit, the first neighbour carrying that bit in M_l -- the
+//    smallest-id parent -- and writes levels and parents.
+//  bottom-up level: every vertex with unseen bits scans its sorted adjacency
+//    list, collecting M_l bits until all its unseen bits are found; the first
+//    neighbour to supply a bit is its parent.
+//  Rows longer than 32 entries are scanned by the whole warp, 32 neighbours a
+//  round, with a prefix-OR over the lanes so that each bit is credited to its
+//  first (smallest-id) neighbour.
+//
+// The same kernel runs a batch of graphs: vertex ids are made global by
+// per-graph offsets, every graph's roots use the low bits, and since the
+// graphs share no edges their searches cannot mix.  Masks are uint64 for up
+// to 64 roots of one graph and uint8 for up to 8 roots per graph of a batch.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <vector>
+
+namespace gb {
+namespace {
+
+constexpr int MS_THREADS = 512;
+constexpr int MS_MAXG = 64;
+constexpr int MS_BIG_CHUNK = 256;
+constexpr int MS_BIG_DEG = 256;
+constexpr int SITE_MS_BAR = 30;
+constexpr int SITE_MS_LEVELS = 31;
+
+struct MsGraph {
+    const int64_t *off;
+    const int32_t *col;
+    int64_t voff;  // first global id
+    int64_t n;
+    int32_t *par;  // [k][n]
+    int32_t *lev;  // [k][n]
+};
+
+struct MsCtl {
+    unsigned long long na;   // active vertices appended
+    unsigned long long mf;   // their degree sum
+    unsigned long long big;  // (count << 32) | chunks
+    unsigned long long pad;
+};
+
+struct MsHeader {
+    GridBarrier bar;
+    unsigned done;
+    unsigned pad0;
+    MsCtl ctl[3];
+    unsigned long long acc[6];
+};
+
+template <typename T>
+struct MsArgs {
+    const MsGraph *graphs;  // device [ng]
+    int ng;
+    int k;                  // bits in use
+    int64_t ntot;           // sum of n over graphs
+    int64_t mstride;        // ntot rounded up to 64: distance between mask buffers
+    int64_t nnz_tot;
+    const int64_t *roots;   // device [ng][k]: local root ids
+    T *seen;
+    T *mbuf;                // 3 masks of ntot (ring)
+    int32_t *act;           // 3 active lists of ntot (ring)
+    unsigned long long *bigq;  // chunk list of big active vertices (gid | cbase << 32)
+    int64_t bigcap;
+    MsHeader *hdr;
+    DevStatus *st;
+    BfsDevStats *stats;
+    float ms_alpha;
+    float ms_beta;
+    uint64_t timeout_ns;
+};
+
+template <typename T>
+__device__ __forceinline__ T ld_mask(const T *p);
+template <>
+__device__ __forceinline__ unsigned long long ld_mask(const unsigned long long *p)
+{
+    return __ldcg(p);
+}
+template <>
+__device__ __forceinline__ unsigned char ld_mask(const unsigned char *p)
+{
+    return __ldcg(p);
+}
+
+template <typename T>
+__device__ __forceinline__ T atomic_or_mask(T *p, T m);
+template <>
+__device__ __forceinline__ unsigned long long atomic_or_mask(unsigned long long *p,
+                                                              unsigned long long m)
+{
+    return atomicOr(p, m);
+}
+template <>
+__device__ __forceinline__ unsigned char atomic_or_mask(unsigned char *p, unsigned char m)
+{
+    unsigned *w = reinterpret_cast<unsigned *>(reinterpret_cast<uintptr_t>(p) & ~uintptr_t(3));
+    const unsigned sh = (unsigned)(reinterpret_cast<uintptr_t>(p) & 3u) * 8u;
+    const unsigned old = atomicOr(w, (unsigned)m << sh);
+    return (unsigned char)(old >> sh);
+}
+
+template <typename T>
+__device__ __forceinline__ void st_mask(T *p, T v)
+{
+    *reinterpret_cast<volatile T *>(p) = v;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_mask(T v, int src)
+{
+    return (T)__shfl_sync(kFull, (unsigned long long)v, src);
+}
+template <typename T>
+__device__ __forceinline__ T shfl_up_mask(T v, int d)
+{
+    return (T)__shfl_up_sync(kFull, (unsigned long long)v, d);
+}
+
+// OR of the masks of lanes below this one.
+template <typename T>
+__device__ __forceinline__ T warp_exclusive_or(T v)
+{
+    const unsigned lane = lane_id();
+    T incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T t = shfl_up_mask(incl, o);
+        if (lane >= (unsigned)o) incl |= t;
+    }
+    const T ex = shfl_up_mask(incl, 1);
+    return lane == 0 ? (T)0 : ex;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_or(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v |= (T)__shfl_xor_sync(kFull, (unsigned long long)v, o);
+    return v;
+}
+
+// graph index of global vertex id (graphs sorted by voff; s_voff has ng+1 entries)
+__device__ __forceinline__ int find_graph(const int64_t *s_voff, int ng, int64_t gid)
+{
+    int lo = 0, hi = ng;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_voff[mid] <= gid) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ void write_parents(const MsGraph &G, int64_t local, T bits, int32_t p)
+{
+    while (bits) {
+        const int b = __ffsll((unsigned long long)bits) - 1;
+        bits &= bits - 1;
+        G.par[(int64_t)b * G.n + local] = p;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void write_levels(const MsGraph &G, int64_t local, T bits, int32_t l)
+{
+    while (bits) {
+        const int b = __ffsll((unsigned long long)bits) - 1;
+        bits &= bits - 1;
+        G.lev[(int64_t)b * G.n + local] = l;
+    }
+}
+
+// Warp-collective append of `gid` (lanes with `on`) to the next active list.
+template <typename T>
+__device__ __forceinline__ void ms_append(bool on, int64_t gid, int64_t deg, const MsArgs<T> &a,
+                                          MsCtl *nxt, int32_t *act_next, int64_t bnext_base)
+{
+    const unsigned bal = __ballot_sync(kFull, on);
+    if (!bal) return;
+    const int leader = __ffs(bal) - 1;
+    unsigned long long base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(&nxt->na, (unsigned long long)__popc(bal));
+    base = __shfl_sync(kFull, base, leader);
+    const unsigned long long dsum = warp_sum((unsigned long long)(on ? deg : 0));
+    if (on) {
+        __stcg(&act_next[base + __popc(bal & lanemask_lt())], (int32_t)gid);
+        if (deg > MS_BIG_DEG) {
+            const unsigned long long p = atomicAdd(
+                &nxt->big, (1ull << 32) | (unsigned long long)((deg + MS_BIG_CHUNK - 1) / MS_BIG_CHUNK));
+            __stcg(&a.bigq[bnext_base + (int64_t)(p >> 32)],
+                   (unsigned long long)(uint32_t)gid | ((p & 0xffffffffull) << 32));
+        }
+    }
+    if ((int)lane_id() == leader) atomicAdd(&nxt->mf, dsum);
+}
+
+// Top-down expansion of one edge (gv -> gu) carrying frontier bits f.
+template <typename T>
+__device__ __forceinline__ void ms_td_edge(bool valid, T f, int64_t gu, const MsArgs<T> &a, T *Mn,
+                                           const MsGraph *s_g, const int64_t *s_voff, MsCtl *nxt,
+                                           int32_t *act_next, int64_t bnext_base)
+{
+    bool first = false;
+    int64_t deg = 0;
+    if (valid) {
+        const T m = f & (T)~ld_mask(&a.seen[gu]);
+        if (m) {
+            const T old = atomic_or_mask(&Mn[gu], m);
+            if (old == 0) {
+                first = true;
+                const int g = find_graph(s_voff, a.ng, gu);
+                const int64_t lu = gu - s_g[g].voff;
+                deg = s_g[g].off[lu + 1] - s_g[g].off[lu];
+            }
+        }
+    }
+    ms_append(first, gu, deg, a, nxt, act_next, bnext_base);
+}
+
+// Scan the adjacency list of global vertex gu (graph g, local lu) for the
+// bits `need`, crediting each bit to its first neighbour in M.  Serial for one
+// lane.  Returns the bits found; writes parents.
+template <typename T>
+__device__ __forceinline__ T scan_serial(const MsGraph &G, int64_t lu, T need, const T *M,
+                                         unsigned long long &edges)
+{
+    T found = 0;
+    const int64_t s = G.off[lu], e = G.off[lu + 1];
+    int64_t j = s;
+    for (; j < e; ++j) {
+        const int32_t v = G.col[j];
+        const T hit = ld_mask(&M[G.voff + v]) & need & (T)~found;
+        if (hit) {
+            write_parents(G, lu, hit, v);
+            found |= hit;
+            if (found == need) {
+                ++j;
+                break;
+            }
+        }
+    }
+    edges += (unsigned long long)(j - s);
+    return found;
+}
+
+// The same scan with the whole warp on one row (all lanes call it with the
+// same arguments).  Returns the bits found (same in all lanes).
+template <typename T>
+__device__ __forceinline__ T scan_warp(const MsGraph &G, int64_t lu, T need, const T *M,
+                                       unsigned long long &edges)
+{
+    const unsigned lane = lane_id();
+    T found = 0;
+    const int64_t s = G.off[lu], e = G.off[lu + 1];
+    for (int64_t b = s; b < e; b += 32) {
+        const int64_t j = b + lane;
+        int32_t v = 0;
+        T hit = 0;
+        if (j < e) {
+            v = G.col[j];
+            hit = ld_mask(&M[G.voff + v]) & need & (T)~found;
+        }
+        const T before = warp_exclusive_or(hit);
+        const T mine = hit & (T)~before;
+        if (mine) write_parents(G, lu, mine, v);
+        found |= warp_or(hit);
+        if (lane == 0) edges += (unsigned long long)(e - b < 32 ? e - b : 32);
+        if (found == need) break;
+    }
+    return found;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
+{
+    __shared__ MsGraph s_g[MS_MAXG];
+    __shared__ int64_t s_voff[MS_MAXG + 1];
+    for (int i = threadIdx.x; i < a.ng; i += blockDim.x) s_g[i] = a.graphs[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i <= a.ng; i += blockDim.x)
+        s_voff[i] = i < a.ng ? s_g[i].voff : s_g[a.ng - 1].voff + s_g[a.ng - 1].n;
+    __syncthreads();
+
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+    const unsigned lane = lane_id();
+    const int64_t gwarp = gtid >> 5;
+    const int64_t nwarps = gthreads >> 5;
+    const int64_t ntot = a.ntot;
+    const T all = a.k >= (int)(8 * sizeof(T)) ? (T)~(T)0 : (T)(((T)1 << a.k) - 1);
+    MsHeader *h = a.hdr;
+
+    // ---- init: outputs -1, masks clear
+    for (int g = 0; g < a.ng; ++g) {
+        const MsGraph G = s_g[g];
+        const int64_t cnt = (int64_t)a.k * G.n;
+        for (int64_t i = gtid; i < cnt; i += gthreads) {
+            G.par[i] = -1;
+            G.lev[i] = -1;
+        }
+    }
+    for (int64_t i = gtid; i < a.mstride; i += gthreads) {
+        a.seen[i] = 0;
+        a.mbuf[i] = 0;
+        a.mbuf[a.mstride + i] = 0;
+        a.mbuf[2 * a.mstride + i] = 0;
+    }
+    if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+    // roots: bit b of graph g at its root; roots that coincide share one entry
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long na = 0, mf = 0;
+        for (int g = 0; g < a.ng; ++g) {
+            const MsGraph G = s_g[g];
+            for (int b = 0; b < a.k; ++b) {
+                const int64_t r = a.roots[(int64_t)g * a.k + b];
+                const int64_t gid = G.voff + r;
+                if (a.mbuf[gid] == 0) {
+                    a.act[na++] = (int32_t)gid;
+                    const int64_t deg = G.off[r + 1] - G.off[r];
+                    mf += deg;
+                    if (deg > MS_BIG_DEG) {
+                        const unsigned long long p = h->ctl[0].big;
+                        a.bigq[p >> 32] = (unsigned long long)(uint32_t)gid | ((p & 0xffffffffull) << 32);
+                        h->ctl[0].big = p + ((1ull << 32) | (unsigned long long)((deg + MS_BIG_CHUNK - 1) / MS_BIG_CHUNK));
+                    }
+                }
+                a.mbuf[gid] |= (T)((T)1 << b);
+                a.seen[gid] |= (T)((T)1 << b);
+                G.par[(int64_t)b * G.n + r] = (int32_t)r;
+                G.lev[(int64_t)b * G.n + r] = 0;
+            }
+        }
+        h->ctl[0].na = na;
+        h->ctl[0].mf = mf;
+        h->acc[2] = (unsigned long long)a.ng * (unsigned long long)a.k;  // the roots themselves
+    }
+    if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+
+    int64_t prev_na = 0;
+    unsigned long long my_edges = 0, my_touched = 0, reached_new = 0;
+    int l = 0;
+    for (;; ++l) {
+        MsCtl *cur = &h->ctl[l % 3];
+        const int64_t na = (int64_t)ldcg_u64(&cur->na);
+        if (na == 0) break;
+        if (l > ntot) {
+            if (gtid == 0) record_error(a.st, GB_ERR_TIMEOUT, SITE_MS_LEVELS, l);
+            break;
+        }
+        const double mf = (double)ldcg_u64(&cur->mf);
+        const unsigned long long bigp = ldcg_u64(&cur->big);
+        const int64_t nb = (int64_t)(bigp >> 32), nc = (int64_t)(bigp & 0xffffffffull);
+        const bool td = mf * a.ms_alpha < (double)a.nnz_tot && (double)na * a.ms_beta < (double)ntot;
+        T *M = a.mbuf + (size_t)(l % 3) * a.mstride;
+        T *Mn = a.mbuf + (size_t)((l + 1) % 3) * a.mstride;
+        T *Mz = a.mbuf + (size_t)((l + 2) % 3) * a.mstride;
+        const int32_t *act = a.act + (size_t)(l % 3) * ntot;
+        int32_t *act_next = a.act + (size_t)((l + 1) % 3) * ntot;
+        const int32_t *act_prev = a.act + (size_t)((l + 2) % 3) * ntot;
+        MsCtl *nxt = &h->ctl[(l + 1) % 3];
+        // big-vertex chunk lists alternate between two halves of bigq
+        const int64_t bbase = (l & 1) ? a.bigcap : 0;
+        const int64_t bnext_base = (l & 1) ? 0 : a.bigcap;
+
+        // Clear the level l-1 frontier (its buffer receives level l+2) and the
+        // control record level l+1 will fill; nobody reads either during level l.
+        for (int64_t i = gtid; i < prev_na; i += gthreads) Mz[ldcg_i32(&act_prev[i])] = 0;
+        if (gtid == 0) {
+            MsCtl z = {0, 0, 0, 0};
+            h->ctl[(l + 2) % 3] = z;
+        }
+
+        if (td) {
+            // (1a) big active vertices in 256-edge chunks
+            if (nc > 0) {
+                const int64_t per = (nc + nwarps - 1) / nwarps;
+                const int64_t c0 = gwarp * per;
+                const int64_t c1 = c0 + per < nc ? c0 + per : nc;
+                if (c0 < c1) {
+                    int64_t lo = 0, hi = nb;
+                    while (hi - lo > 1) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        if ((int64_t)(__ldcg(&a.bigq[bbase + mid]) >> 32) <= c0) lo = mid;
+                        else hi = mid;
+                    }
+                    int64_t ow = lo;
+                    unsigned long long be = __ldcg(&a.bigq[bbase + ow]);
+                    for (int64_t c = c0; c < c1; ++c) {
+                        while (ow + 1 < nb && (int64_t)(__ldcg(&a.bigq[bbase + ow + 1]) >> 32) <= c) {
+                            ++ow;
+                            be = __ldcg(&a.bigq[bbase + ow]);
+                        }
+                        const int64_t gv = (int64_t)(uint32_t)(be & 0xffffffffull);
+                        const int g = find_graph(s_voff, a.ng, gv);
+                        const MsGraph &G = s_g[g];
+                        const int64_t lv = gv - G.voff;
+                        const T f = ld_mask(&M[gv]);
+                        const int64_t s = G.off[lv] + (c - (int64_t)(be >> 32)) * MS_BIG_CHUNK;
+                        const int64_t eu = G.off[lv + 1];
+                        const int64_t e = s + MS_BIG_CHUNK < eu ? s + MS_BIG_CHUNK : eu;
+                        if (lane == 0) my_edges += (unsigned long long)(e - s);
+                        for (int64_t b = s; b < e; b += 32) {
+                            const int64_t j = b + lane;
+                            const bool valid = j < e;
+                            const int64_t gu = valid ? G.voff + G.col[j] : 0;
+                            ms_td_edge(valid, f, gu, a, Mn, s_g, s_voff, nxt, act_next, bnext_base);
+                        }
+                    }
+                }
+            }
+            // (1b) other active vertices, 32 per warp, adjacency gathered as one stream
+            for (int64_t i0 = gwarp * 32; i0 < na; i0 += nwarps * 32) {
+                const int64_t i = i0 + lane;
+                int64_t gv = 0, s = 0, d = 0, vo = 0;
+                int g = 0;
+                T f = 0;
+                if (i < na) {
+                    gv = ldcg_i32(&act[i]);
+                    g = find_graph(s_voff, a.ng, gv);
+                    vo = s_g[g].voff;
+                    s = s_g[g].off[gv - vo];
+                    d = s_g[g].off[gv - vo + 1] - s;
+                    if (d > MS_BIG_DEG) d = 0;
+                    f = ld_mask(&M[gv]);
+                }
+                my_touched += (i < na);
+                my_edges += d;
+                const int64_t incl = warp_inclusive_scan(d);
+                const int64_t total = __shfl_sync(kFull, incl, 31);
+                const int64_t excl = incl - d;
+                for (int64_t b = 0; b < total; b += 32) {
+                    const int64_t kk = b + lane;
+                    int owner = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int cand = owner + step;
+                        if (__shfl_sync(kFull, excl, cand) <= kk) owner = cand;
+                    }
+                    const int og = __shfl_sync(kFull, g, owner);
+                    const int64_t so = __shfl_sync(kFull, s, owner);
+                    const int64_t eo = __shfl_sync(kFull, excl, owner);
+                    const int64_t vvo = __shfl_sync(kFull, vo, owner);
+                    const T fo = shfl_mask(f, owner);
+                    const bool valid = kk < total;
+                    const int64_t gu = valid ? vvo + s_g[og].col[so + (kk - eo)] : 0;
+                    ms_td_edge(valid, fo, gu, a, Mn, s_g, s_voff, nxt, act_next, bnext_base);
+                }
+            }
+            if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+            // (2) parents and levels of the vertices that gained bits
+            const int64_t nn = (int64_t)ldcg_u64(&nxt->na);
+            for (int64_t i0 = gwarp * 32; i0 < nn; i0 += nwarps * 32) {
+                const int64_t i = i0 + lane;
+                int64_t gu = 0, lu = 0, deg = 0;
+                int g = 0;
+                T nw = 0;
+                if (i < nn) {
+                    gu = ldcg_i32(&act_next[i]);
+                    g = find_graph(s_voff, a.ng, gu);
+                    lu = gu - s_g[g].voff;
+                    nw = ld_mask(&Mn[gu]);
+                    deg = s_g[g].off[lu + 1] - s_g[g].off[lu];
+                    if (deg <= 32) scan_serial(s_g[g], lu, nw, M, my_edges);
+                    write_levels(s_g[g], lu, nw, l + 1);
+                    st_mask(&a.seen[gu], (T)(ld_mask(&a.seen[gu]) | nw));
+                    reached_new += __popcll((unsigned long long)nw);
+                }
+                unsigned bigm = __ballot_sync(kFull, i < nn && deg > 32);
+                while (bigm) {
+                    const int jl = __ffs(bigm) - 1;
+                    bigm &= bigm - 1;
+                    const int gj = __shfl_sync(kFull, g, jl);
+                    const int64_t luj = __shfl_sync(kFull, lu, jl);
+                    const T nwj = shfl_mask(nw, jl);
+                    scan_warp(s_g[gj], luj, nwj, M, my_edges);
+                }
+            }
+        } else {
+            // bottom-up over all vertices with unseen bits, 32 consecutive ids per warp
+            for (int64_t b0 = gwarp * 32; b0 < ntot; b0 += nwarps * 32) {
+                const int64_t gu = b0 + lane;
+                T need = 0;
+                int g = 0;
+                int64_t lu = 0, deg = 0;
+                T sn = 0;
+                if (gu < ntot) {
+                    sn = ld_mask(&a.seen[gu]);
+                    need = all & (T)~sn;
+                    if (need) {
+                        g = find_graph(s_voff, a.ng, gu);
+                        lu = gu - s_g[g].voff;
+                        deg = s_g[g].off[lu + 1] - s_g[g].off[lu];
+                        if (deg == 0) need = 0;
+                    }
+                }
+                T found = 0;
+                if (need && deg <= 32) found = scan_serial(s_g[g], lu, need, M, my_edges);
+                my_touched += (need != 0);
+                unsigned bigm = __ballot_sync(kFull, need && deg > 32);
+                while (bigm) {
+                    const int jl = __ffs(bigm) - 1;
+                    bigm &= bigm - 1;
+                    const int gj = __shfl_sync(kFull, g, jl);
+                    const int64_t luj = __shfl_sync(kFull, lu, jl);
+                    const T nj = shfl_mask(need, jl);
+                    const T fj = scan_warp(s_g[gj], luj, nj, M, my_edges);
+                    if ((int)lane == jl) found = fj;
+                }
+                if (found) {
+                    write_levels(s_g[g], lu, found, l + 1);
+                    st_mask(&a.seen[gu], (T)(sn | found));
+                    st_mask(&Mn[gu], found);
+                    reached_new += __popcll((unsigned long long)found);
+                }
+                ms_append(found != 0, gu, deg, a, nxt, act_next, bnext_base);
+            }
+        }
+        prev_na = na;
+        if (gtid == 0) atomicAdd(&h->acc[td ? 4 : 5], 1ull);
+        if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+    }
+
+    my_edges = warp_sum(my_edges);
+    my_touched = warp_sum(my_touched);
+    reached_new = warp_sum(reached_new);
+    if (lane == 0) {
+        if (my_edges) atomicAdd(&h->acc[0], my_edges);
+        if (my_touched) atomicAdd(&h->acc[1], my_touched);
+        if (reached_new) atomicAdd(&h->acc[2], reached_new);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&h->done, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            BfsDevStats s;
+            s.nlevels = (unsigned long long)l;
+            s.edges_examined = ldcg_u64(&h->acc[0]);
+            s.vertices_touched = ldcg_u64(&h->acc[1]);
+            s.reached = ldcg_u64(&h->acc[2]);
+            s.td_levels = ldcg_u64(&h->acc[4]);
+            s.bu_levels = ldcg_u64(&h->acc[5]);
+            *a.stats = s;
+        }
+    }
+}
+
+template <typename T>
+gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &roots,
+                    int64_t nnz_tot, BfsDevStats *stats, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    const gb_bfs_options &o = options();
+    const int ng = (int)gs.size();
+    int64_t ntot = 0;
+    for (int i = 0; i < ng; ++i) {
+        gs[i].voff = ntot;
+        ntot += gs[i].n;
+    }
+    if (ntot >= (int64_t(1) << 31)) {
+        set_error("multi-source BFS: more than 2^31 vertices in total");
+        return GB_ERR_RANGE;
+    }
+    // Byte masks are updated with 32-bit atomics, so every mask array is padded.
+    const int64_t np = (ntot + 63) & ~int64_t(63);
+    const int64_t bigcap = nnz_tot / (MS_BIG_DEG + 1) + ng * k + 2;
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t o_g = up(sizeof(MsHeader));
+    const size_t o_r = o_g + up(ng * sizeof(MsGraph));
+    const size_t o_seen = o_r + up((size_t)ng * k * sizeof(int64_t));
+    const size_t o_m = o_seen + up(np * sizeof(T));
+    const size_t o_act = o_m + up(3 * np * sizeof(T));
+    const size_t o_big = o_act + up(3 * (size_t)ntot * sizeof(int32_t));
+    const size_t total = o_big + 2 * bigcap * sizeof(unsigned long long);
+    unsigned char *ws = nullptr;
+    GB_CUDA(cudaMallocAsync((void **)&ws, total, s));
+    GB_CUDA(cudaMemsetAsync(ws, 0, sizeof(MsHeader), s));
+    GB_CUDA(cudaMemcpyAsync(ws + o_g, gs.data(), ng * sizeof(MsGraph), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(ws + o_r, roots.data(), (size_t)ng * k * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s));
+    MsArgs<T> a;
+    a.graphs = reinterpret_cast<const MsGraph *>(ws + o_g);
+    a.ng = ng;
+    a.k = k;
+    a.ntot = ntot;
+    a.mstride = np;
+    a.nnz_tot = nnz_tot;
+    a.roots = reinterpret_cast<const int64_t *>(ws + o_r);
+    a.seen = reinterpret_cast<T *>(ws + o_seen);
+    a.mbuf = reinterpret_cast<T *>(ws + o_m);
+    a.act = reinterpret_cast<int32_t *>(ws + o_act);
+    a.bigq = reinterpret_cast<unsigned long long *>(ws + o_big);
+    a.bigcap = bigcap;
+    a.hdr = reinterpret_cast<MsHeader *>(ws);
+    a.st = ctx->status;
+    a.stats = stats;
+    a.ms_alpha = (float)o.ms_alpha;
+    a.ms_beta = (float)o.ms_beta;
+    a.timeout_ns = timeout_ns();
+    void *args[] = {&a};
+    GB_CUDA(cudaLaunchCooperativeKernel((const void *)ms_kernel<T>, dim3(ctx->ms_blocks),
+                                        dim3(MS_THREADS), args, 0, s));
+    GB_CUDA(cudaFreeAsync(ws, s));
+    return GB_OK;
+}
+
+}  // namespace
+
+gb_status msbfs_impl(const gb_graph *g, const int64_t *roots, int k, int32_t *parents,
+                     int32_t *levels, BfsDevStats *stats, cudaStream_t s)
+{
+    MsGraph G;
+    G.off = g->off;
+    G.col = g->col;
+    G.voff = 0;
+    G.n = g->n;
+    G.par = parents;
+    G.lev = levels;
+    std::vector<int64_t> r(roots, roots + k);
+    return ms_launch<unsigned long long>({G}, k, r, g->nnz, stats, s);
+}
+
+gb_status multigraph_impl(const gb_graph *const *gs, int ng, const int64_t *roots, int r,
+                          int32_t *const *parents, int32_t *const *levels, BfsDevStats *stats,
+                          cudaStream_t s)
+{
+    std::vector<MsGraph> v(ng);
+    int64_t nnz = 0;
+    for (int i = 0; i < ng; ++i) {
+        v[i].off = gs[i]->off;
+        v[i].col = gs[i]->col;
+        v[i].voff = 0;
+        v[i].n = gs[i]->n;
+        v[i].par = parents[i];
+        v[i].lev = levels[i];
+        nnz += gs[i]->nnz;
+    }
+    std::vector<int64_t> rr(roots, roots + (size_t)ng * r);
+    return ms_launch<unsigned char>(v, r, rr, nnz, stats, s);
+}
+
+int msbfs_pick_blocks(int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_kernel<unsigned long long>,
+                                                      MS_THREADS, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int per_sm8 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, ms_kernel<unsigned char>,
+                                                      MS_THREADS, 0) != cudaSuccess ||
+        per_sm8 < 1)
+        per_sm8 = 1;
+    return num_sms * std::min(std::min(per_sm, per_sm8), 2);
+}
+
+}  // namespace gb

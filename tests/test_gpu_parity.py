@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA path against the oracle, element by element.
+
+Integer results, so the bar is bit-exactness: edge lists, CSR offsets and
+columns, level arrays, and parents in canonical mode (the smallest-id
+neighbour one level up, which is unique).  In fast mode any valid parent is
+allowed, so parents are checked with the Graph500 validator instead.
+Every call goes through the C ABI (paper_2012_13548_gb300.binding).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2012_13548_gb300 as gb  # noqa: E402
+from paper_2012_13548_gb300 import workloads as W  # noqa: E402
+from tests.conftest import oracle_bfs, oracle_graph, roots_for  # noqa: E402
+from tests.golden import load_hand_graphs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEFAULTS = dict(canonical_parents=0, alpha=14.0, beta=24.0, big_degree=256, ms_alpha=16.0,
+                ms_beta=32.0, timeout_ms=5000.0)
+
+
+@pytest.fixture(autouse=True)
+def _reset_options():
+    gb.bfs_set_options(**DEFAULTS)
+    yield
+    gb.bfs_set_options(**DEFAULTS)
+    gb.gb_device_status()   # no kernel may have recorded an error
+
+
+def np_(t):
+    return t.cpu().numpy()
+
+
+_graphs = {}
+
+
+def gpu_graph(scale, index=-1):
+    key = (scale, index)
+    if key not in _graphs:
+        spec = W.GraphSpec(scale=scale, index=index)
+        e = gb.kron_generate(**spec.kron_args())
+        _graphs[key] = (e, gb.graph_build_csr(e, scale))
+    return _graphs[key]
+
+
+# ---------------------------------------------------------------------------
+# Generator (Sec. 2.1) and kernel 1 (Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scale", list(range(1, 13)) + [16, 20])
+def test_generator_bit_exact(scale):
+    e_ref, _, _ = oracle_graph(scale)
+    e, _ = gpu_graph(scale)
+    assert np.array_equal(np_(e), e_ref)
+
+
+@pytest.mark.parametrize("scale", list(range(1, 13)) + [16, 20])
+def test_csr_bit_exact(scale):
+    _, off_ref, col_ref = oracle_graph(scale)
+    _, g = gpu_graph(scale)
+    off, col = g.csr()
+    assert g.n == off_ref.size - 1 and g.nnz == col_ref.size
+    assert np.array_equal(np_(off), off_ref)
+    assert np.array_equal(np_(col), col_ref)
+
+
+def test_generator_other_initiators_and_edgefactors():
+    for (a, b, c, ef, scale) in [(0.25, 0.25, 0.25, 1, 9), (0.45, 0.15, 0.15, 3, 11),
+                                 (1.0, 0.0, 0.0, 2, 5), (0.0, 0.0, 0.0, 2, 5)]:
+        e = gb.kron_generate(scale, ef, a, b, c, 11, 12, 13)
+        ref = oracle.kron_generate(scale, ef, a, b, c, 11, 12, 13)
+        assert np.array_equal(np_(e), ref), (a, b, c, ef, scale)
+
+
+def test_csr_of_hand_fixtures_and_random_lists():
+    for g in load_hand_graphs():
+        if "off" not in g:
+            continue
+        scale = max(1, (g["n"] - 1).bit_length())
+        e = torch.as_tensor(g["edges"]).cuda()
+        G = gb.graph_build_csr(e, scale)
+        off, col = G.csr()
+        assert np.array_equal(np_(off)[: g["n"] + 1], g["off"])
+        assert np.array_equal(np_(col), g["col"])
+    rng = np.random.default_rng(3)
+    for scale in [1, 2, 3, 5, 8, 11]:
+        n = 1 << scale
+        for m in [0, 1, 7, 4097, 3 * n]:
+            e = rng.integers(0, n, size=(2, m)).astype(np.int64)
+            off_ref, col_ref = oracle.csr_build(e, scale)
+            G = gb.graph_build_csr(torch.as_tensor(e).cuda(), scale)
+            off, col = G.csr()
+            assert np.array_equal(np_(off), off_ref), (scale, m)
+            assert np.array_equal(np_(col), col_ref), (scale, m)
+
+
+def test_csr_rejects_out_of_range_endpoints():
+    e = torch.tensor([[0, 1, 2], [1, 2, 9]], dtype=torch.int64, device="cuda")
+    with pytest.raises(gb.GbError, match="RANGE"):
+        gb.graph_build_csr(e, 3)
+    e = torch.tensor([[0, -1], [1, 2]], dtype=torch.int64, device="cuda")
+    with pytest.raises(gb.GbError, match="RANGE"):
+        gb.graph_build_csr(e, 3)
+
+
+# ---------------------------------------------------------------------------
+# Kernel 2 (Sec. 2.3): single-source BFS
+# ---------------------------------------------------------------------------
+
+def check_bfs(G, off_ref, col_ref, root, canonical):
+    parent, level = gb.bfs(G, root)
+    p_ref, l_ref = oracle.bfs(off_ref, col_ref, root)
+    lev = np_(level)
+    par = np_(parent)
+    assert np.array_equal(lev, l_ref), "levels differ (root %d)" % root
+    if canonical:
+        assert np.array_equal(par, p_ref), "canonical parents differ (root %d)" % root
+    else:
+        assert oracle.validate(off_ref, col_ref, root, par, lev) == 0, "invalid tree (root %d)" % root
+
+
+@pytest.mark.parametrize("canonical", [0, 1])
+def test_bfs_hand_fixtures(canonical):
+    gb.bfs_set_options(canonical_parents=canonical)
+    for g in load_hand_graphs():
+        off_ref, col_ref = oracle.csr_build(g["edges"], max(1, (g["n"] - 1).bit_length()))
+        off_ref = off_ref[: g["n"] + 1]
+        G = gb.graph_from_csr(torch.as_tensor(off_ref).cuda(), torch.as_tensor(col_ref).cuda())
+        parent, level = gb.bfs(G, g["root"])
+        assert np.array_equal(np_(level), g["levels"]), g["name"]
+        if canonical:
+            assert np.array_equal(np_(parent), g["parents"]), g["name"]
+        else:
+            assert oracle.validate(off_ref, col_ref, g["root"], np_(parent), np_(level)) == 0
+
+
+def _random_graph(rng, n, m):
+    e = rng.integers(0, n, size=(2, m)).astype(np.int64)
+    scale = max(1, (n - 1).bit_length())
+    off, col = oracle.csr_build(e, scale)
+    return off[: n + 1].copy(), col
+
+
+@pytest.mark.parametrize("canonical", [0, 1])
+def test_bfs_random_small_graphs_all_roots(canonical):
+    gb.bfs_set_options(canonical_parents=canonical)
+    rng = np.random.default_rng(5)
+    for trial in range(12):
+        n = int(rng.integers(1, 200))
+        off, col = _random_graph(rng, n, int(rng.integers(0, 3 * n)))
+        G = gb.graph_from_csr(torch.as_tensor(off).cuda(), torch.as_tensor(col).cuda())
+        for root in range(n):
+            check_bfs(G, off, col, root, canonical)
+
+
+SWITCHES = {
+    "default": {},
+    "top_down_only": dict(alpha=1e-9),
+    "bottom_up_early": dict(alpha=1e9, beta=1e9),
+    "flip_flop": dict(alpha=1e9, beta=1e-9),
+    "tiny_big_degree": dict(big_degree=1),
+}
+
+
+@pytest.mark.parametrize("mode", list(SWITCHES))
+@pytest.mark.parametrize("canonical", [0, 1])
+@pytest.mark.parametrize("scale", [4, 8, 10, 12])
+def test_bfs_kronecker_direction_modes(scale, canonical, mode):
+    gb.bfs_set_options(canonical_parents=canonical, **SWITCHES[mode])
+    _, off_ref, col_ref = oracle_graph(scale)
+    _, G = gpu_graph(scale)
+    roots = roots_for(scale, 8)
+    if scale <= 8:
+        roots = list(range(1 << scale))       # every vertex, isolated ones included
+    for r in roots:
+        check_bfs(G, off_ref, col_ref, r, canonical)
+
+
+@pytest.mark.parametrize("scale,k", [(16, 16), (20, 64)])
+@pytest.mark.parametrize("canonical", [0, 1])
+def test_bfs_large_scales(scale, k, canonical):
+    gb.bfs_set_options(canonical_parents=canonical)
+    _, off_ref, col_ref = oracle_graph(scale)
+    _, G = gpu_graph(scale)
+    for r in roots_for(scale, k):
+        parent, level = gb.bfs(G, r)
+        p_ref, l_ref = oracle_bfs(scale, r)
+        assert np.array_equal(np_(level), l_ref), r
+        if canonical:
+            assert np.array_equal(np_(parent), p_ref), r
+        else:
+            assert oracle.validate(off_ref, col_ref, r, np_(parent), np_(level)) == 0, r
+
+
+def test_bfs_isolated_root_and_bad_root():
+    _, off_ref, col_ref = oracle_graph(10)
+    _, G = gpu_graph(10)
+    iso = int(np.nonzero(np.diff(off_ref) == 0)[0][0])
+    parent, level = gb.bfs(G, iso)
+    lev = np_(level)
+    assert lev[iso] == 0 and (np.delete(lev, iso) == -1).all()
+    assert np_(parent)[iso] == iso
+    with pytest.raises(gb.GbError, match="RANGE"):
+        gb.bfs(G, G.n)
+    with pytest.raises(gb.GbError, match="RANGE"):
+        gb.bfs(G, -1)
+
+
+def test_bfs_stats_count_the_search():
+    _, G = gpu_graph(12)
+    r = roots_for(12, 1)[0]
+    _, level = gb.bfs(G, r)
+    st = gb.bfs_last_stats()
+    lev = np_(level)
+    assert st["nlevels"] == lev.max() + 1
+    assert st["reached"] == int((lev >= 0).sum())
+    assert st["td_levels"] + st["bu_levels"] == st["nlevels"]
+    assert 0 < st["edges_examined"] <= 2 * G.nnz
+
+
+# ---------------------------------------------------------------------------
+# Batched kernel 2: multi-source BFS and a batch of graphs
+# ---------------------------------------------------------------------------
+
+MS_SWITCHES = {"default": {}, "top_down": dict(ms_alpha=1e-9, ms_beta=1e-9),
+               "bottom_up": dict(ms_alpha=1e9, ms_beta=1e9)}
+
+
+@pytest.mark.parametrize("mode", list(MS_SWITCHES))
+@pytest.mark.parametrize("scale,k", [(6, 64), (10, 1), (10, 7), (12, 64), (16, 64)])
+def test_msbfs_rows_equal_single_source(scale, k, mode):
+    gb.bfs_set_options(**MS_SWITCHES[mode])
+    _, off_ref, col_ref = oracle_graph(scale)
+    _, G = gpu_graph(scale)
+    roots = roots_for(scale, k)
+    if scale == 6:
+        roots = [int(x) for x in np.arange(64) % (1 << scale)]   # isolated roots included
+    P, L = gb.bfs_batch(G, roots)
+    for i, r in enumerate(roots):
+        p_ref, l_ref = oracle_bfs(scale, r)
+        assert np.array_equal(np_(L[i]), l_ref), (i, r)
+        assert np.array_equal(np_(P[i]), p_ref), (i, r)
+
+
+def test_msbfs_repeated_roots_and_random_graphs():
+    rng = np.random.default_rng(9)
+    for trial in range(6):
+        n = int(rng.integers(2, 300))
+        off, col = _random_graph(rng, n, int(rng.integers(0, 3 * n)))
+        G = gb.graph_from_csr(torch.as_tensor(off).cuda(), torch.as_tensor(col).cuda())
+        k = int(rng.integers(1, 65))
+        roots = [int(x) for x in rng.integers(0, n, size=k)]
+        P, L = gb.bfs_batch(G, roots)
+        for i, r in enumerate(roots):
+            p_ref, l_ref = oracle.bfs(off, col, r)
+            assert np.array_equal(np_(L[i]), l_ref)
+            assert np.array_equal(np_(P[i]), p_ref)
+
+
+@pytest.mark.parametrize("lo,hi,count", [(4, 9, 32), (12, 18, 32)])
+def test_multi_graph_batch_equals_standalone(lo, hi, count):
+    specs = W.batch_specs(count, lo, hi)
+    graphs, roots = [], []
+    for sp in specs:
+        _, off_ref, _ = oracle_graph(sp.scale, sp.index)
+        _, G = gpu_graph(sp.scale, sp.index)
+        graphs.append(G)
+        rs = roots_for(sp.scale, 8, sp.index)
+        rs = (rs * 8)[:8]
+        roots.append(rs)
+    P, L = gb.bfs_multi_graph(graphs, roots)
+    for gi, sp in enumerate(specs):
+        for b, r in enumerate(roots[gi]):
+            p_ref, l_ref = oracle_bfs(sp.scale, r, sp.index)
+            assert np.array_equal(np_(L[gi][b]), l_ref), (gi, b)
+            assert np.array_equal(np_(P[gi][b]), p_ref), (gi, b)
