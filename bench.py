@@ -1,0 +1,463 @@
+#!/usr/bin/env python3
+"""Graph500 BFS benchmark on GB300 (kernel 1 + kernel 2 of arXiv 2012.13548, Sec. 2).
+
+Default workload (SCALE 20, edgefactor 16, 64 roots): one step is
+  kernel 1 (CSR build from the device-resident Kronecker edge list),
+  64 single-source direction-optimising BFS runs (one per root, each timed),
+  one 64-root multi-source BFS of the same roots ("batched").
+`value` is the Graph500 figure: the harmonic mean over the timed roots of
+m_r / t_r, m_r = input tuples whose start vertex the search reached (Sec. 4.3),
+t_r = the bfs() call timed with CUDA events on its stream.  L2 is flushed (a
+256 MB write) before every timed call.
+
+Other workloads (--workload): s26 (SCALE 26), s22ms (SCALE 22, plain vs one
+64-root launch), batch32 (32 graphs of SCALE 12..18, 8 roots each),
+serve6 (serving loop, p50/p99 latency).
+
+`--impl reference` times the CPU oracle (serial C) on a bounded sample of the
+same workload and prints the same JSON line with "impl": "reference".
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2012_13548_gb300 import workloads as W  # noqa: E402
+
+METRIC = "BFS GTEPS (harm. mean, 64 roots) plain vs batched; % HBM peak; p50/p99 ms"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="s20", choices=["s20", "s26", "s22ms"])
+    p.add_argument("--roots", type=int, default=64)
+    p.add_argument("--canonical", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def harmonic_mean(x):
+    x = [v for v in x]
+    return len(x) / sum(1.0 / v for v in x)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas, no data-path collective)
+# ---------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self, want):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if want == "cuda" else "gloo"
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def gather(self, xs):
+        """Concatenate per-rank float lists on every rank."""
+        if not self.pg:
+            return list(xs)
+        out = [None] * self.world
+        self.pg.all_gather_object(out, list(xs))
+        return [v for part in out for v in part]
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def shard_roots(all_roots, rank, world, per_rank):
+    """Root list of one rank: ranks take disjoint consecutive blocks."""
+    return list(all_roots[rank * per_rank:(rank + 1) * per_rank])
+
+
+# ---------------------------------------------------------------------------
+# clocks under load
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, f in rows for i, v in enumerate(f)
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(scale, nroots, seconds):
+    """Time the serial oracle BFS over the workload's roots until `seconds` of
+    BFS work; returns (harmonic-mean GTEPS, roots timed, seconds spent)."""
+    import oracle
+    spec = W.GraphSpec(scale=scale)
+    e = oracle.kron_generate(**spec.kron_args())
+    off, col = oracle.csr_build(e, scale)
+    roots = W.select_roots(off, nroots, spec.seeds()[3])
+    rates, spent, done = [], 0.0, 0
+    for r in roots:
+        t0 = time.perf_counter()
+        _, lev = oracle.bfs(off, col, int(r))
+        dt = time.perf_counter() - t0
+        rates.append(oracle.teps_edges(e, lev) / dt / 1e9)
+        spent += dt
+        done += 1
+        if spent >= seconds:
+            break
+    return harmonic_mean(rates), done, spent, (off, col, e)
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    wl = W.WORKLOADS[args.workload]
+    scale = wl["scale"]
+    import oracle
+    spec = W.GraphSpec(scale=scale)
+    e = oracle.kron_generate(**spec.kron_args())
+    off, col = oracle.csr_build(e, scale)
+    roots = W.select_roots(off, args.roots, spec.seeds()[3])
+    per_step = max(1, min(len(roots), 4))
+    rates, step_times = [], []
+    i = 0
+    for s in range(args.warmup + args.steps):
+        t_step = 0.0
+        for _ in range(per_step):
+            r = int(roots[i % len(roots)])
+            i += 1
+            t0 = time.perf_counter()
+            _, lev = oracle.bfs(off, col, r)
+            dt = time.perf_counter() - t0
+            t_step += dt
+            if s >= args.warmup:
+                rates.append(oracle.teps_edges(e, lev) / dt / 1e9)
+        if s >= args.warmup:
+            step_times.append(t_step)
+    v = harmonic_mean(rates)
+    sample = ("serial C oracle queue BFS on the SCALE %d graph (oracle-built), %d roots per step, "
+              "%d timed steps" % (scale, per_step, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(step_times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": workload_config(args, scale),
+            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_config(args, scale):
+    return {"workload": "graph500-kronecker-scale%d-ef16-%droots" % (scale, args.roots),
+            "scale": scale, "edgefactor": W.EDGEFACTOR, "initiator": [W.A, W.B, W.C,
+                                                                     round(1 - W.A - W.B - W.C, 2)],
+            "roots": args.roots, "parents": "canonical" if args.canonical else "any-valid",
+            "l2": "flushed before every timed call (256 MB write)",
+            "step": "kernel1 + %d single-source BFS + one %d-root batched BFS" % (args.roots, args.roots)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def run_ours(args, dist):
+    import torch
+    import paper_2012_13548_gb300 as gb
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    stream = torch.cuda.current_stream()
+    wl = W.WORKLOADS[args.workload]
+    scale = wl["scale"]
+    spec = W.GraphSpec(scale=scale)
+    gb.bfs_set_options(canonical_parents=args.canonical)
+
+    edges = gb.kron_generate(**spec.kron_args())            # input: generated, untimed
+    g = gb.graph_build_csr(edges, scale)
+    off, _ = g.csr()
+    all_roots = W.select_roots(off.cpu().numpy(), args.roots * dist.world, spec.seeds()[3])
+    roots = shard_roots(all_roots, dist.rank, dist.world, args.roots)
+    n = g.n
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    P = torch.empty((len(roots), n), dtype=torch.int32, device=dev)
+    L = torch.empty((len(roots), n), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    # TEPS numerators and per-root counters (bookkeeping, outside the timed region)
+    m_r, stats = [], []
+    src = edges[0]
+    for r in roots:
+        gb.bfs(g, int(r), parent, level)
+        stats.append(gb.bfs_last_stats())
+        m_r.append(int((level[src] >= 0).sum().item()))
+    gb.gb_device_status()
+
+    def step(rec):
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        k0, k1 = ev(), ev()
+        flush.fill_(1)
+        k0.record(stream)
+        g2 = gb.graph_build_csr(edges, scale)
+        k1.record(stream)
+        per = []
+        for r in roots:
+            flush.fill_(2)
+            a, b = ev(), ev()
+            a.record(stream)
+            gb.bfs(g, int(r), parent, level)
+            b.record(stream)
+            per.append((a, b))
+        flush.fill_(3)
+        b0, b1 = ev(), ev()
+        b0.record(stream)
+        gb.bfs_batch(g, roots, P, L)
+        b1.record(stream)
+        rec.append((k0, k1, per, b0, b1, g2))
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    launches0 = gb.gb_kernel_launches()
+    t_all0, t_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rec = []
+    t_all0.record(stream)
+    for _ in range(args.steps):
+        step(rec)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    launches = gb.gb_kernel_launches() - launches0
+    clk = clocks.stop()
+    gb.gb_device_status()
+    total_ms = t_all0.elapsed_time(t_all1)
+    for r in rec:
+        r[5].free()
+
+    bfs_ms = [[a.elapsed_time(b) for (a, b) in r[2]] for r in rec]
+    k1_ms = [r[0].elapsed_time(r[1]) for r in rec]
+    batch_ms = [r[3].elapsed_time(r[4]) for r in rec]
+    rates = [m_r[i] / (t[i] * 1e-3) / 1e9 for t in bfs_ms for i in range(len(roots))]
+    all_rates = dist.gather(rates)
+    hm = harmonic_mean(all_rates)
+    value = hm * dist.world          # replicas run their roots concurrently
+    ms_per_step = dist.max(total_ms / args.steps)
+    flat_ms = [x for t in bfs_ms for x in t]
+    lat = dist.gather(flat_ms)
+    batched_gteps = sum(m_r) / (statistics.median(batch_ms) * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the persistent BFS kernel), algorithmic bytes
+    peaks = load_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    alg = [4 * s["edges_examined"] + 32 * s["reached"] + 8 * n for s in stats]
+    mean_bytes = statistics.mean(alg)
+    mean_ms = statistics.mean(flat_ms)
+    achieved = mean_bytes / (mean_ms * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "bfs_kernel_traffic.json")
+    if os.path.exists(tp):
+        try:
+            tj = json.load(open(tp))
+            if tj.get("scale") == scale and tj.get("source_hash") == kernel_source_hash():
+                traffic = tj["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    k1_bytes = kernel1_bytes(edges.shape[1], scale, g.nnz, n)
+
+    # end to end through the public API from pinned host memory
+    e2e = None if args.no_e2e else run_e2e(args, gb, torch, edges, scale, roots, m_r, dist)
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cs = min(scale, 20)   # the serial oracle builds SCALE > 20 graphs too slowly
+        v, done, spent, _ = oracle_sample(cs, len(all_roots), args.cpu_seconds)
+        cpu = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": "serial C oracle queue BFS on the SCALE %d graph of this workload "
+                         "rebuilt by the oracle, first %d of its %d roots (%.1f s of BFS)" % (
+                             cs, done, len(all_roots), spent)}
+    if dist.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": dist.world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic", "config": workload_config(args, scale),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "kernel": "bfs_kernel (persistent, one launch per root)",
+                             "peak_source": "measured" if peaks else "fallback"},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "batched": {"gteps": batched_gteps, "ms": statistics.median(batch_ms),
+                            "vs_plain": batched_gteps / hm, "roots": len(roots)},
+                "kernel1": {"ms": statistics.median(k1_ms),
+                            "gbs": k1_bytes / (statistics.median(k1_ms) * 1e-3) / 1e9,
+                            "alg_bytes": k1_bytes},
+                "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                               "p99": float(np.percentile(lat, 99))},
+                "graph": {"n": n, "nnz": g.nnz, "m": int(edges.shape[1]),
+                          "mean_levels": statistics.mean(s["nlevels"] for s in stats),
+                          "mean_edges_examined": statistics.mean(s["edges_examined"] for s in stats)}}
+        print(json.dumps(line))
+
+
+def kernel1_bytes(m, scale, nnz, n):
+    """Algorithmic HBM bytes of kernel 1: read tuples, write 2m keys, histogram
+    read, P sort passes (read+write 16 bytes per key), count + write passes
+    (read keys twice), write columns and offsets."""
+    nk = 2 * m
+    passes = (2 * scale + 7) // 8
+    return 16 * m + 8 * nk + 8 * nk + passes * 16 * nk + 16 * nk + 4 * nnz + 8 * (n + 1)
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("bfs.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2012_13548_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def run_e2e(args, gb, torch, edges, scale, roots, m_r, dist):
+    """The same metric end to end: per step the edge list goes host->device from
+    pinned memory, kernel 1 builds the graph, and every root's BFS result comes
+    back device->host into pinned memory.  A root's time is its BFS plus its
+    copy back plus 1/k of the upload and the build."""
+    stream = torch.cuda.current_stream()
+    h_edges = edges.cpu().pin_memory()
+    n = 1 << scale
+    d_edges = torch.empty_like(edges)
+    parent = torch.empty(n, dtype=torch.int32, device=edges.device)
+    level = torch.empty(n, dtype=torch.int32, device=edges.device)
+    h_par = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_lev = torch.empty(n, dtype=torch.int32).pin_memory()
+    k = len(roots)
+    rates = []
+    for s in range(args.warmup + args.steps):
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        d_edges.copy_(h_edges, non_blocking=True)
+        g = gb.graph_build_csr(d_edges, scale)
+        a1.record(stream)
+        per = []
+        for r in roots:
+            b0, b1 = ev(), ev()
+            b0.record(stream)
+            gb.bfs(g, int(r), parent, level)
+            h_par.copy_(parent, non_blocking=True)
+            h_lev.copy_(level, non_blocking=True)
+            b1.record(stream)
+            per.append((b0, b1))
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            share = a0.elapsed_time(a1) / k
+            rates += [m_r[i] / ((per[i][0].elapsed_time(per[i][1]) + share) * 1e-3) / 1e9
+                      for i in range(k)]
+        g.free()
+    all_rates = dist.gather(rates)
+    return {"value": harmonic_mean(all_rates) * dist.world, "unit": "GTEPS",
+            "h2d_bytes_per_step": int(h_edges.numel() * 8),
+            "d2h_bytes_per_step": int(k * 2 * n * 4)}
+
+
+def main():
+    args = parse_args()
+    dist = Dist("cpu" if args.impl == "reference" else "cuda")
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

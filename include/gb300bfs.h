@@ -62,6 +62,11 @@ const char *gb_last_error(void);
 /* ABI version of this header (incremented on incompatible change). */
 int gb_abi_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all threads); a caller takes differences to count the kernels of
+ * a region.  Library bookkeeping: the paper has no counterpart. */
+uint64_t gb_kernel_launches(void);
+
 /* Synchronise `s`, then return and clear the device status word: GB_OK, or
  * the first GB_ERR_RANGE / GB_ERR_TIMEOUT a kernel recorded since the last
  * call. */

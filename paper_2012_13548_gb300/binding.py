@@ -55,6 +55,7 @@ def lib():
         sigs = {
             "gb_last_error": (ctypes.c_char_p, []),
             "gb_abi_version": (ctypes.c_int, []),
+            "gb_kernel_launches": (ctypes.c_uint64, []),
             "gb_device_status": (ctypes.c_int, [_vp]),
             "kron_generate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
@@ -90,7 +91,7 @@ def lib():
 
 def exported_symbols():
     """Names of the C-ABI functions this binding wraps."""
-    return ["gb_last_error", "gb_abi_version", "gb_device_status", "kron_generate",
+    return ["gb_last_error", "gb_abi_version", "gb_kernel_launches", "gb_device_status", "kron_generate",
             "graph_build_csr", "graph_from_csr", "graph_free", "graph_info", "graph_csr_view",
             "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
             "bfs_last_stats", "server_create", "server_submit", "server_poll", "server_release",
@@ -161,6 +162,11 @@ class Graph:
                 _lib.graph_free(self._h)
         except Exception:
             pass
+
+
+def gb_kernel_launches():
+    """Kernels this library has launched so far in this process."""
+    return int(lib().gb_kernel_launches())
 
 
 def gb_device_status(stream=None):

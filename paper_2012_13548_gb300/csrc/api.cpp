@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -17,6 +18,7 @@
 namespace gb {
 
 namespace {
+std::atomic<unsigned long long> g_launches{0};
 thread_local std::string t_err;
 std::mutex g_ctx_mu;
 std::vector<Context *> g_ctx;  // indexed by device
@@ -52,6 +54,8 @@ gb_status check_graph(const gb_graph *g)
 }  // namespace
 
 void set_error(const std::string &msg) { t_err = msg; }
+void note_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
 const std::string &last_error() { return t_err; }
 
 gb_status cuda_fail(cudaError_t e, const char *what)
@@ -161,6 +165,8 @@ extern "C" {
 const char *gb_last_error(void) { return last_error().c_str(); }
 
 int gb_abi_version(void) { return 1; }
+
+uint64_t gb_kernel_launches(void) { return launches(); }
 
 gb_status gb_device_status(gb_stream s)
 {

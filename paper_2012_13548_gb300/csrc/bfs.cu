@@ -471,6 +471,7 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     void *args[] = {&a};
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfs_kernel, dim3(ctx->bfs_blocks),
                                         dim3(BFS_THREADS), args, 0, s));
+    note_launch();
     GB_CUDA(cudaFreeAsync(ws, s));
     return GB_OK;
 }

@@ -169,6 +169,7 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
     GB_CUDA(alloc_async(&k1, (size_t)nk, s));
     k1_sym_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(edges, m, scale,
                                                    reinterpret_cast<ulonglong2 *>(k0), ctx->status);
+    note_launch();
     GB_CUDA(cudaGetLastError());
     gb_status rc = radix_sort(k0, k1, nullptr, nullptr, nk, 0, 2 * scale, &ks, nullptr, s);
     if (rc != GB_OK) return rc;
@@ -178,7 +179,9 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
     GB_CUDA(alloc_async(&tcnt, (size_t)ntiles, s));
     GB_CUDA(alloc_async(&tbase, (size_t)ntiles + 1, s));
     k1_count_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tcnt);
+    note_launch();
     k1_scan_tiles_kernel<<<1, 1024, 0, s>>>(tcnt, ntiles, tbase);
+    note_launch();
     GB_CUDA(cudaGetLastError());
     unsigned long long nnz = 0;
     DevStatus hst;
@@ -201,6 +204,7 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
     GB_CUDA(cudaMalloc(&g->col, std::max<int64_t>(g->nnz, 4) * sizeof(int32_t)));
     k1_write_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tbase, n, g->off, g->col,
                                                              g->nnz, ctx->status);
+    note_launch();
     GB_CUDA(cudaGetLastError());
     GB_CUDA(cudaFreeAsync(k0, s));
     GB_CUDA(cudaFreeAsync(k1, s));

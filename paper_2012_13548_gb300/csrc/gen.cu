@@ -116,17 +116,21 @@ gb_status kron_generate_impl(int scale, int edgefactor, double a, double b, doub
     GB_CUDA(alloc_async(&v1, (size_t)m, s));
     GB_CUDA(alloc_async(&pi, (size_t)n, s));
     gen_hash_iota_kernel<<<blocks, 256, 0, s>>>(n, seed_perm, k0, v0);
+    note_launch();
     GB_CUDA(cudaGetLastError());
     gb_status rc = radix_sort(k0, k1, v0, v1, n, 0, 64, &ks, &vs, s);
     if (rc != GB_OK) return rc;
     gen_perm_scatter_kernel<<<blocks, 256, 0, s>>>(vs, n, pi, ctx->status);
+    note_launch();
     // Edge shuffle order.
     gen_hash_iota_kernel<<<blocks, 256, 0, s>>>(m, seed_shuf, k0, v0);
+    note_launch();
     GB_CUDA(cudaGetLastError());
     rc = radix_sort(k0, k1, v0, v1, m, 0, 64, &ks, &vs, s);
     if (rc != GB_OK) return rc;
     gen_edges_kernel<<<blocks, 256, 0, s>>>(scale, m, t_ab, t_a, t_c, seed_gen, vs, pi, edges,
                                             ctx->status);
+    note_launch();
     GB_CUDA(cudaGetLastError());
     GB_CUDA(cudaFreeAsync(k0, s));
     GB_CUDA(cudaFreeAsync(k1, s));

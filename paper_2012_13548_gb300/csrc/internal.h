@@ -43,6 +43,10 @@ gb_status cuda_fail(cudaError_t e, const char *what);
         if (e__ != cudaSuccess) return ::gb::cuda_fail(e__, #call); \
     } while (0)
 
+// Count of kernels this library has launched (process-wide).
+void note_launch(unsigned long long n = 1);
+unsigned long long launches();
+
 // Process-wide BFS options.
 gb_bfs_options &options();
 uint64_t timeout_ns();

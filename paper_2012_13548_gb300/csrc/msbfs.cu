@@ -620,6 +620,7 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     void *args[] = {&a};
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)ms_kernel<T>, dim3(ctx->ms_blocks),
                                         dim3(MS_THREADS), args, 0, s));
+    note_launch();
     GB_CUDA(cudaFreeAsync(ws, s));
     return GB_OK;
 }

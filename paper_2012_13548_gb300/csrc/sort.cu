@@ -246,7 +246,9 @@ gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_
 
     const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 4, (n + 511) / 512));
     rs_hist_kernel<<<hist_blocks, 512, 0, s>>>(keys, n, begin_bit, passes, hist);
+    note_launch();
     rs_scan_kernel<<<1, 256, 0, s>>>(hist, passes, portions, base);
+    note_launch();
     GB_CUDA(cudaGetLastError());
 
     uint64_t *kc = keys, *ka = keys_alt;
@@ -268,6 +270,7 @@ gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_
                 rs_onesweep_kernel<false><<<ntiles, RS_THREADS, dyn_smem, s>>>(
                     kc, ka, nullptr, nullptr, pb, pc, shift, ntiles, bin, bout, status, ctx->status,
                     tmo, n);
+            note_launch();
             GB_CUDA(cudaGetLastError());
         }
         std::swap(kc, ka);

@@ -1,0 +1,58 @@
+"""Run one small, self-contained case of a library kernel, for profilers.
+
+  python -m paper_2012_13548_gb300.profile_case --kernel bfs --scale 22 --roots 3
+  python -m paper_2012_13548_gb300.profile_case --kernel msbfs --scale 20 --roots 64
+  python -m paper_2012_13548_gb300.profile_case --kernel k1 --scale 22
+
+It generates the Kronecker graph of the given SCALE on the device, builds the
+CSR and then runs the chosen kernel a few times, holding nothing else on the
+device (a few GB at SCALE 22), so that a profiler can replay one launch.
+"""
+import argparse
+
+import torch
+
+from . import binding as gb
+from . import workloads as W
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--kernel", choices=["bfs", "msbfs", "k1"], default="bfs")
+    p.add_argument("--scale", type=int, default=22)
+    p.add_argument("--roots", type=int, default=3)
+    p.add_argument("--canonical", type=int, default=0)
+    a = p.parse_args()
+    spec = W.GraphSpec(scale=a.scale)
+    gb.bfs_set_options(canonical_parents=a.canonical)
+    edges = gb.kron_generate(**spec.kron_args())
+    g = gb.graph_build_csr(edges, a.scale)
+    off, _ = g.csr()
+    roots = [int(r) for r in W.select_roots(off.cpu().numpy(), max(a.roots, 1), spec.seeds()[3])]
+    if a.kernel == "bfs":
+        parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        level = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for r in roots:
+            gb.bfs(g, r, parent, level)
+            st = gb.bfs_last_stats()
+            print("root %d levels %d reached %d edges_examined %d td %d bu %d" % (
+                r, st["nlevels"], st["reached"], st["edges_examined"], st["td_levels"],
+                st["bu_levels"]))
+    elif a.kernel == "msbfs":
+        P = torch.empty((len(roots), g.n), dtype=torch.int32, device="cuda")
+        L = torch.empty((len(roots), g.n), dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            gb.bfs_batch(g, roots, P, L)
+            print(gb.bfs_last_stats())
+    else:
+        del g
+        for _ in range(2):
+            g2 = gb.graph_build_csr(edges, a.scale)
+            g2.free()
+    gb.gb_device_status()
+    torch.cuda.synchronize()
+    print("ok")
+
+
+if __name__ == "__main__":
+    main()

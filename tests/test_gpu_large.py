@@ -1,0 +1,82 @@
+"""Full-size checks that need no oracle run: at SCALE 24 (and SCALE 26 when
+GB_TEST_S26=1) the CSR must satisfy the Sec. 2.2 invariants and every BFS
+result must pass the Graph500 rules, which together force the levels to be
+the exact hop distances.  The properties are computed here with plain torch
+tensor operations, independently of the library."""
+import os
+
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2012_13548_gb300 as gb  # noqa: E402
+from paper_2012_13548_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+SCALES = [24] + ([26] if os.environ.get("GB_TEST_S26") == "1" else [])
+
+
+def csr_properties(off, col, n):
+    assert off.numel() == n + 1 and int(off[0]) == 0 and int(off[-1]) == col.numel()
+    deg = off[1:] - off[:-1]
+    assert bool((deg >= 0).all())
+    assert int(col.min()) >= 0 and int(col.max()) < n
+    rows = torch.repeat_interleave(torch.arange(n, device=col.device, dtype=torch.int32), deg)
+    assert bool((rows != col).all()), "self-loop in the CSR"
+    same = rows[1:] == rows[:-1]
+    assert bool((col[1:][same] > col[:-1][same]).all()), "row not strictly ascending"
+    key = rows.to(torch.int64) * n + col.to(torch.int64)
+    rkey = col.to(torch.int64) * n + rows.to(torch.int64)
+    pos = torch.searchsorted(key, rkey)
+    assert bool((key[pos.clamp(max=key.numel() - 1)] == rkey).all()), "CSR not symmetric"
+    return rows, key
+
+
+def tree_properties(off, col, rows, key, n, root, parent, level):
+    assert int(level[root]) == 0 and int(parent[root]) == root
+    assert bool(((parent == -1) == (level == -1)).all())
+    lr, lc = level[rows.long()], level[col.long()]
+    assert bool(((lr >= 0) == (lc >= 0)).all()), "edge leaves the reached set"
+    assert bool(((lr - lc).abs()[lr >= 0] <= 1).all()), "edge spans two levels"
+    v = torch.nonzero(level > 0).flatten()
+    p = parent[v].long()
+    assert bool((level[p] == level[v] - 1).all()), "parent not one level up"
+    pk = v * n + p
+    pos = torch.searchsorted(key, pk).clamp(max=key.numel() - 1)
+    assert bool((key[pos] == pk).all()), "parent is not a neighbour"
+
+
+@pytest.mark.parametrize("scale", SCALES)
+def test_full_size_csr_and_bfs_properties(scale):
+    spec = W.GraphSpec(scale=scale)
+    edges = gb.kron_generate(**spec.kron_args())
+    e0 = edges[0].clone()
+    g = gb.graph_build_csr(edges, scale)
+    del edges
+    torch.cuda.empty_cache()
+    off, col = g.csr()
+    n = g.n
+    rows, key = csr_properties(off, col, n)
+    roots = W.select_roots(off.cpu().numpy(), 4, spec.seeds()[3])
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    for canonical in (0, 1):
+        gb.bfs_set_options(canonical_parents=canonical)
+        for r in roots:
+            gb.bfs(g, int(r), parent, level)
+            gb.gb_device_status()
+            tree_properties(off, col, rows, key, n, int(r), parent, level)
+            st = gb.bfs_last_stats()
+            assert st["reached"] == int((level >= 0).sum())
+    gb.bfs_set_options(canonical_parents=0)
+    # the multi-source rows equal the single-source levels
+    P, L = gb.bfs_batch(g, [int(r) for r in roots])
+    for i, r in enumerate(roots):
+        gb.bfs(g, int(r), parent, level)
+        assert torch.equal(L[i], level)
+        tree_properties(off, col, rows, key, n, int(r), P[i], L[i])
+    gb.gb_device_status()
+    del e0
