@@ -146,7 +146,9 @@ gb_status graph_csr_view(const gb_graph *g, const int64_t **off, const int32_t *
  *   ms_alpha, ms_beta  the same switch for the multi-source BFS.
  *   timeout_ms         limit of every device-side wait (grid barriers, the
  *                      radix-sort look-back); on expiry the kernel records
- *                      GB_ERR_TIMEOUT and returns. */
+ *                      GB_ERR_TIMEOUT and returns.
+ *   blocks_per_sm      2 or 3: resident blocks of the single-source kernel
+ *                      per SM (3 trades register spills for more warps). */
 typedef struct gb_bfs_options {
     int canonical_parents;
     double alpha;
@@ -155,6 +157,7 @@ typedef struct gb_bfs_options {
     double ms_alpha;
     double ms_beta;
     double timeout_ms;
+    int blocks_per_sm;
 } gb_bfs_options;
 
 gb_status bfs_get_options(gb_bfs_options *out);
@@ -193,7 +196,9 @@ gb_status bfs_multi_graph(const gb_graph *const *gs, int ng, const int64_t *root
  *   vertices_touched frontier vertices expanded plus unvisited vertices
  *                    tested
  *   reached          vertices with level >= 0 (summed over roots)
- *   td_levels, bu_levels  levels run top-down / bottom-up */
+ *   td_levels, bu_levels  levels run top-down / bottom-up
+ *   level_*          per-level device time, frontier and step (see below) */
+#define GB_STAT_LEVELS 32
 typedef struct gb_bfs_stats {
     int64_t nlevels;
     int64_t edges_examined;
@@ -201,6 +206,12 @@ typedef struct gb_bfs_stats {
     int64_t reached;
     int64_t td_levels;
     int64_t bu_levels;
+    /* single-source bfs() only, first GB_STAT_LEVELS levels: device time of
+     * each level in ns, its frontier size, and its step (1 top-down,
+     * 2 bottom-up); zero for the batched calls */
+    int64_t level_ns[GB_STAT_LEVELS];
+    int64_t level_frontier[GB_STAT_LEVELS];
+    int32_t level_dir[GB_STAT_LEVELS];
 } gb_bfs_stats;
 
 gb_status bfs_last_stats(gb_bfs_stats *out);

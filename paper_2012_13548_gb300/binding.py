@@ -11,7 +11,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libgb300bfs.so")
+# GB_CHECKED=1 selects the index-checking debug build (build_ext --checked).
+LIB_PATH = os.path.join(_HERE, "_build_checked" if os.environ.get("GB_CHECKED") == "1" else "_build",
+                        "libgb300bfs.so")
 
 GB_OK, GB_ERR_INVALID, GB_ERR_NOMEM, GB_ERR_CUDA = 0, -1, -2, -3
 GB_ERR_TIMEOUT, GB_ERR_RANGE, GB_ERR_BUSY, GB_ERR_UNIMPLEMENTED = -4, -5, -6, -7
@@ -29,13 +31,18 @@ class gb_bfs_options(ctypes.Structure):
     _fields_ = [("canonical_parents", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("big_degree", ctypes.c_int),
                 ("ms_alpha", ctypes.c_double), ("ms_beta", ctypes.c_double),
-                ("timeout_ms", ctypes.c_double)]
+                ("timeout_ms", ctypes.c_double), ("blocks_per_sm", ctypes.c_int)]
+
+
+GB_STAT_LEVELS = 32
 
 
 class gb_bfs_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in
                 ("nlevels", "edges_examined", "vertices_touched", "reached", "td_levels",
-                 "bu_levels")]
+                 "bu_levels")] + [("level_ns", ctypes.c_int64 * GB_STAT_LEVELS),
+                                  ("level_frontier", ctypes.c_int64 * GB_STAT_LEVELS),
+                                  ("level_dir", ctypes.c_int32 * GB_STAT_LEVELS)]
 
 
 _lib = None
@@ -214,7 +221,8 @@ def bfs_get_options():
 
 
 def bfs_set_options(**kw):
-    """Update any of canonical_parents, alpha, beta, big_degree, ms_alpha, ms_beta, timeout_ms."""
+    """Update any of canonical_parents, alpha, beta, big_degree, ms_alpha, ms_beta,
+    timeout_ms, blocks_per_sm."""
     cur = bfs_get_options()
     unknown = set(kw) - set(cur)
     if unknown:
@@ -276,4 +284,9 @@ def bfs_last_stats():
     """Counters of this thread's last BFS call (synchronises its stream)."""
     s = gb_bfs_stats()
     _check(lib().bfs_last_stats(ctypes.byref(s)))
-    return {f: getattr(s, f) for f, _ in gb_bfs_stats._fields_}
+    out = {f: getattr(s, f) for f, _ in gb_bfs_stats._fields_[:6]}
+    k = min(out["nlevels"], GB_STAT_LEVELS)
+    out["level_ns"] = list(s.level_ns)[:k]
+    out["level_frontier"] = list(s.level_frontier)[:k]
+    out["level_dir"] = ["td" if d == 1 else "bu" if d == 2 else "-" for d in list(s.level_dir)[:k]]
+    return out

@@ -16,6 +16,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgb300bfs.so")
+# A debugging variant whose kernels test every global index first and record a
+# bad one in the device status word instead of touching memory.
+OUT_DIR_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(OUT_DIR_CHECKED, "libgb300bfs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,14 +44,18 @@ def _compile(src, obj, extra):
     return r.stderr
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile every csrc/*.cu and csrc/*.cpp and link the shared library."""
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, extra=(), checked=False):
+    """Compile every csrc/*.cu and csrc/*.cpp and link the shared library
+    (the index-checking variant with checked=True)."""
+    out_dir, lib = (OUT_DIR_CHECKED, LIB_CHECKED) if checked else (OUT_DIR, LIB)
+    if checked:
+        extra = list(extra) + ["-DGB_CHECKED"]
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     dep_time = max([os.path.getmtime(p) for p in _deps()] + [os.path.getmtime(__file__)])
     jobs, objs = [], []
     for src in srcs:
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         objs.append(obj)
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), dep_time):
             jobs.append((src, obj))
@@ -56,17 +64,18 @@ def build(force=False, verbose=False, extra=()):
             for (src, _), log in zip(jobs, ex.map(lambda j: _compile(j[0], j[1], list(extra)), jobs)):
                 if verbose and log:
                     print("[%s]\n%s" % (os.path.basename(src), log))
-    if jobs or force or not os.path.exists(LIB):
-        tmp = LIB + ".tmp.%d" % os.getpid()
+    if jobs or force or not os.path.exists(lib):
+        tmp = lib + ".tmp.%d" % os.getpid()
         cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [],
+                checked="--checked" in sys.argv))

@@ -31,6 +31,7 @@ gb_bfs_options g_opt = {
     16.0,    // ms_alpha
     32.0,    // ms_beta
     5000.0,  // timeout_ms
+    2,       // blocks_per_sm
 };
 
 // last-call statistics of this thread
@@ -104,7 +105,8 @@ Context *context()
         uint64_t thr = ~0ull;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
-    c->bfs_blocks = bfs_pick_blocks(c->num_sms);
+    c->bfs_blocks = bfs_pick_blocks(c->num_sms, 3);
+    c->bfs_blocks2 = bfs_pick_blocks(c->num_sms, 2);
     c->ms_blocks = msbfs_pick_blocks(c->num_sms);
     g_ctx[dev] = c;
     return c;
@@ -212,6 +214,7 @@ gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *
         if (rc != GB_OK) {
             if (g->off) cudaFree(g->off);
             if (g->col) cudaFree(g->col);
+            if (g->nz) cudaFree(g->nz);
             delete g;
             return rc;
         }
@@ -267,6 +270,15 @@ gb_status graph_from_csr(const int64_t *off, const int32_t *col, int64_t n, int6
             delete g;
             return cuda_fail(e, "graph_from_csr");
         }
+        gb_status rc = build_nz_bitmap(g, st);
+        if (rc == GB_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "graph_from_csr");
+        if (rc != GB_OK) {
+            cudaFree(g->off);
+            cudaFree(g->col);
+            if (g->nz) cudaFree(g->nz);
+            delete g;
+            return rc;
+        }
         *out = g;
         return GB_OK;
     });
@@ -279,8 +291,10 @@ gb_status graph_free(gb_graph *g)
         cudaDeviceSynchronize();
         if (g->off) cudaFree(g->off);
         if (g->col) cudaFree(g->col);
+        if (g->nz) cudaFree(g->nz);
         g->off = nullptr;
         g->col = nullptr;
+        g->nz = nullptr;
         delete g;
         return GB_OK;
     });
@@ -317,8 +331,10 @@ gb_status bfs_get_options(gb_bfs_options *out)
 gb_status bfs_set_options(const gb_bfs_options *opt)
 {
     if (!opt || !(opt->alpha > 0) || !(opt->beta > 0) || opt->big_degree < 1 ||
-        !(opt->ms_alpha > 0) || !(opt->ms_beta > 0) || !(opt->timeout_ms > 0)) {
-        set_error("bfs_set_options: alpha, beta, ms_alpha, ms_beta, timeout_ms must be > 0 and big_degree >= 1");
+        !(opt->ms_alpha > 0) || !(opt->ms_beta > 0) || !(opt->timeout_ms > 0) ||
+        (opt->blocks_per_sm != 2 && opt->blocks_per_sm != 3)) {
+        set_error("bfs_set_options: alpha, beta, ms_alpha, ms_beta, timeout_ms must be > 0, "
+                  "big_degree >= 1 and blocks_per_sm 2 or 3");
         return GB_ERR_INVALID;
     }
     options() = *opt;
@@ -418,6 +434,12 @@ gb_status bfs_last_stats(gb_bfs_stats *out)
         out->reached = (int64_t)h.reached;
         out->td_levels = (int64_t)h.td_levels;
         out->bu_levels = (int64_t)h.bu_levels;
+        for (int i = 0; i < GB_STAT_LEVELS; ++i) {
+            const bool in = i < kStatLevels && (uint64_t)i < h.nlevels;
+            out->level_ns[i] = in ? (int64_t)h.level_ns[i] : 0;
+            out->level_frontier[i] = in ? (int64_t)h.level_frontier[i] : 0;
+            out->level_dir[i] = in ? h.level_dir[i] : 0;
+        }
         return GB_OK;
     });
 }

@@ -40,9 +40,24 @@ namespace {
 
 constexpr int BFS_THREADS = 512;
 constexpr int BIG_CHUNK = 256;      // edges per chunk of a big frontier vertex
-constexpr int BU_SERIAL_MAX = 32;   // bottom-up: larger rows are scanned by the whole warp
+constexpr int BU_LANE_MAX = 32;     // bottom-up: rows up to this length are scanned by one lane
+constexpr int BU_LANE_FIRST = 16;   // longer rows: one lane tests the first 16, then the warp
+constexpr int BU_BATCH = 8;         // neighbours whose loads one lane issues together
+constexpr int BFS_WARPS = BFS_THREADS / 32;
+constexpr int QBUF = 256;           // per-warp buffer of discovered vertices (shared memory)
+constexpr int BBUF = 32;            // per-warp buffer of discovered big-degree vertices
 constexpr int SITE_BFS_BAR = 20;
 constexpr int SITE_BFS_LEVELS = 21;
+
+// With GB_CHECKED defined every global index below is tested first; a bad
+// one is recorded in the status word (site, index) and the access skipped.
+#ifdef GB_CHECKED
+#define GB_OK_IDX(st, i, bound, site) \
+    ((int64_t)(i) >= 0 && (int64_t)(i) < (int64_t)(bound) \
+         ? true : (record_error((st), GB_ERR_RANGE, (site), (long long)(i)), false))
+#else
+#define GB_OK_IDX(st, i, bound, site) true
+#endif
 
 struct LevelCtl {
     unsigned long long qcnt;  // vertices appended to the next queue
@@ -62,11 +77,13 @@ struct WsHeader {
     unsigned pad0;
     LevelCtl ctl[4];
     unsigned long long acc[6];  // edges, touched, reached, nlevels, td, bu
+    unsigned long long t0;      // global timer at the end of the init phase
 };
 
 struct BfsArgs {
     const int64_t *off;
     const int32_t *col;
+    const uint32_t *nz;  // degree >= 1 bitmap
     int64_t n;
     int64_t nnz;
     int32_t root;
@@ -77,6 +94,7 @@ struct BfsArgs {
     int64_t nw;
     int32_t *queue;
     BigEnt *bigq;
+    int64_t bigcap;
     WsHeader *hdr;
     DevStatus *st;
     BfsDevStats *stats;
@@ -103,41 +121,95 @@ __device__ __forceinline__ unsigned nchunks(int64_t deg)
     return (unsigned)((deg + BIG_CHUNK - 1) / BIG_CHUNK);
 }
 
-// Warp-collective: append the lanes with `won` to the next frontier (queue,
-// degree sum and, for big degrees, the chunk list).
+// Discovered vertices are staged per warp in shared memory and moved to the
+// global queue with one atomic per flush, so that the level counters see a
+// few atomics per warp instead of one per 32 discoveries.  The fill levels
+// are warp-uniform registers: every lane adds the same ballot counts, so no
+// lane ever reads a count another lane is writing.
+struct WarpBuf {
+    int32_t q[QBUF];
+    unsigned long long b[BBUF];  // v | nchunks << 32
+};
+
+// Warp-collective: move the staged queue entries to the next level's queue.
+__device__ __forceinline__ void flush_queue(WarpBuf &wb, int &qn, const BfsArgs &a,
+                                            LevelCtl *nxt, int64_t qnext_base)
+{
+    if (qn == 0) return;
+    __syncwarp();  // the lanes' buffer writes are visible to the whole warp
+    const unsigned lane = lane_id();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&nxt->qcnt, (unsigned long long)qn);
+    base = __shfl_sync(kFull, base, 0);
+    for (int i = lane; i < qn; i += 32)
+        if (GB_OK_IDX(a.st, qnext_base + (int64_t)base + i, a.n, 200))
+            __stcg(&a.queue[qnext_base + (int64_t)base + i], wb.q[i]);
+    __syncwarp();  // every lane has read the buffer before it is refilled
+    qn = 0;
+}
+
+// Warp-collective: give the staged big vertices their chunk ranges and list them.
+__device__ __forceinline__ void flush_big(WarpBuf &wb, int &bn, const BfsArgs &a, LevelCtl *nxt,
+                                          int64_t bnext_base)
+{
+    if (bn == 0) return;
+    __syncwarp();
+    const unsigned lane = lane_id();
+    const unsigned long long e = (int)lane < bn ? wb.b[lane] : 0ull;
+    const unsigned nch = (unsigned)(e >> 32);
+    const unsigned incl = warp_inclusive_scan(nch);
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    unsigned long long p = 0;
+    if (lane == 0) p = atomicAdd(&nxt->big, ((unsigned long long)bn << 32) | total);
+    p = __shfl_sync(kFull, p, 0);
+    if ((int)lane < bn && GB_OK_IDX(a.st, bnext_base + (int64_t)(p >> 32) + lane, a.bigcap, 202)) {
+        const unsigned long long cb = (p & 0xffffffffull) + incl - nch;
+        __stcg(reinterpret_cast<unsigned long long *>(a.bigq) + bnext_base + (int64_t)(p >> 32) + lane,
+               (e & 0xffffffffull) | (cb << 32));
+    }
+    __syncwarp();
+    bn = 0;
+}
+
+// Warp-collective: the lanes with `won` join the next frontier.
 __device__ __forceinline__ void append_next(bool won, int32_t v, int64_t dv, const BfsArgs &a,
-                                            LevelCtl *nxt, int64_t qnext_base, int64_t bnext_base)
+                                            WarpBuf &wb, int &qn, int &bn,
+                                            unsigned long long &my_mf, LevelCtl *nxt,
+                                            int64_t qnext_base, int64_t bnext_base)
 {
     const unsigned bal = __ballot_sync(kFull, won);
     if (bal == 0) return;
-    const unsigned lane = lane_id();
-    const int leader = __ffs(bal) - 1;
-    unsigned long long base = 0;
-    if ((int)lane == leader) base = atomicAdd(&nxt->qcnt, (unsigned long long)__popc(bal));
-    base = __shfl_sync(kFull, base, leader);
-    unsigned long long dsum = warp_sum((unsigned long long)(won ? dv : 0));
+    const int cnt = __popc(bal);
+    if (qn + cnt > QBUF) flush_queue(wb, qn, a, nxt, qnext_base);
     if (won) {
-        __stcg(&a.queue[qnext_base + (int64_t)base + __popc(bal & lanemask_lt())], v);
-        if (dv > a.big_deg) {
-            const unsigned long long p =
-                atomicAdd(&nxt->big, (1ull << 32) | (unsigned long long)nchunks(dv));
-            const unsigned long long packed =
-                (unsigned long long)(uint32_t)v | ((p & 0xffffffffull) << 32);
-            __stcg(reinterpret_cast<unsigned long long *>(a.bigq) + bnext_base + (int64_t)(p >> 32),
-                   packed);
-        }
+        const int pos = qn + __popc(bal & lanemask_lt());
+        if (GB_OK_IDX(a.st, pos, QBUF, 203)) wb.q[pos] = v;
+        my_mf += (unsigned long long)dv;
     }
-    if ((int)lane == leader) atomicAdd(&nxt->mf, dsum);
+    qn += cnt;
+    const bool big = won && dv > a.big_deg;
+    const unsigned bb = __ballot_sync(kFull, big);
+    if (bb) {
+        const int bc = __popc(bb);
+        if (bn + bc > BBUF) flush_big(wb, bn, a, nxt, bnext_base);
+        if (big) {
+            const int pos = bn + __popc(bb & lanemask_lt());
+            if (GB_OK_IDX(a.st, pos, BBUF, 204))
+                wb.b[pos] = (unsigned long long)(uint32_t)v | ((unsigned long long)nchunks(dv) << 32);
+        }
+        bn += bc;
+    }
 }
 
 // Warp-collective top-down visit of edge (src -> v) for the lanes with `valid`.
 __device__ __forceinline__ void td_visit(bool valid, int32_t src, int32_t v, int l,
-                                         const BfsArgs &a, unsigned *Fn, LevelCtl *nxt,
+                                         const BfsArgs &a, unsigned *Fn, WarpBuf &wb, int &qn,
+                                         int &bn, unsigned long long &my_mf, LevelCtl *nxt,
                                          int64_t qnext_base, int64_t bnext_base)
 {
     bool won = false;
     int64_t dv = 0;
-    if (valid) {
+    if (valid && GB_OK_IDX(a.st, v, a.n, 205)) {
         const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
         if (!(ldcg_u32(&a.vis[w]) & bit)) {
             const unsigned old = atomicOr(&a.vis[w], bit);
@@ -150,10 +222,13 @@ __device__ __forceinline__ void td_visit(bool valid, int32_t src, int32_t v, int
             }
         }
     }
-    append_next(won, v, dv, a, nxt, qnext_base, bnext_base);
+    append_next(won, v, dv, a, wb, qn, bn, my_mf, nxt, qnext_base, bnext_base);
 }
 
-__global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
+// MINB = blocks of BFS_THREADS per SM the register budget is sized for:
+// 2 (64 registers, no spills) or 3 (40 registers, more warps to hide latency).
+template <int MINB>
+__global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
 {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
@@ -163,6 +238,12 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
     const int64_t n = a.n, nw = a.nw;
     WsHeader *h = a.hdr;
     const int32_t root = a.root;
+    __shared__ WarpBuf s_wb[BFS_WARPS];
+    __shared__ unsigned long long s_mf;
+    WarpBuf &wb = s_wb[threadIdx.x >> 5];
+    int qn_buf = 0, bn_buf = 0;  // warp-uniform fill levels of wb
+    if (threadIdx.x == 0) s_mf = 0;
+    unsigned long long my_mf = 0;
 
     // ---- init: outputs to -1, bitmaps cleared, the root placed
     for (int64_t v = gtid; v < n; v += gthreads) {
@@ -170,9 +251,10 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
         a.level[v] = v == root ? 0 : -1;
     }
     for (int64_t w = gtid; w < nw; w += gthreads) {
-        const unsigned tail = (w == nw - 1 && (n & 31)) ? ~((1u << (n & 31)) - 1u) : 0u;
         const unsigned rb = (w == (root >> 5)) ? 1u << (root & 31) : 0u;
-        a.vis[w] = tail | rb;  // ids >= n count as visited
+        // isolated vertices (and ids >= n) start as visited: no search reaches
+        // them and the bottom-up step need not test them; their outputs stay -1
+        a.vis[w] = ~a.nz[w] | rb;
         a.fb[w] = rb;
         a.fb[nw + w] = 0;
         a.fb[2 * nw + w] = 0;
@@ -192,6 +274,10 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
         }
     }
     if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_BFS_BAR)) return;
+    if (gtid == 0) {
+        h->t0 = globaltimer_ns();
+        a.stats->init_ns = 0;
+    }
 
     int64_t qbase = 0, bbase = 0, prev_qn = 0;
     double mu = (double)a.nnz;
@@ -268,15 +354,16 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
                             ++ow;
                             be = load_big(a.bigq, bbase + ow);
                         }
+                        if (!GB_OK_IDX(a.st, be.u, a.n, 206)) continue;
                         const int64_t s = a.off[be.u] + (c - (int64_t)be.cbase) * BIG_CHUNK;
                         const int64_t eu = a.off[be.u + 1];
                         const int64_t e = s + BIG_CHUNK < eu ? s + BIG_CHUNK : eu;
                         if (lane == 0) my_edges += (unsigned long long)(e - s);
                         for (int64_t b = s; b < e; b += 32) {
                             const int64_t j = b + lane;
-                            const bool valid = j < e;
+                            const bool valid = j < e && GB_OK_IDX(a.st, j, a.nnz, 207);
                             const int32_t v = valid ? a.col[j] : 0;
-                            td_visit(valid, be.u, v, l, a, Fn, nxt, qnext_base, bnext_base);
+                            td_visit(valid, be.u, v, l, a, Fn, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
                         }
                     }
                 }
@@ -286,8 +373,9 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
                 const int64_t i = i0 + lane;
                 int32_t u = 0;
                 int64_t s = 0, d = 0;
-                if (i < qn) {
+                if (i < qn && GB_OK_IDX(a.st, qbase + i, a.n, 208)) {
                     u = ldcg_i32(&a.queue[qbase + i]);
+                    if (!GB_OK_IDX(a.st, u, a.n, 209)) u = 0;
                     s = a.off[u];
                     d = a.off[u + 1] - s;
                     if (d > a.big_deg) d = 0;
@@ -309,9 +397,9 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
                     const int32_t src = __shfl_sync(kFull, u, owner);
                     const int64_t so = __shfl_sync(kFull, s, owner);
                     const int64_t eo = __shfl_sync(kFull, excl, owner);
-                    const bool valid = k < total;
+                    const bool valid = k < total && GB_OK_IDX(a.st, so + (k - eo), a.nnz, 210);
                     const int32_t v = valid ? a.col[so + (k - eo)] : 0;
-                    td_visit(valid, src, v, l, a, Fn, nxt, qnext_base, bnext_base);
+                    td_visit(valid, src, v, l, a, Fn, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
                 }
             }
         } else {
@@ -322,55 +410,83 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
                 const int64_t u = w * 32 + lane;
                 const bool cand = !((vw >> lane) & 1u);
                 int64_t s = 0, e = 0;
-                if (cand) {
+                if (cand && GB_OK_IDX(a.st, u, a.n, 216)) {
                     s = a.off[u];
                     e = a.off[u + 1];
                 }
                 const int64_t deg = e - s;
                 int32_t found = -1;
-                if (cand && deg <= BU_SERIAL_MAX) {
-                    int64_t j = s;
-                    for (; j < e; ++j) {
-                        const int32_t v = a.col[j];
-                        if ((ldcg_u32(&F[v >> 5]) >> (v & 31)) & 1u) {
-                            found = v;
-                            break;
-                        }
+                int64_t j = s;
+                if (cand) {
+                    // one lane, neighbours in ascending order, BU_BATCH loads in flight
+                    const int64_t jl = deg <= BU_LANE_MAX ? e : s + BU_LANE_FIRST;
+                    int64_t hit = -1;
+                    while (j < jl) {
+                        int32_t vv[BU_BATCH];
+                        unsigned fw[BU_BATCH];
+#pragma unroll
+                        for (int t = 0; t < BU_BATCH; ++t)
+                            vv[t] = j + t < jl && GB_OK_IDX(a.st, j + t, a.nnz, 211) ? __ldg(&a.col[j + t]) : -1;
+#pragma unroll
+                        for (int t = 0; t < BU_BATCH; ++t)
+                            fw[t] = vv[t] >= 0 && GB_OK_IDX(a.st, vv[t], a.n, 212) ? ldcg_u32(&F[vv[t] >> 5]) : 0u;
+#pragma unroll
+                        for (int t = 0; t < BU_BATCH; ++t)
+                            if (hit < 0 && vv[t] >= 0 && ((fw[t] >> (vv[t] & 31)) & 1u)) {
+                                hit = j + t;
+                                found = vv[t];
+                            }
+                        if (hit >= 0) break;
+                        j += BU_BATCH;
                     }
-                    my_edges += (found >= 0) ? (j - s + 1) : deg;
+                    if (j > jl) j = jl;
+                    my_edges += hit >= 0 ? (unsigned long long)(hit - s + 1) : (unsigned long long)(j - s);
                 }
                 my_touched += cand;
-                unsigned bigm = __ballot_sync(kFull, cand && deg > BU_SERIAL_MAX);
+                // rows left unresolved: the whole warp scans the rest, 32 per round
+                unsigned bigm = __ballot_sync(kFull, cand && found < 0 && j < e);
                 while (bigm) {
                     const int jl = __ffs(bigm) - 1;
                     bigm &= bigm - 1;
-                    const int64_t sj = __shfl_sync(kFull, s, jl);
+                    const int64_t sj = __shfl_sync(kFull, j, jl);
                     const int64_t ej = __shfl_sync(kFull, e, jl);
                     int32_t fj = -1;
                     int64_t scanned = 0;
-                    for (int64_t b = sj; b < ej; b += 32) {
-                        const int64_t j = b + lane;
-                        int32_t v = 0;
-                        bool hit = false;
-                        if (j < ej) {
-                            v = a.col[j];
-                            hit = (ldcg_u32(&F[v >> 5]) >> (v & 31)) & 1u;
+                    for (int64_t b = sj; b < ej; b += 128) {
+                        // lane i tests entries b+4i .. b+4i+3: 128 loads in flight per round
+                        int32_t vv[4];
+                        unsigned fw[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int64_t jj = b + 4 * lane + t;
+                            vv[t] = jj < ej && GB_OK_IDX(a.st, jj, a.nnz, 213) ? __ldg(&a.col[jj]) : -1;
                         }
-                        const unsigned hb = __ballot_sync(kFull, hit);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            fw[t] = vv[t] >= 0 && GB_OK_IDX(a.st, vv[t], a.n, 214) ? ldcg_u32(&F[vv[t] >> 5]) : 0u;
+                        int first = -1;
+                        int32_t hv = 0;
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            if (first < 0 && vv[t] >= 0 && ((fw[t] >> (vv[t] & 31)) & 1u)) {
+                                first = t;
+                                hv = vv[t];
+                            }
+                        const unsigned hb = __ballot_sync(kFull, first >= 0);
                         if (hb) {
                             const int fl = __ffs(hb) - 1;
-                            fj = __shfl_sync(kFull, v, fl);
-                            scanned += fl + 1;
+                            fj = __shfl_sync(kFull, hv, fl);
+                            scanned += 4 * fl + __shfl_sync(kFull, first, fl) + 1;
                             break;
                         }
-                        scanned += (ej - b < 32 ? ej - b : 32);
+                        scanned += (ej - b < 128 ? ej - b : 128);
                     }
                     if ((int)lane == jl) {
                         found = fj;
                         my_edges += scanned;
                     }
                 }
-                const bool won = found >= 0;
+                const bool won = found >= 0 && GB_OK_IDX(a.st, u, a.n, 215);
                 if (won) {
                     a.parent[u] = found;
                     a.level[u] = l + 1;
@@ -380,7 +496,20 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
                     __stcg(&a.vis[w], vw | nm);
                     __stcg(&Fn[w], nm);
                 }
-                append_next(won, (int32_t)u, deg, a, nxt, qnext_base, bnext_base);
+                append_next(won, (int32_t)u, deg, a, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
+            }
+        }
+        // end of level: flush the staged vertices and add the block's degree sum
+        flush_queue(wb, qn_buf, a, nxt, qnext_base);
+        flush_big(wb, bn_buf, a, nxt, bnext_base);
+        {
+            const unsigned long long t = warp_sum(my_mf);
+            my_mf = 0;
+            if (lane == 0 && t) atomicAdd(&s_mf, t);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (s_mf) atomicAdd(&nxt->mf, s_mf);
+                s_mf = 0;
             }
         }
         prev_td = td;
@@ -389,6 +518,13 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
         bbase += nb;
         if (gtid == 0) atomicAdd(&h->acc[td ? 4 : 5], 1ull);
         if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_BFS_BAR)) return;
+        if (gtid == 0 && l < kStatLevels) {
+            const uint64_t now = globaltimer_ns();
+            a.stats->level_ns[l] = now - h->t0;
+            a.stats->level_frontier[l] = qn;
+            a.stats->level_dir[l] = td ? 1 : 2;
+            h->t0 = now;
+        }
     }
 
     // ---- statistics: block partial sums, the last block publishes them
@@ -404,28 +540,27 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) bfs_kernel(BfsArgs a)
         const unsigned prev = atomicAdd(&h->done, 1u);
         if (prev == gridDim.x - 1) {
             __threadfence();
-            BfsDevStats s;
+            BfsDevStats &s = *a.stats;
             s.nlevels = (unsigned long long)l;
             s.edges_examined = ldcg_u64(&h->acc[0]);
             s.vertices_touched = ldcg_u64(&h->acc[1]);
             s.reached = (unsigned long long)qbase;
             s.td_levels = ldcg_u64(&h->acc[4]);
             s.bu_levels = ldcg_u64(&h->acc[5]);
-            *a.stats = s;
         }
     }
 }
 
 }  // namespace
 
-int bfs_pick_blocks(int num_sms)
+int bfs_pick_blocks(int num_sms, int minb)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_kernel, BFS_THREADS, 0) !=
-            cudaSuccess ||
+    const void *k = minb == 2 ? (const void *)bfs_kernel<2> : (const void *)bfs_kernel<3>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BFS_THREADS, 0) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    return num_sms * std::min(per_sm, 2);
+    return num_sms * std::min(per_sm, minb);
 }
 
 gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level,
@@ -450,6 +585,7 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     BfsArgs a;
     a.off = g->off;
     a.col = g->col;
+    a.nz = g->nz;
     a.n = n;
     a.nnz = g->nnz;
     a.root = (int32_t)root;
@@ -461,6 +597,7 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.nw = nw;
     a.queue = reinterpret_cast<int32_t *>(ws + off_q);
     a.bigq = reinterpret_cast<BigEnt *>(ws + off_big);
+    a.bigcap = bigcap;
     a.st = ctx->status;
     a.stats = stats;
     a.alpha = (float)o.alpha;
@@ -469,7 +606,10 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.canonical = o.canonical_parents;
     a.timeout_ns = timeout_ns();
     void *args[] = {&a};
-    GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfs_kernel, dim3(ctx->bfs_blocks),
+    const int minb = o.blocks_per_sm == 2 ? 2 : 3;
+    const int blocks = minb == 2 ? ctx->bfs_blocks2 : ctx->bfs_blocks;
+    const void *kern = minb == 2 ? (const void *)bfs_kernel<2> : (const void *)bfs_kernel<3>;
+    GB_CUDA(cudaLaunchCooperativeKernel(kern, dim3(blocks),
                                         dim3(BFS_THREADS), args, 0, s));
     note_launch();
     GB_CUDA(cudaFreeAsync(ws, s));

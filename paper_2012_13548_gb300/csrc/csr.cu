@@ -144,7 +144,34 @@ __global__ void __launch_bounds__(FIN_THREADS) k1_write_kernel(
     }
 }
 
+// Bit v of word v/32: row v is not empty.  One warp per word.
+__global__ void nz_bitmap_kernel(const int64_t *__restrict__ off, int64_t n,
+                                 uint32_t *__restrict__ nz, int64_t nw)
+{
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    for (int64_t w = gw; w < nw; w += stride) {
+        const int64_t v = w * 32 + lane;
+        const bool has = v < n && off[v + 1] > off[v];
+        const unsigned b = __ballot_sync(kFull, has);
+        if (lane == 0) nz[w] = b;
+    }
+}
+
 }  // namespace
+
+gb_status build_nz_bitmap(gb_graph *g, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    const int64_t nw = (g->n + 31) / 32;
+    GB_CUDA(cudaMalloc(&g->nz, nw * sizeof(uint32_t)));
+    nz_bitmap_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->off, g->n, g->nz, nw);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
+    return GB_OK;
+}
 
 gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s)
 {
@@ -161,6 +188,8 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
         GB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(int64_t)));
         GB_CUDA(cudaMalloc(&g->col, 16));
         GB_CUDA(cudaMemsetAsync(g->off, 0, (n + 1) * sizeof(int64_t), s));
+        gb_status r0 = build_nz_bitmap(g, s);
+        if (r0 != GB_OK) return r0;
         GB_CUDA(cudaStreamSynchronize(s));
         return GB_OK;
     }
@@ -210,7 +239,7 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
     GB_CUDA(cudaFreeAsync(k1, s));
     GB_CUDA(cudaFreeAsync(tcnt, s));
     GB_CUDA(cudaFreeAsync(tbase, s));
-    return GB_OK;
+    return build_nz_bitmap(g, s);
 }
 
 }  // namespace gb

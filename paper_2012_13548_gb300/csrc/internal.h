@@ -22,7 +22,8 @@ struct Context {
     int device = -1;
     int num_sms = 0;
     DevStatus *status = nullptr;  // device memory
-    int bfs_blocks = 0;           // cooperative grid of the BFS kernel
+    int bfs_blocks = 0;           // cooperative grid of the BFS kernel (3 blocks per SM)
+    int bfs_blocks2 = 0;          // the same with 2 blocks per SM
     int ms_blocks = 0;            // cooperative grid of the multi-source kernel
 };
 
@@ -79,6 +80,7 @@ struct gb_graph {
     int scale = -1;          // -1 if built from a caller CSR of arbitrary n
     int64_t *off = nullptr;  // device [n+1]
     int32_t *col = nullptr;  // device [nnz]
+    uint32_t *nz = nullptr;  // device [ceil(n/32)]: bit v set iff degree(v) >= 1
     int device = -1;
 };
 
@@ -86,6 +88,8 @@ namespace gb {
 
 // Kernel 1 pieces (csr.cu).
 gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s);
+// The degree >= 1 bitmap of a graph whose off array is in place (csr.cu).
+gb_status build_nz_bitmap(gb_graph *g, cudaStream_t s);
 
 // Kronecker generator (gen.cu).
 gb_status kron_generate_impl(int scale, int edgefactor, double a, double b, double c,
@@ -93,6 +97,7 @@ gb_status kron_generate_impl(int scale, int edgefactor, double a, double b, doub
                              int64_t *edges, cudaStream_t s);
 
 // Per-call statistics written by the BFS kernels (device layout).
+constexpr int kStatLevels = 32;
 struct BfsDevStats {
     unsigned long long nlevels;
     unsigned long long edges_examined;
@@ -100,12 +105,16 @@ struct BfsDevStats {
     unsigned long long reached;
     unsigned long long td_levels;
     unsigned long long bu_levels;
+    unsigned long long init_ns;
+    unsigned long long level_ns[kStatLevels];
+    unsigned long long level_frontier[kStatLevels];
+    int level_dir[kStatLevels];
 };
 
 // Single-source BFS (bfs.cu).
 gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level,
                    BfsDevStats *stats, cudaStream_t s);
-int bfs_pick_blocks(int num_sms);
+int bfs_pick_blocks(int num_sms, int minb);
 
 // Multi-source BFS over one graph or a batch of graphs (msbfs.cu).
 gb_status msbfs_impl(const gb_graph *g, const int64_t *roots, int k, int32_t *parents,

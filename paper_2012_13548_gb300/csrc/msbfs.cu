@@ -43,6 +43,7 @@ constexpr int SITE_MS_LEVELS = 31;
 struct MsGraph {
     const int64_t *off;
     const int32_t *col;
+    const uint32_t *nz;  // degree >= 1 bitmap
     int64_t voff;  // first global id
     int64_t n;
     int32_t *par;  // [k][n]
@@ -242,22 +243,29 @@ template <typename T>
 __device__ __forceinline__ T scan_serial(const MsGraph &G, int64_t lu, T need, const T *M,
                                          unsigned long long &edges)
 {
+    constexpr int B = 8;  // neighbours whose loads are issued together
     T found = 0;
     const int64_t s = G.off[lu], e = G.off[lu + 1];
     int64_t j = s;
-    for (; j < e; ++j) {
-        const int32_t v = G.col[j];
-        const T hit = ld_mask(&M[G.voff + v]) & need & (T)~found;
-        if (hit) {
-            write_parents(G, lu, hit, v);
-            found |= hit;
-            if (found == need) {
-                ++j;
-                break;
+    while (j < e) {
+        int32_t vv[B];
+        T mm[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) vv[t] = j + t < e ? __ldg(&G.col[j + t]) : -1;
+#pragma unroll
+        for (int t = 0; t < B; ++t) mm[t] = vv[t] >= 0 ? ld_mask(&M[G.voff + vv[t]]) : (T)0;
+#pragma unroll
+        for (int t = 0; t < B; ++t) {
+            const T hit = mm[t] & need & (T)~found;   // bits first supplied by neighbour j+t
+            if (hit) {
+                write_parents(G, lu, hit, vv[t]);
+                found |= hit;
             }
         }
+        j += B;
+        if (found == need) break;
     }
-    edges += (unsigned long long)(j - s);
+    edges += (unsigned long long)((j < e ? j : e) - s);
     return found;
 }
 
@@ -318,7 +326,15 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
         }
     }
     for (int64_t i = gtid; i < a.mstride; i += gthreads) {
-        a.seen[i] = 0;
+        // isolated vertices start fully seen: no search reaches them, and the
+        // bottom-up step skips them; their outputs stay -1
+        T s0 = 0;
+        if (i < ntot) {
+            const int g = find_graph(s_voff, a.ng, i);
+            const int64_t lu = i - s_g[g].voff;
+            if (!((s_g[g].nz[lu >> 5] >> (lu & 31)) & 1u)) s0 = all;
+        }
+        a.seen[i] = s0;
         a.mbuf[i] = 0;
         a.mbuf[a.mstride + i] = 0;
         a.mbuf[2 * a.mstride + i] = 0;
@@ -552,14 +568,18 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
         const unsigned prev = atomicAdd(&h->done, 1u);
         if (prev == gridDim.x - 1) {
             __threadfence();
-            BfsDevStats s;
+            BfsDevStats &s = *a.stats;
             s.nlevels = (unsigned long long)l;
             s.edges_examined = ldcg_u64(&h->acc[0]);
             s.vertices_touched = ldcg_u64(&h->acc[1]);
             s.reached = ldcg_u64(&h->acc[2]);
             s.td_levels = ldcg_u64(&h->acc[4]);
             s.bu_levels = ldcg_u64(&h->acc[5]);
-            *a.stats = s;
+            for (int i = 0; i < kStatLevels; ++i) {
+                s.level_ns[i] = 0;
+                s.level_frontier[i] = 0;
+                s.level_dir[i] = 0;
+            }
         }
     }
 }
@@ -633,6 +653,7 @@ gb_status msbfs_impl(const gb_graph *g, const int64_t *roots, int k, int32_t *pa
     MsGraph G;
     G.off = g->off;
     G.col = g->col;
+    G.nz = g->nz;
     G.voff = 0;
     G.n = g->n;
     G.par = parents;
@@ -650,6 +671,7 @@ gb_status multigraph_impl(const gb_graph *const *gs, int ng, const int64_t *root
     for (int i = 0; i < ng; ++i) {
         v[i].off = gs[i]->off;
         v[i].col = gs[i]->col;
+        v[i].nz = gs[i]->nz;
         v[i].voff = 0;
         v[i].n = gs[i]->n;
         v[i].par = parents[i];

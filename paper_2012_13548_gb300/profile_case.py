@@ -22,9 +22,19 @@ def main():
     p.add_argument("--scale", type=int, default=22)
     p.add_argument("--roots", type=int, default=3)
     p.add_argument("--canonical", type=int, default=0)
+    p.add_argument("--alpha", type=float, default=None)
+    p.add_argument("--beta", type=float, default=None)
+    p.add_argument("--blocks-per-sm", type=int, default=None)
     a = p.parse_args()
     spec = W.GraphSpec(scale=a.scale)
-    gb.bfs_set_options(canonical_parents=a.canonical)
+    opts = dict(canonical_parents=a.canonical)
+    if a.alpha is not None:
+        opts["alpha"] = a.alpha
+    if a.beta is not None:
+        opts["beta"] = a.beta
+    if a.blocks_per_sm is not None:
+        opts["blocks_per_sm"] = a.blocks_per_sm
+    gb.bfs_set_options(**opts)
     edges = gb.kron_generate(**spec.kron_args())
     g = gb.graph_build_csr(edges, a.scale)
     off, _ = g.csr()
@@ -38,6 +48,9 @@ def main():
             print("root %d levels %d reached %d edges_examined %d td %d bu %d" % (
                 r, st["nlevels"], st["reached"], st["edges_examined"], st["td_levels"],
                 st["bu_levels"]))
+            print("  per level (us, frontier, step):", [
+                ("%.1f" % (t / 1e3), f, d) for t, f, d in
+                zip(st["level_ns"], st["level_frontier"], st["level_dir"])])
     elif a.kernel == "msbfs":
         P = torch.empty((len(roots), g.n), dtype=torch.int32, device="cuda")
         L = torch.empty((len(roots), g.n), dtype=torch.int32, device="cuda")

@@ -24,7 +24,7 @@ from tests.golden import load_hand_graphs  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 DEFAULTS = dict(canonical_parents=0, alpha=14.0, beta=24.0, big_degree=256, ms_alpha=16.0,
-                ms_beta=32.0, timeout_ms=5000.0)
+                ms_beta=32.0, timeout_ms=5000.0, blocks_per_sm=2)
 
 
 @pytest.fixture(autouse=True)
@@ -167,6 +167,7 @@ SWITCHES = {
     "bottom_up_early": dict(alpha=1e9, beta=1e9),
     "flip_flop": dict(alpha=1e9, beta=1e-9),
     "tiny_big_degree": dict(big_degree=1),
+    "three_blocks_per_sm": dict(blocks_per_sm=3),
 }
 
 
