@@ -188,6 +188,30 @@ gb_status bfs_batch(const gb_graph *g, const int64_t *roots, int k, int32_t *par
 gb_status bfs_multi_graph(const gb_graph *const *gs, int ng, const int64_t *roots, int r,
                           int32_t *const *parents, int32_t *const *levels, gb_stream s);
 
+/* Allocation-free single-source BFS (no counterpart in the paper: it exists
+ * for callers that may not allocate device memory).  Some callers cannot call
+ * cudaMalloc or cudaMallocAsync: a framework whose own allocator has reserved
+ * the device's memory, a real-time or embedded host loop that must not stall
+ * on the allocator, or code running where allocation is not allowed.  This
+ * entry point runs the same kernel as bfs() but keeps every temporary in one
+ * file-scope device array built into the library (about 13 MB, held on every
+ * GPU that loads the library until the process exits), so it never allocates.
+ *   off, col   caller's CSR in device memory: off int64 [n+1], col int32
+ *              [nnz], rows sorted ascending, symmetric, no self-loops
+ *   parent, level  caller's device int32 [n] outputs, as for bfs()
+ *   s          the stream it runs on; the call synchronises `s` before it
+ *              returns and reports a device-side timeout as GB_ERR_TIMEOUT
+ * Limits and rules: n <= 2^20 (1,048,576) vertices, else GB_ERR_RANGE with
+ * no work done.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and the grid size; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (the header and status word are cleared by each call):
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must not be issued.  Options come from bfs_set_options; bfs_last_stats
+ * does not see these calls. */
+gb_status bfs_noalloc(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
+                      int64_t root, int32_t *parent, int32_t *level, gb_stream s);
+
 /* Counters of the last bfs/bfs_batch/bfs_multi_graph call on this thread;
  * synchronises the stream of that call.
  *   nlevels          number of BFS levels (max level + 1)

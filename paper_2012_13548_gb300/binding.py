@@ -80,6 +80,7 @@ def lib():
                                                ctypes.POINTER(_i64), ctypes.c_int,
                                                ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
             "bfs_last_stats": (ctypes.c_int, [ctypes.POINTER(gb_bfs_stats)]),
+            "bfs_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp]),
             "server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t,
                                              ctypes.POINTER(_vp)]),
             "server_submit": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.POINTER(_i64)]),
@@ -101,7 +102,7 @@ def exported_symbols():
     return ["gb_last_error", "gb_abi_version", "gb_kernel_launches", "gb_device_status", "kron_generate",
             "graph_build_csr", "graph_from_csr", "graph_free", "graph_info", "graph_csr_view",
             "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
-            "bfs_last_stats", "server_create", "server_submit", "server_poll", "server_release",
+            "bfs_last_stats", "bfs_noalloc", "server_create", "server_submit", "server_poll", "server_release",
             "server_run_trace", "server_destroy"]
 
 
@@ -278,6 +279,23 @@ def bfs_multi_graph(graphs, roots, parents=None, levels=None, stream=None):
     ll = (_vp * ng)(*[_dev(x, torch.int32, "levels").value for x in levels])
     _check(lib().bfs_multi_graph(gh, ng, rr, r, pp, ll, _stream(stream)))
     return parents, levels
+
+
+def bfs_noalloc(off, col, root, parent, level, stream=None):
+    """Allocation-free single-source BFS into caller tensors parent/level (int32 [n]).
+
+    For callers that must not allocate device memory: the library keeps this
+    call's temporaries in a fixed built-in device array, so graphs are limited
+    to 2^20 vertices.  off/col are a CSR in CUDA tensors (int64 [n+1], int32
+    [nnz]); the call synchronises the stream.  Nothing here allocates."""
+    n = off.numel() - 1
+    if parent.numel() != n or level.numel() != n:
+        raise ValueError("outputs must have n = %d entries" % n)
+    _check(lib().bfs_noalloc(_dev(off, torch.int64, "off"),
+                             _dev(col, torch.int32, "col") if col.numel() else ctypes.c_void_p(None),
+                             n, col.numel(), int(root), _dev(parent, torch.int32, "parent"),
+                             _dev(level, torch.int32, "level"), _stream(stream)))
+    return parent, level
 
 
 def bfs_last_stats():

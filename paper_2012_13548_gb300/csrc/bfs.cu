@@ -34,6 +34,8 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 namespace gb {
 namespace {
@@ -617,3 +619,157 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
 }
 
 }  // namespace gb
+
+// ---------------------------------------------------------------------------
+// bfs_noalloc: the single-source BFS kernel above, for callers that cannot
+// allocate device memory.  Its scratch lives in one file-scope device array
+// sized for graphs of up to 2^20 vertices; nothing here calls cudaMalloc,
+// cudaMallocAsync or cudaFree.
+// ---------------------------------------------------------------------------
+namespace gb {
+namespace {
+
+constexpr int64_t kNaMaxN = int64_t(1) << 20;      // largest graph (vertices)
+constexpr int64_t kNaWords = kNaMaxN / 32;
+constexpr int64_t kNaBigCap = kNaMaxN + 2;         // a vertex enters the big list at most once
+constexpr size_t kNaHdr = 0;
+constexpr size_t kNaVis = 1024;
+constexpr size_t kNaFb = kNaVis + kNaWords * 4;
+constexpr size_t kNaNz = kNaFb + 4 * kNaWords * 4;
+constexpr size_t kNaQueue = kNaNz + kNaWords * 4;
+constexpr size_t kNaBig = kNaQueue + kNaMaxN * 4;
+constexpr size_t kNaStatus = kNaBig + kNaBigCap * sizeof(BigEnt);
+constexpr size_t kNaStats = kNaStatus + 256;
+constexpr size_t kNaBytes = kNaStats + ((sizeof(BfsDevStats) + 255) & ~size_t(255));
+static_assert(sizeof(WsHeader) <= kNaVis - kNaHdr, "header region too small");
+static_assert(sizeof(DevStatus) <= 256, "status region too small");
+
+// Shared by every call on a device; the last call's contents stay behind.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Bit v of word v/32: row v is not empty (computed into the scratch).
+__global__ void na_nz_kernel(const int64_t *__restrict__ off, int64_t n, uint32_t *__restrict__ nz,
+                             int64_t nw)
+{
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    for (int64_t w = gw; w < nw; w += stride) {
+        const int64_t v = w * 32 + lane;
+        const bool has = v < n && off[v + 1] > off[v];
+        const unsigned b = __ballot_sync(kFull, has);
+        if (lane == 0) nz[w] = b;
+    }
+}
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch
+    int num_sms = 0;
+    int blocks = 0;
+};
+std::mutex g_na_mu;
+NoAllocDevice g_na[64];
+
+}  // namespace
+
+gb_status bfs_noalloc_impl(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
+                           int64_t root, int32_t *parent, int32_t *level, cudaStream_t s)
+{
+    if (!off || !parent || !level || (nnz > 0 && !col) || n < 1 || nnz < 0) {
+        set_error("bfs_noalloc: need off, parent, level (and col when nnz > 0), n >= 1");
+        return GB_ERR_INVALID;
+    }
+    if (n > kNaMaxN) {
+        set_error("bfs_noalloc: the graph has more than 2^20 vertices, the size of the "
+                  "built-in scratch; use bfs() instead");
+        return GB_ERR_RANGE;
+    }
+    if (root < 0 || root >= n) {
+        set_error("bfs_noalloc: root outside [0, n)");
+        return GB_ERR_RANGE;
+    }
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("bfs_noalloc: device index above 63");
+        return GB_ERR_INVALID;
+    }
+    NoAllocDevice d;
+    {
+        // One-time set-up per device, with that device current: the device
+        // address of the scratch array and the cooperative grid size.
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (!g_na[dev].ready) {
+            NoAllocDevice nd;
+            GB_CUDA(cudaGetSymbolAddress((void **)&nd.scratch, g_noalloc_scratch));
+            GB_CUDA(cudaDeviceGetAttribute(&nd.num_sms, cudaDevAttrMultiProcessorCount, dev));
+            int per_sm = 0;
+            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_kernel<2>,
+                                                                  BFS_THREADS, 0));
+            nd.blocks = nd.num_sms * std::max(1, std::min(per_sm, 2));
+            nd.ready = true;
+            g_na[dev] = nd;
+        }
+        d = g_na[dev];
+    }
+    const gb_bfs_options &o = options();
+    const int64_t nw = (n + 31) / 32;
+    unsigned char *ws = d.scratch;
+    // The header (barrier, level counters) and the status word must start at zero.
+    GB_CUDA(cudaMemsetAsync(ws + kNaHdr, 0, sizeof(WsHeader), s));
+    GB_CUDA(cudaMemsetAsync(ws + kNaStatus, 0, sizeof(DevStatus), s));
+    na_nz_kernel<<<d.num_sms * 4, 256, 0, s>>>(off, n, reinterpret_cast<uint32_t *>(ws + kNaNz), nw);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
+    BfsArgs a;
+    a.off = off;
+    a.col = col;
+    a.nz = reinterpret_cast<const uint32_t *>(ws + kNaNz);
+    a.n = n;
+    a.nnz = nnz;
+    a.root = (int32_t)root;
+    a.parent = parent;
+    a.level = level;
+    a.hdr = reinterpret_cast<WsHeader *>(ws + kNaHdr);
+    a.vis = reinterpret_cast<unsigned *>(ws + kNaVis);
+    a.fb = reinterpret_cast<unsigned *>(ws + kNaFb);
+    a.nw = nw;
+    a.queue = reinterpret_cast<int32_t *>(ws + kNaQueue);
+    a.bigq = reinterpret_cast<BigEnt *>(ws + kNaBig);
+    a.bigcap = kNaBigCap;
+    a.st = reinterpret_cast<DevStatus *>(ws + kNaStatus);
+    a.stats = reinterpret_cast<BfsDevStats *>(ws + kNaStats);
+    a.alpha = (float)o.alpha;
+    a.beta = (float)o.beta;
+    a.big_deg = std::max(o.big_degree, 1);
+    a.canonical = o.canonical_parents;
+    a.timeout_ns = timeout_ns();
+    void *args[] = {&a};
+    GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfs_kernel<2>, dim3(d.blocks),
+                                        dim3(BFS_THREADS), args, 0, s));
+    note_launch();
+    DevStatus hst;
+    GB_CUDA(cudaMemcpyAsync(&hst, ws + kNaStatus, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (hst.code != 0) {
+        set_error("bfs_noalloc: device status " + std::to_string(hst.code) + " at site " +
+                  std::to_string(hst.where));
+        return (gb_status)hst.code;
+    }
+    return GB_OK;
+}
+
+}  // namespace gb
+
+extern "C" gb_status bfs_noalloc(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
+                                 int64_t root, int32_t *parent, int32_t *level, gb_stream s)
+{
+    try {
+        return gb::bfs_noalloc_impl(off, col, n, nnz, root, parent, level,
+                                    reinterpret_cast<cudaStream_t>(s));
+    } catch (...) {
+        gb::set_error("bfs_noalloc: internal error");
+        return GB_ERR_INVALID;
+    }
+}
