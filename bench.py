@@ -44,7 +44,9 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="s20", choices=["s20", "s26", "s22ms"])
+    p.add_argument("--workload", default="s20", choices=["s20", "s26", "s22ms", "serve6"])
+    p.add_argument("--duration", type=float, default=3.0, help="serve6: seconds of arrivals")
+    p.add_argument("--rate", type=float, default=None, help="serve6: arrivals per second")
     p.add_argument("--roots", type=int, default=64)
     p.add_argument("--canonical", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -447,12 +449,115 @@ def run_e2e(args, gb, torch, edges, scale, roots, m_r, dist):
             "d2h_bytes_per_step": int(k * 2 * n * 4)}
 
 
+# ---------------------------------------------------------------------------
+# Serving workload: resident graphs, open-loop Poisson arrivals
+# ---------------------------------------------------------------------------
+
+def run_serve(args, dist):
+    import torch
+    import paper_2012_13548_gb300 as gb
+
+    torch.cuda.set_device(dist.local)
+    wl = W.WORKLOADS["serve6"]
+    rate = args.rate or wl["rate"]
+    graphs, edges, offs = [], [], []
+    for sc in wl["scales"]:
+        spec = W.GraphSpec(scale=sc)
+        e = gb.kron_generate(**spec.kron_args())
+        g = gb.graph_build_csr(e, sc)
+        graphs.append(g)
+        edges.append(e)
+        offs.append(g.csr()[0].cpu().numpy())
+    t, gid, draw = W.poisson_trace(rate, args.duration, len(graphs), seed=W.SEED_ARRIVAL + dist.rank)
+    roots = np.empty(t.size, dtype=np.int64)
+    for gi in range(len(graphs)):
+        sel = gid == gi
+        roots[sel] = W.root_from_draw(offs[gi], draw[sel])
+
+    # TEPS numerators: every root of the giant component reaches the same set
+    m_of = {}
+    reach = []
+    for gi, g in enumerate(graphs):
+        r0 = int(W.select_roots(offs[gi], 1, W.GraphSpec(scale=wl["scales"][gi]).seeds()[3])[0])
+        _, lev = gb.bfs(g, r0)
+        reach.append((lev >= 0).cpu().numpy())
+        m_of[(gi, -1)] = int((lev[edges[gi][0]] >= 0).sum().item())
+
+    def m_r(gi, r):
+        if reach[gi][r]:
+            return m_of[(gi, -1)]
+        if (gi, r) not in m_of:
+            _, lev = gb.bfs(graphs[gi], int(r))
+            m_of[(gi, r)] = int((lev[edges[gi][0]] >= 0).sum().item())
+        return m_of[(gi, r)]
+
+    total_m = sum(m_r(int(g), int(r)) for g, r in zip(gid, roots))
+    budget = 64 << 30
+
+    # warm-up on a short prefix, then the timed trace
+    srv = gb.Server(graphs, mem_budget=budget)
+    k = min(t.size, 200)
+    srv.run_trace(t[:k] - t[0], gid[:k], roots[:k])
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    launches0 = gb.gb_kernel_launches()
+    w0 = time.perf_counter()
+    lat = srv.run_trace(t, gid, roots)
+    wall = time.perf_counter() - w0
+    launches = gb.gb_kernel_launches() - launches0
+    clk = clocks.stop()
+    srv.close()
+    gb.gb_device_status()
+
+    # the same stream through the plain per-query path: one bfs() at a time, FIFO
+    par = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    lvl = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    for i in range(min(50, t.size)):
+        gb.bfs(graphs[int(gid[i])], int(roots[i]), par[int(gid[i])], lvl[int(gid[i])])
+    torch.cuda.synchronize()
+    plain = np.zeros(t.size)
+    p0 = time.perf_counter()
+    for i in range(t.size):
+        due = p0 + t[i]
+        while time.perf_counter() < due:
+            pass
+        gi = int(gid[i])
+        gb.bfs(graphs[gi], int(roots[i]), par[gi], lvl[gi])
+        torch.cuda.current_stream().synchronize()
+        plain[i] = (time.perf_counter() - due) * 1e3
+    plain_wall = time.perf_counter() - p0
+
+    if dist.rank == 0:
+        line = {"metric": METRIC, "value": total_m / wall / 1e9, "unit": "GTEPS",
+                "n_gpus": dist.world, "steps": 1, "warmup": 1,
+                "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "serving-6-resident-kronecker-graphs-scale14-24-poisson",
+                           "scales": list(wl["scales"]), "rate_per_s": rate,
+                           "duration_s": args.duration, "queries": int(t.size),
+                           "batch": "up to 64 queries per graph per launch, admitted per level",
+                           "mem_budget_bytes": budget},
+                "serving": {"p50_ms": float(np.percentile(lat, 50)),
+                            "p99_ms": float(np.percentile(lat, 99)),
+                            "qps": t.size / wall, "gteps": total_m / wall / 1e9,
+                            "wall_s": wall},
+                "plain_per_query": {"p50_ms": float(np.percentile(plain, 50)),
+                                    "p99_ms": float(np.percentile(plain, 99)),
+                                    "qps": t.size / plain_wall,
+                                    "gteps": total_m / plain_wall / 1e9, "wall_s": plain_wall},
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line))
+
+
 def main():
     args = parse_args()
     dist = Dist("cpu" if args.impl == "reference" else "cuda")
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.workload == "serve6":
+            run_serve(args, dist)
         else:
             run_ours(args, dist)
     finally:

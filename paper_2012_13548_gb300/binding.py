@@ -308,3 +308,77 @@ def bfs_last_stats():
     out["level_frontier"] = list(s.level_frontier)[:k]
     out["level_dir"] = ["td" if d == 1 else "bu" if d == 2 else "-" for d in list(s.level_dir)[:k]]
     return out
+
+
+class Server:
+    """Continuous-batching BFS server over resident graphs (C ABI server_*).
+
+    Queries are admitted at BFS level boundaries into one of 64 bit-slots per
+    graph while their output buffers fit in `mem_budget` bytes; finished
+    queries are retired at the next boundary."""
+
+    def __init__(self, graphs, mem_budget):
+        self.graphs = list(graphs)
+        arr = (_vp * len(self.graphs))(*[g.handle.value for g in self.graphs])
+        h = _vp()
+        _check(lib().server_create(arr, len(self.graphs), int(mem_budget), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, graph_id, root):
+        t = _i64()
+        _check(lib().server_submit(self._h, int(graph_id), int(root), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        """(parent, level) borrowed int32 CUDA tensors once done, else None."""
+        p, l = _vp(), _vp()
+        rc = lib().server_poll(self._h, int(ticket), ctypes.byref(p), ctypes.byref(l))
+        if rc == GB_ERR_BUSY:
+            return None
+        _check(rc)
+        return p.value, l.value
+
+    def result(self, ticket, graph_id, timeout_s=60.0):
+        """Wait for a query and return copies of its (parent, level) tensors."""
+        import time
+        t0 = time.time()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                break
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError("query %d not finished" % ticket)
+            time.sleep(1e-4)
+        n = self.graphs[graph_id].n
+        dev = "cuda:%d" % torch.cuda.current_device()
+        par = torch.as_tensor(_DevArray(r[0], (n,), "<i4", self), device=dev).clone()
+        lev = torch.as_tensor(_DevArray(r[1], (n,), "<i4", self), device=dev).clone()
+        return par, lev
+
+    def release(self, ticket):
+        _check(lib().server_release(self._h, int(ticket)))
+
+    def run_trace(self, t_arrival_s, graph_id, roots, keep_results=False):
+        """Replay an open-loop trace; returns arrival-to-done latencies in ms."""
+        import numpy as np
+        t = np.ascontiguousarray(t_arrival_s, dtype=np.float64)
+        gid = np.ascontiguousarray(graph_id, dtype=np.int32)
+        rr = np.ascontiguousarray(roots, dtype=np.int64)
+        lat = np.zeros(t.size, dtype=np.float64)
+        _check(lib().server_run_trace(self._h, t.size, ctypes.c_void_p(t.ctypes.data),
+                                      ctypes.c_void_p(gid.ctypes.data), ctypes.c_void_p(rr.ctypes.data),
+                                      1 if keep_results else 0, ctypes.c_void_p(lat.ctypes.data)))
+        return lat
+
+    def close(self):
+        if self._h:
+            _check(lib().server_destroy(self._h))
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.server_destroy(self._h)
+        except Exception:
+            pass
+

@@ -124,6 +124,31 @@ gb_status multigraph_impl(const gb_graph *const *gs, int ng, const int64_t *root
                           BfsDevStats *stats, cudaStream_t s);
 int msbfs_pick_blocks(int num_sms);
 
+// Serving (msbfs.cu): one multi-source search state per resident graph, run
+// one level per launch with up to 64 queries as bits.
+struct MsCtl {
+    unsigned long long na;      // active vertices appended for the level
+    unsigned long long mf;      // their degree sum
+    unsigned long long big;     // (count << 32) | chunks of the big ones
+    unsigned long long anynew;  // OR of the bits that reached new vertices
+};
+struct MsSlots {              // per-bit outputs and start levels
+    int32_t *par[64];
+    int32_t *lev[64];
+    int32_t start[64];
+};
+struct MsServe;
+gb_status ms_serve_create(const gb_graph *g, int blocks, MsServe **out, cudaStream_t s);
+void ms_serve_destroy(MsServe *m);
+// Place `count` new queries (bit, root) into the frontier of `level` (the next
+// level to run); `table` is the full slot table to upload.
+gb_status ms_serve_admit(MsServe *m, int level, int count, const int *bits, const int64_t *roots,
+                         const MsSlots *table, cudaStream_t s);
+// Run `level` for the bits in `active`; the next level's control record is
+// copied to host_ctl (pinned) on the same stream.
+gb_status ms_serve_step(MsServe *m, int level, unsigned long long active, MsCtl *host_ctl,
+                        cudaStream_t s);
+
 // Last-call statistics bookkeeping (api.cpp).
 void note_stats_call(BfsDevStats *dev_stats, cudaStream_t s);
 BfsDevStats *stats_buffer();

@@ -24,6 +24,12 @@
 // per-graph offsets, every graph's roots use the low bits, and since the
 // graphs share no edges their searches cannot mix.  Masks are uint64 for up
 // to 64 roots of one graph and uint8 for up to 8 roots per graph of a batch.
+//
+// Serving runs the same kernel one level per launch on a resident graph: the
+// search state stays in a per-graph workspace between launches, queries take
+// free bits at level boundaries (a per-slot table gives each bit its own
+// output buffers and the level it started at), and the kernel reports which
+// bits still advance so the host can retire finished queries.
 #include "common.cuh"
 #include "internal.h"
 
@@ -37,6 +43,9 @@ constexpr int MS_THREADS = 512;
 constexpr int MS_MAXG = 64;
 constexpr int MS_BIG_CHUNK = 256;
 constexpr int MS_BIG_DEG = 256;
+constexpr int MS_WARPS = MS_THREADS / 32;
+constexpr int MS_QBUF = 256;  // per-warp staging of newly active vertices
+constexpr int MS_BBUF = 32;   // per-warp staging of newly active big vertices
 constexpr int SITE_MS_BAR = 30;
 constexpr int SITE_MS_LEVELS = 31;
 
@@ -50,12 +59,7 @@ struct MsGraph {
     int32_t *lev;  // [k][n]
 };
 
-struct MsCtl {
-    unsigned long long na;   // active vertices appended
-    unsigned long long mf;   // their degree sum
-    unsigned long long big;  // (count << 32) | chunks
-    unsigned long long pad;
-};
+}  // namespace
 
 struct MsHeader {
     GridBarrier bar;
@@ -63,7 +67,10 @@ struct MsHeader {
     unsigned pad0;
     MsCtl ctl[3];
     unsigned long long acc[6];
+    unsigned long long na_hist[4];  // active-list length of each level (ring)
 };
+
+namespace {
 
 template <typename T>
 struct MsArgs {
@@ -81,10 +88,15 @@ struct MsArgs {
     int64_t bigcap;
     MsHeader *hdr;
     DevStatus *st;
-    BfsDevStats *stats;
+    BfsDevStats *stats;     // nullptr: no statistics (serving)
     float ms_alpha;
     float ms_beta;
     uint64_t timeout_ns;
+    int l0;                 // first level to run
+    int max_levels;         // levels to run in this launch, 0 = until the frontier is empty
+    int do_init;            // 1: clear state and place the roots first (batch calls)
+    unsigned long long active;  // serving: bits in use; ignored when do_init
+    const MsSlots *slots;   // serving: per-bit outputs; nullptr = graph outputs [k][n]
 };
 
 template <typename T>
@@ -170,54 +182,108 @@ __device__ __forceinline__ int find_graph(const int64_t *s_voff, int ng, int64_t
 }
 
 template <typename T>
-__device__ __forceinline__ void write_parents(const MsGraph &G, int64_t local, T bits, int32_t p)
+__device__ __forceinline__ void write_parents(const MsGraph &G, const MsSlots *S, int64_t local,
+                                              T bits, int32_t p)
 {
     while (bits) {
         const int b = __ffsll((unsigned long long)bits) - 1;
         bits &= bits - 1;
-        G.par[(int64_t)b * G.n + local] = p;
+        if (S) S->par[b][local] = p;
+        else G.par[(int64_t)b * G.n + local] = p;
     }
 }
 
+// lvl = the global level number; a serving slot stores it relative to its start
 template <typename T>
-__device__ __forceinline__ void write_levels(const MsGraph &G, int64_t local, T bits, int32_t l)
+__device__ __forceinline__ void write_levels(const MsGraph &G, const MsSlots *S, int64_t local,
+                                             T bits, int32_t lvl)
 {
     while (bits) {
         const int b = __ffsll((unsigned long long)bits) - 1;
         bits &= bits - 1;
-        G.lev[(int64_t)b * G.n + local] = l;
+        if (S) S->lev[b][local] = lvl - S->start[b];
+        else G.lev[(int64_t)b * G.n + local] = lvl;
     }
 }
 
-// Warp-collective append of `gid` (lanes with `on`) to the next active list.
-template <typename T>
-__device__ __forceinline__ void ms_append(bool on, int64_t gid, int64_t deg, const MsArgs<T> &a,
-                                          MsCtl *nxt, int32_t *act_next, int64_t bnext_base)
+// Newly active vertices are staged per warp in shared memory and moved to the
+// next active list with one atomic per flush; the fill levels qn/bn are
+// warp-uniform registers (every lane adds the same ballot counts).
+struct MsWarpBuf {
+    int32_t q[MS_QBUF];
+    unsigned long long b[MS_BBUF];  // gid | nchunks << 32
+};
+
+// Warp-collective: move the staged vertices to the next active list.
+__device__ __forceinline__ void ms_flush_q(MsWarpBuf &wb, int &qn, MsCtl *nxt, int32_t *act_next)
+{
+    if (qn == 0) return;
+    __syncwarp();
+    const unsigned lane = lane_id();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&nxt->na, (unsigned long long)qn);
+    base = __shfl_sync(kFull, base, 0);
+    for (int i = lane; i < qn; i += 32) __stcg(&act_next[base + i], wb.q[i]);
+    __syncwarp();
+    qn = 0;
+}
+
+// Warp-collective: chunk ranges for the staged big vertices.
+__device__ __forceinline__ void ms_flush_b(MsWarpBuf &wb, int &bn, MsCtl *nxt,
+                                           unsigned long long *bigq_next)
+{
+    if (bn == 0) return;
+    __syncwarp();
+    const unsigned lane = lane_id();
+    const unsigned long long e = (int)lane < bn ? wb.b[lane] : 0ull;
+    const unsigned nch = (unsigned)(e >> 32);
+    const unsigned incl = warp_inclusive_scan(nch);
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    unsigned long long p = 0;
+    if (lane == 0) p = atomicAdd(&nxt->big, ((unsigned long long)bn << 32) | total);
+    p = __shfl_sync(kFull, p, 0);
+    if ((int)lane < bn) {
+        const unsigned long long cb = (p & 0xffffffffull) + incl - nch;
+        __stcg(&bigq_next[(int64_t)(p >> 32) + lane], (e & 0xffffffffull) | (cb << 32));
+    }
+    __syncwarp();
+    bn = 0;
+}
+
+// Warp-collective: the lanes with `on` join the next active list.
+__device__ __forceinline__ void ms_append(bool on, int64_t gid, int64_t deg, MsWarpBuf &wb,
+                                          int &qn, int &bn, unsigned long long &my_mf, MsCtl *nxt,
+                                          int32_t *act_next, unsigned long long *bigq_next)
 {
     const unsigned bal = __ballot_sync(kFull, on);
     if (!bal) return;
-    const int leader = __ffs(bal) - 1;
-    unsigned long long base = 0;
-    if ((int)lane_id() == leader) base = atomicAdd(&nxt->na, (unsigned long long)__popc(bal));
-    base = __shfl_sync(kFull, base, leader);
-    const unsigned long long dsum = warp_sum((unsigned long long)(on ? deg : 0));
+    const int cnt = __popc(bal);
+    if (qn + cnt > MS_QBUF) ms_flush_q(wb, qn, nxt, act_next);
     if (on) {
-        __stcg(&act_next[base + __popc(bal & lanemask_lt())], (int32_t)gid);
-        if (deg > MS_BIG_DEG) {
-            const unsigned long long p = atomicAdd(
-                &nxt->big, (1ull << 32) | (unsigned long long)((deg + MS_BIG_CHUNK - 1) / MS_BIG_CHUNK));
-            __stcg(&a.bigq[bnext_base + (int64_t)(p >> 32)],
-                   (unsigned long long)(uint32_t)gid | ((p & 0xffffffffull) << 32));
-        }
+        wb.q[qn + __popc(bal & lanemask_lt())] = (int32_t)gid;
+        my_mf += (unsigned long long)deg;
     }
-    if ((int)lane_id() == leader) atomicAdd(&nxt->mf, dsum);
+    qn += cnt;
+    const bool big = on && deg > MS_BIG_DEG;
+    const unsigned bb = __ballot_sync(kFull, big);
+    if (bb) {
+        const int bc = __popc(bb);
+        if (bn + bc > MS_BBUF) ms_flush_b(wb, bn, nxt, bigq_next);
+        if (big)
+            wb.b[bn + __popc(bb & lanemask_lt())] =
+                (unsigned long long)(uint32_t)gid |
+                ((unsigned long long)((deg + MS_BIG_CHUNK - 1) / MS_BIG_CHUNK) << 32);
+        bn += bc;
+    }
 }
 
 // Top-down expansion of one edge (gv -> gu) carrying frontier bits f.
 template <typename T>
 __device__ __forceinline__ void ms_td_edge(bool valid, T f, int64_t gu, const MsArgs<T> &a, T *Mn,
-                                           const MsGraph *s_g, const int64_t *s_voff, MsCtl *nxt,
-                                           int32_t *act_next, int64_t bnext_base)
+                                           const MsGraph *s_g, const int64_t *s_voff, MsWarpBuf &wb,
+                                           int &qn, int &bn, unsigned long long &my_mf,
+                                           MsCtl *nxt, int32_t *act_next,
+                                           unsigned long long *bigq_next)
 {
     bool first = false;
     int64_t deg = 0;
@@ -233,65 +299,90 @@ __device__ __forceinline__ void ms_td_edge(bool valid, T f, int64_t gu, const Ms
             }
         }
     }
-    ms_append(first, gu, deg, a, nxt, act_next, bnext_base);
+    ms_append(first, gu, deg, wb, qn, bn, my_mf, nxt, act_next, bigq_next);
 }
 
-// Scan the adjacency list of global vertex gu (graph g, local lu) for the
-// bits `need`, crediting each bit to its first neighbour in M.  Serial for one
-// lane.  Returns the bits found; writes parents.
+// Rows of a warp (lane i owns one row: graph g, local id lu, adjacency
+// [s, e), missing bits `need`) are scanned together.  Each round deals 4 x 32
+// neighbour slots, an equal share to every row still missing bits, so a row
+// that completes early stops taking slots; the loads of a round are issued
+// together.  Slots are processed in neighbour order: a segmented prefix-OR
+// over the slots of each row credits every bit to the first neighbour that
+// carries it in M, which is the smallest-id parent.  Returns the bits found
+// for this lane's row (parents written).
 template <typename T>
-__device__ __forceinline__ T scan_serial(const MsGraph &G, int64_t lu, T need, const T *M,
-                                         unsigned long long &edges)
+__device__ __forceinline__ T ms_rows(const MsGraph *s_g, const MsSlots *S, const T *M, int g,
+                                     int64_t lu, int64_t s, int64_t e, T need,
+                                     unsigned long long &edges)
 {
-    constexpr int B = 8;  // neighbours whose loads are issued together
+    constexpr int E = 4;
+    constexpr int SLOTS = 32 * E;
+    const int lane = (int)lane_id();
     T found = 0;
-    const int64_t s = G.off[lu], e = G.off[lu + 1];
-    int64_t j = s;
-    while (j < e) {
-        int32_t vv[B];
-        T mm[B];
+    int64_t pos = s;
+    while (true) {
+        const bool act = need != 0 && found != need && pos < e;
+        const unsigned am = __ballot_sync(kFull, act);
+        if (!am) break;
+        const int q = SLOTS / __popc(am);
+        const int64_t rem = act ? e - pos : 0;
+        const int len = (int)(rem < q ? rem : q);
+        const int incl = warp_inclusive_scan(len);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - len;
+        int own[E];
+        int32_t vv[E];
+        T mm[E];
 #pragma unroll
-        for (int t = 0; t < B; ++t) vv[t] = j + t < e ? __ldg(&G.col[j + t]) : -1;
+        for (int t = 0; t < E; ++t) {
+            const int k = t * 32 + lane;
+            int o = 0;
 #pragma unroll
-        for (int t = 0; t < B; ++t) mm[t] = vv[t] >= 0 ? ld_mask(&M[G.voff + vv[t]]) : (T)0;
-#pragma unroll
-        for (int t = 0; t < B; ++t) {
-            const T hit = mm[t] & need & (T)~found;   // bits first supplied by neighbour j+t
-            if (hit) {
-                write_parents(G, lu, hit, vv[t]);
-                found |= hit;
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int c = o + step;
+                if (__shfl_sync(kFull, excl, c) <= k) o = c;
             }
+            own[t] = o;
+            const int64_t po = __shfl_sync(kFull, pos, o);
+            const int eo = __shfl_sync(kFull, excl, o);
+            const int go = __shfl_sync(kFull, g, o);
+            vv[t] = k < total ? __ldg(&s_g[go].col[po + (k - eo)]) : -1;
         }
-        j += B;
-        if (found == need) break;
-    }
-    edges += (unsigned long long)((j < e ? j : e) - s);
-    return found;
-}
-
-// The same scan with the whole warp on one row (all lanes call it with the
-// same arguments).  Returns the bits found (same in all lanes).
-template <typename T>
-__device__ __forceinline__ T scan_warp(const MsGraph &G, int64_t lu, T need, const T *M,
-                                       unsigned long long &edges)
-{
-    const unsigned lane = lane_id();
-    T found = 0;
-    const int64_t s = G.off[lu], e = G.off[lu + 1];
-    for (int64_t b = s; b < e; b += 32) {
-        const int64_t j = b + lane;
-        int32_t v = 0;
-        T hit = 0;
-        if (j < e) {
-            v = G.col[j];
-            hit = ld_mask(&M[G.voff + v]) & need & (T)~found;
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int go = __shfl_sync(kFull, g, own[t]);
+            mm[t] = vv[t] >= 0 ? ld_mask(&M[s_g[go].voff + vv[t]]) : (T)0;
         }
-        const T before = warp_exclusive_or(hit);
-        const T mine = hit & (T)~before;
-        if (mine) write_parents(G, lu, mine, v);
-        found |= warp_or(hit);
-        if (lane == 0) edges += (unsigned long long)(e - b < 32 ? e - b : 32);
-        if (found == need) break;
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int o = own[t];
+            const T need_o = shfl_mask(need, o);
+            const T found_o = shfl_mask(found, o);
+            const T h = mm[t] & need_o & (T)~found_o;
+            // inclusive OR over the earlier slots of the same row in this group
+            int seg0 = __shfl_sync(kFull, excl, o) - t * 32;
+            seg0 = seg0 > 0 ? seg0 : 0;
+            T x = h;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const T y = shfl_up_mask(x, d);
+                if (lane - d >= seg0) x |= y;
+            }
+            const T y1 = shfl_up_mask(x, 1);
+            const T before = lane > seg0 ? y1 : (T)0;
+            const T mine = h & (T)~before;
+            const int go = __shfl_sync(kFull, g, o);
+            const int64_t luo = __shfl_sync(kFull, lu, o);
+            if (mine) write_parents(s_g[go], S, luo, mine, vv[t]);
+            // each row collects the OR of its slots in this group (its last slot)
+            const int a0 = excl - t * 32, a1 = excl + len - t * 32;
+            const bool has = len > 0 && a1 > 0 && a0 < 32;
+            const int last = has ? (a1 < 32 ? a1 : 32) - 1 : 0;
+            const T got = shfl_mask(x, last);
+            if (has) found |= got;
+        }
+        pos += len;
+        edges += (unsigned long long)len;
     }
     return found;
 }
@@ -301,11 +392,27 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
 {
     __shared__ MsGraph s_g[MS_MAXG];
     __shared__ int64_t s_voff[MS_MAXG + 1];
+    __shared__ MsSlots s_slots;
+    __shared__ MsWarpBuf s_wb[MS_WARPS];
+    __shared__ unsigned long long s_mf, s_any;
     for (int i = threadIdx.x; i < a.ng; i += blockDim.x) s_g[i] = a.graphs[i];
+    if (a.slots)
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+            s_slots.par[i] = a.slots->par[i];
+            s_slots.lev[i] = a.slots->lev[i];
+            s_slots.start[i] = a.slots->start[i];
+        }
+    if (threadIdx.x == 0) {
+        s_mf = 0;
+        s_any = 0;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i <= a.ng; i += blockDim.x)
         s_voff[i] = i < a.ng ? s_g[i].voff : s_g[a.ng - 1].voff + s_g[a.ng - 1].n;
     __syncthreads();
+    const MsSlots *S = a.slots ? &s_slots : nullptr;
+    MsWarpBuf &wb = s_wb[threadIdx.x >> 5];
+    int qn_buf = 0, bn_buf = 0;
 
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
@@ -313,74 +420,79 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
     const int64_t gwarp = gtid >> 5;
     const int64_t nwarps = gthreads >> 5;
     const int64_t ntot = a.ntot;
-    const T all = a.k >= (int)(8 * sizeof(T)) ? (T)~(T)0 : (T)(((T)1 << a.k) - 1);
+    const T all = a.do_init
+                      ? (a.k >= (int)(8 * sizeof(T)) ? (T)~(T)0 : (T)(((T)1 << a.k) - 1))
+                      : (T)a.active;
     MsHeader *h = a.hdr;
 
-    // ---- init: outputs -1, masks clear
-    for (int g = 0; g < a.ng; ++g) {
-        const MsGraph G = s_g[g];
-        const int64_t cnt = (int64_t)a.k * G.n;
-        for (int64_t i = gtid; i < cnt; i += gthreads) {
-            G.par[i] = -1;
-            G.lev[i] = -1;
-        }
-    }
-    for (int64_t i = gtid; i < a.mstride; i += gthreads) {
-        // isolated vertices start fully seen: no search reaches them, and the
-        // bottom-up step skips them; their outputs stay -1
-        T s0 = 0;
-        if (i < ntot) {
-            const int g = find_graph(s_voff, a.ng, i);
-            const int64_t lu = i - s_g[g].voff;
-            if (!((s_g[g].nz[lu >> 5] >> (lu & 31)) & 1u)) s0 = all;
-        }
-        a.seen[i] = s0;
-        a.mbuf[i] = 0;
-        a.mbuf[a.mstride + i] = 0;
-        a.mbuf[2 * a.mstride + i] = 0;
-    }
-    if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
-    // roots: bit b of graph g at its root; roots that coincide share one entry
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        unsigned long long na = 0, mf = 0;
+    if (a.do_init) {
+        // ---- outputs -1, masks clear; isolated vertices start fully seen: no
+        // search reaches them and the bottom-up step skips them
         for (int g = 0; g < a.ng; ++g) {
             const MsGraph G = s_g[g];
-            for (int b = 0; b < a.k; ++b) {
-                const int64_t r = a.roots[(int64_t)g * a.k + b];
-                const int64_t gid = G.voff + r;
-                if (a.mbuf[gid] == 0) {
-                    a.act[na++] = (int32_t)gid;
-                    const int64_t deg = G.off[r + 1] - G.off[r];
-                    mf += deg;
-                    if (deg > MS_BIG_DEG) {
-                        const unsigned long long p = h->ctl[0].big;
-                        a.bigq[p >> 32] = (unsigned long long)(uint32_t)gid | ((p & 0xffffffffull) << 32);
-                        h->ctl[0].big = p + ((1ull << 32) | (unsigned long long)((deg + MS_BIG_CHUNK - 1) / MS_BIG_CHUNK));
-                    }
-                }
-                a.mbuf[gid] |= (T)((T)1 << b);
-                a.seen[gid] |= (T)((T)1 << b);
-                G.par[(int64_t)b * G.n + r] = (int32_t)r;
-                G.lev[(int64_t)b * G.n + r] = 0;
+            const int64_t cnt = (int64_t)a.k * G.n;
+            for (int64_t i = gtid; i < cnt; i += gthreads) {
+                G.par[i] = -1;
+                G.lev[i] = -1;
             }
         }
-        h->ctl[0].na = na;
-        h->ctl[0].mf = mf;
-        h->acc[2] = (unsigned long long)a.ng * (unsigned long long)a.k;  // the roots themselves
+        for (int64_t i = gtid; i < a.mstride; i += gthreads) {
+            T s0 = 0;
+            if (i < ntot) {
+                const int g = find_graph(s_voff, a.ng, i);
+                const int64_t lu = i - s_g[g].voff;
+                if (!((s_g[g].nz[lu >> 5] >> (lu & 31)) & 1u)) s0 = all;
+            }
+            a.seen[i] = s0;
+            a.mbuf[i] = 0;
+            a.mbuf[a.mstride + i] = 0;
+            a.mbuf[2 * a.mstride + i] = 0;
+        }
+        if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+        // roots: bit b of graph g at its root; roots that coincide share one entry
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            unsigned long long na = 0, mf = 0;
+            for (int g = 0; g < a.ng; ++g) {
+                const MsGraph G = s_g[g];
+                for (int b = 0; b < a.k; ++b) {
+                    const int64_t r = a.roots[(int64_t)g * a.k + b];
+                    const int64_t gid = G.voff + r;
+                    if (a.mbuf[gid] == 0) {
+                        a.act[na++] = (int32_t)gid;
+                        const int64_t deg = G.off[r + 1] - G.off[r];
+                        mf += deg;
+                        if (deg > MS_BIG_DEG) {
+                            const unsigned long long p = h->ctl[0].big;
+                            a.bigq[p >> 32] = (unsigned long long)(uint32_t)gid | ((p & 0xffffffffull) << 32);
+                            h->ctl[0].big = p + ((1ull << 32) | (unsigned long long)((deg + MS_BIG_CHUNK - 1) / MS_BIG_CHUNK));
+                        }
+                    }
+                    a.mbuf[gid] |= (T)((T)1 << b);
+                    a.seen[gid] |= (T)((T)1 << b);
+                    G.par[(int64_t)b * G.n + r] = (int32_t)r;
+                    G.lev[(int64_t)b * G.n + r] = 0;
+                }
+            }
+            h->ctl[0].na = na;
+            h->ctl[0].mf = mf;
+            h->acc[2] = (unsigned long long)a.ng * (unsigned long long)a.k;  // the roots themselves
+        }
+        if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
     }
-    if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
 
-    int64_t prev_na = 0;
-    unsigned long long my_edges = 0, my_touched = 0, reached_new = 0;
-    int l = 0;
+    unsigned long long my_edges = 0, my_touched = 0, reached_new = 0, my_mf = 0;
+    T my_any = 0;
+    int l = a.l0;
     for (;; ++l) {
+        if (a.max_levels > 0 && l >= a.l0 + a.max_levels) break;
         MsCtl *cur = &h->ctl[l % 3];
         const int64_t na = (int64_t)ldcg_u64(&cur->na);
         if (na == 0) break;
-        if (l > ntot) {
+        if (l - a.l0 > ntot) {
             if (gtid == 0) record_error(a.st, GB_ERR_TIMEOUT, SITE_MS_LEVELS, l);
             break;
         }
+        const int64_t prev_na = l > 0 ? (int64_t)ldcg_u64(&h->na_hist[(l - 1) & 3]) : 0;
         const double mf = (double)ldcg_u64(&cur->mf);
         const unsigned long long bigp = ldcg_u64(&cur->big);
         const int64_t nb = (int64_t)(bigp >> 32), nc = (int64_t)(bigp & 0xffffffffull);
@@ -394,7 +506,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
         MsCtl *nxt = &h->ctl[(l + 1) % 3];
         // big-vertex chunk lists alternate between two halves of bigq
         const int64_t bbase = (l & 1) ? a.bigcap : 0;
-        const int64_t bnext_base = (l & 1) ? 0 : a.bigcap;
+        unsigned long long *bigq_next = a.bigq + ((l & 1) ? 0 : a.bigcap);
 
         // Clear the level l-1 frontier (its buffer receives level l+2) and the
         // control record level l+1 will fill; nobody reads either during level l.
@@ -437,7 +549,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                             const int64_t j = b + lane;
                             const bool valid = j < e;
                             const int64_t gu = valid ? G.voff + G.col[j] : 0;
-                            ms_td_edge(valid, f, gu, a, Mn, s_g, s_voff, nxt, act_next, bnext_base);
+                            ms_td_edge(valid, f, gu, a, Mn, s_g, s_voff, wb, qn_buf, bn_buf, my_mf,
+                                       nxt, act_next, bigq_next);
                         }
                     }
                 }
@@ -477,15 +590,18 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                     const T fo = shfl_mask(f, owner);
                     const bool valid = kk < total;
                     const int64_t gu = valid ? vvo + s_g[og].col[so + (kk - eo)] : 0;
-                    ms_td_edge(valid, fo, gu, a, Mn, s_g, s_voff, nxt, act_next, bnext_base);
+                    ms_td_edge(valid, fo, gu, a, Mn, s_g, s_voff, wb, qn_buf, bn_buf, my_mf, nxt,
+                               act_next, bigq_next);
                 }
             }
+            ms_flush_q(wb, qn_buf, nxt, act_next);
+            ms_flush_b(wb, bn_buf, nxt, bigq_next);
             if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
             // (2) parents and levels of the vertices that gained bits
             const int64_t nn = (int64_t)ldcg_u64(&nxt->na);
             for (int64_t i0 = gwarp * 32; i0 < nn; i0 += nwarps * 32) {
                 const int64_t i = i0 + lane;
-                int64_t gu = 0, lu = 0, deg = 0;
+                int64_t gu = 0, lu = 0, rs = 0, re = 0;
                 int g = 0;
                 T nw = 0;
                 if (i < nn) {
@@ -493,20 +609,15 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                     g = find_graph(s_voff, a.ng, gu);
                     lu = gu - s_g[g].voff;
                     nw = ld_mask(&Mn[gu]);
-                    deg = s_g[g].off[lu + 1] - s_g[g].off[lu];
-                    if (deg <= 32) scan_serial(s_g[g], lu, nw, M, my_edges);
-                    write_levels(s_g[g], lu, nw, l + 1);
+                    rs = s_g[g].off[lu];
+                    re = s_g[g].off[lu + 1];
+                }
+                ms_rows(s_g, S, M, g, lu, rs, re, nw, my_edges);
+                if (i < nn) {
+                    write_levels(s_g[g], S, lu, nw, l + 1);
                     st_mask(&a.seen[gu], (T)(ld_mask(&a.seen[gu]) | nw));
                     reached_new += __popcll((unsigned long long)nw);
-                }
-                unsigned bigm = __ballot_sync(kFull, i < nn && deg > 32);
-                while (bigm) {
-                    const int jl = __ffs(bigm) - 1;
-                    bigm &= bigm - 1;
-                    const int gj = __shfl_sync(kFull, g, jl);
-                    const int64_t luj = __shfl_sync(kFull, lu, jl);
-                    const T nwj = shfl_mask(nw, jl);
-                    scan_warp(s_g[gj], luj, nwj, M, my_edges);
+                    my_any |= nw;
                 }
             }
         } else {
@@ -527,33 +638,51 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                         if (deg == 0) need = 0;
                     }
                 }
-                T found = 0;
-                if (need && deg <= 32) found = scan_serial(s_g[g], lu, need, M, my_edges);
-                my_touched += (need != 0);
-                unsigned bigm = __ballot_sync(kFull, need && deg > 32);
-                while (bigm) {
-                    const int jl = __ffs(bigm) - 1;
-                    bigm &= bigm - 1;
-                    const int gj = __shfl_sync(kFull, g, jl);
-                    const int64_t luj = __shfl_sync(kFull, lu, jl);
-                    const T nj = shfl_mask(need, jl);
-                    const T fj = scan_warp(s_g[gj], luj, nj, M, my_edges);
-                    if ((int)lane == jl) found = fj;
+                int64_t rs = 0, re = 0;
+                if (need) {
+                    rs = s_g[g].off[lu];
+                    re = rs + deg;
                 }
+                my_touched += (need != 0);
+                const T found = ms_rows(s_g, S, M, g, lu, rs, re, need, my_edges);
                 if (found) {
-                    write_levels(s_g[g], lu, found, l + 1);
+                    write_levels(s_g[g], S, lu, found, l + 1);
                     st_mask(&a.seen[gu], (T)(sn | found));
                     st_mask(&Mn[gu], found);
                     reached_new += __popcll((unsigned long long)found);
+                    my_any |= found;
                 }
-                ms_append(found != 0, gu, deg, a, nxt, act_next, bnext_base);
+                ms_append(found != 0, gu, deg, wb, qn_buf, bn_buf, my_mf, nxt, act_next, bigq_next);
+            }
+            ms_flush_q(wb, qn_buf, nxt, act_next);
+            ms_flush_b(wb, bn_buf, nxt, bigq_next);
+        }
+        // end of level: the block's degree sum and advancing bits, one atomic each
+        {
+            const unsigned long long t = warp_sum(my_mf);
+            const unsigned long long o = (unsigned long long)warp_or(my_any);
+            my_mf = 0;
+            my_any = 0;
+            if (lane == 0) {
+                if (t) atomicAdd(&s_mf, t);
+                if (o) atomicOr(&s_any, o);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (s_mf) atomicAdd(&nxt->mf, s_mf);
+                if (s_any) atomicOr(&nxt->anynew, s_any);
+                s_mf = 0;
+                s_any = 0;
             }
         }
-        prev_na = na;
-        if (gtid == 0) atomicAdd(&h->acc[td ? 4 : 5], 1ull);
+        if (gtid == 0) {
+            h->na_hist[l & 3] = (unsigned long long)na;
+            atomicAdd(&h->acc[td ? 4 : 5], 1ull);
+        }
         if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
     }
 
+    if (!a.stats) return;
     my_edges = warp_sum(my_edges);
     my_touched = warp_sum(my_touched);
     reached_new = warp_sum(reached_new);
@@ -568,17 +697,17 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
         const unsigned prev = atomicAdd(&h->done, 1u);
         if (prev == gridDim.x - 1) {
             __threadfence();
-            BfsDevStats &s = *a.stats;
-            s.nlevels = (unsigned long long)l;
-            s.edges_examined = ldcg_u64(&h->acc[0]);
-            s.vertices_touched = ldcg_u64(&h->acc[1]);
-            s.reached = ldcg_u64(&h->acc[2]);
-            s.td_levels = ldcg_u64(&h->acc[4]);
-            s.bu_levels = ldcg_u64(&h->acc[5]);
+            BfsDevStats &st = *a.stats;
+            st.nlevels = (unsigned long long)l;
+            st.edges_examined = ldcg_u64(&h->acc[0]);
+            st.vertices_touched = ldcg_u64(&h->acc[1]);
+            st.reached = ldcg_u64(&h->acc[2]);
+            st.td_levels = ldcg_u64(&h->acc[4]);
+            st.bu_levels = ldcg_u64(&h->acc[5]);
             for (int i = 0; i < kStatLevels; ++i) {
-                s.level_ns[i] = 0;
-                s.level_frontier[i] = 0;
-                s.level_dir[i] = 0;
+                st.level_ns[i] = 0;
+                st.level_frontier[i] = 0;
+                st.level_dir[i] = 0;
             }
         }
     }
@@ -637,6 +766,11 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     a.ms_alpha = (float)o.ms_alpha;
     a.ms_beta = (float)o.ms_beta;
     a.timeout_ns = timeout_ns();
+    a.l0 = 0;
+    a.max_levels = 0;
+    a.do_init = 1;
+    a.active = 0;
+    a.slots = nullptr;
     void *args[] = {&a};
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)ms_kernel<T>, dim3(ctx->ms_blocks),
                                         dim3(MS_THREADS), args, 0, s));
@@ -680,6 +814,200 @@ gb_status multigraph_impl(const gb_graph *const *gs, int ng, const int64_t *root
     }
     std::vector<int64_t> rr(roots, roots + (size_t)ng * r);
     return ms_launch<unsigned char>(v, r, rr, nnz, stats, s);
+}
+
+// ---------------------------------------------------------------------------
+// Serving: a resident graph's search state, admissions and one-level steps.
+// ---------------------------------------------------------------------------
+namespace {
+
+// seen[u] loses the bits `fresh` (slots being reused), except that isolated
+// vertices keep them set: no query reaches them and bottom-up skips them.
+__global__ void ms_admit_clear_kernel(const uint32_t *__restrict__ nz, int64_t n,
+                                      unsigned long long *__restrict__ seen,
+                                      unsigned long long fresh)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const bool iso = !((nz[u >> 5] >> (u & 31)) & 1u);
+        seen[u] = (seen[u] & ~fresh) | (iso ? fresh : 0ull);
+    }
+}
+
+struct AdmitList {
+    int count;
+    int bit[64];
+    int64_t root[64];
+};
+
+// One thread: place each admitted root into level l's frontier.
+__global__ void ms_admit_roots_kernel(MsGraph G, MsHeader *h, unsigned long long *seen,
+                                      unsigned long long *Ml, int32_t *act_l,
+                                      unsigned long long *bigq_l, int l, AdmitList adm,
+                                      const MsSlots *slots)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    MsCtl &c = h->ctl[l % 3];
+    for (int i = 0; i < adm.count; ++i) {
+        const int b = adm.bit[i];
+        const int64_t r = adm.root[i];
+        const unsigned long long bit = 1ull << b;
+        seen[r] |= bit;
+        if (Ml[r] == 0) {
+            act_l[c.na++] = (int32_t)r;
+            const int64_t deg = G.off[r + 1] - G.off[r];
+            c.mf += (unsigned long long)deg;
+            if (deg > MS_BIG_DEG) {
+                const unsigned long long p = c.big;
+                bigq_l[p >> 32] = (unsigned long long)(uint32_t)r | ((p & 0xffffffffull) << 32);
+                c.big = p + ((1ull << 32) | (unsigned long long)((deg + MS_BIG_CHUNK - 1) / MS_BIG_CHUNK));
+            }
+        }
+        Ml[r] |= bit;
+        slots->lev[b][r] = 0;
+        slots->par[b][r] = (int32_t)r;
+    }
+}
+
+}  // namespace
+
+struct MsServe {
+    const gb_graph *g = nullptr;
+    unsigned char *ws = nullptr;
+    MsHeader *hdr = nullptr;
+    MsGraph *graph_dev = nullptr;
+    MsSlots *slots_dev = nullptr;
+    unsigned long long *seen = nullptr;
+    unsigned long long *mbuf = nullptr;
+    int32_t *act = nullptr;
+    unsigned long long *bigq = nullptr;
+    int64_t bigcap = 0;
+    int64_t mstride = 0;
+    int blocks = 0;
+    MsGraph graph_host;
+};
+
+gb_status ms_serve_create(const gb_graph *g, int blocks, MsServe **out, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    MsServe *m = new MsServe();
+    m->g = g;
+    const int64_t n = g->n;
+    m->mstride = (n + 63) & ~int64_t(63);
+    m->bigcap = g->nnz / (MS_BIG_DEG + 1) + 66;
+    m->blocks = std::max(1, std::min(blocks, ctx->ms_blocks));
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t o_g = up(sizeof(MsHeader));
+    const size_t o_sl = o_g + up(sizeof(MsGraph));
+    const size_t o_seen = o_sl + up(sizeof(MsSlots));
+    const size_t o_m = o_seen + up(m->mstride * 8);
+    const size_t o_act = o_m + up(3 * m->mstride * 8);
+    const size_t o_big = o_act + up(3 * (size_t)n * 4);
+    const size_t total = o_big + 2 * m->bigcap * 8;
+    cudaError_t e = cudaMalloc((void **)&m->ws, total);
+    if (e != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "server workspace");
+    }
+    m->hdr = reinterpret_cast<MsHeader *>(m->ws);
+    m->graph_dev = reinterpret_cast<MsGraph *>(m->ws + o_g);
+    m->slots_dev = reinterpret_cast<MsSlots *>(m->ws + o_sl);
+    m->seen = reinterpret_cast<unsigned long long *>(m->ws + o_seen);
+    m->mbuf = reinterpret_cast<unsigned long long *>(m->ws + o_m);
+    m->act = reinterpret_cast<int32_t *>(m->ws + o_act);
+    m->bigq = reinterpret_cast<unsigned long long *>(m->ws + o_big);
+    MsGraph G;
+    G.off = g->off;
+    G.col = g->col;
+    G.nz = g->nz;
+    G.voff = 0;
+    G.n = n;
+    G.par = nullptr;
+    G.lev = nullptr;
+    m->graph_host = G;
+    GB_CUDA(cudaMemsetAsync(m->ws, 0, o_big, s));
+    GB_CUDA(cudaMemcpyAsync(m->graph_dev, &m->graph_host, sizeof(MsGraph), cudaMemcpyHostToDevice, s));
+    ms_admit_clear_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->nz, n, m->seen, ~0ull);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
+    GB_CUDA(cudaStreamSynchronize(s));
+    *out = m;
+    return GB_OK;
+}
+
+void ms_serve_destroy(MsServe *m)
+{
+    if (!m) return;
+    if (m->ws) cudaFree(m->ws);
+    delete m;
+}
+
+gb_status ms_serve_admit(MsServe *m, int level, int count, const int *bits, const int64_t *roots,
+                         const MsSlots *table, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    if (count < 1 || count > 64) return GB_OK;
+    AdmitList adm;
+    adm.count = count;
+    unsigned long long fresh = 0;
+    for (int i = 0; i < count; ++i) {
+        adm.bit[i] = bits[i];
+        adm.root[i] = roots[i];
+        fresh |= 1ull << bits[i];
+    }
+    GB_CUDA(cudaMemcpyAsync(m->slots_dev, table, sizeof(MsSlots), cudaMemcpyHostToDevice, s));
+    ms_admit_clear_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(m->g->nz, m->g->n, m->seen, fresh);
+    note_launch();
+    const int64_t ntot = m->g->n;
+    ms_admit_roots_kernel<<<1, 32, 0, s>>>(m->graph_host, m->hdr, m->seen,
+                                           m->mbuf + (size_t)(level % 3) * m->mstride,
+                                           m->act + (size_t)(level % 3) * ntot,
+                                           m->bigq + ((level & 1) ? m->bigcap : 0), level, adm,
+                                           m->slots_dev);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
+    return GB_OK;
+}
+
+gb_status ms_serve_step(MsServe *m, int level, unsigned long long active, MsCtl *host_ctl,
+                        cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    const gb_bfs_options &o = options();
+    MsArgs<unsigned long long> a;
+    a.graphs = m->graph_dev;
+    a.ng = 1;
+    a.k = 64;
+    a.ntot = m->g->n;
+    a.mstride = m->mstride;
+    a.nnz_tot = m->g->nnz;
+    a.roots = nullptr;
+    a.seen = m->seen;
+    a.mbuf = m->mbuf;
+    a.act = m->act;
+    a.bigq = m->bigq;
+    a.bigcap = m->bigcap;
+    a.hdr = m->hdr;
+    a.st = ctx->status;
+    a.stats = nullptr;
+    a.ms_alpha = (float)o.ms_alpha;
+    a.ms_beta = (float)o.ms_beta;
+    a.timeout_ns = timeout_ns();
+    a.l0 = level;
+    a.max_levels = 1;
+    a.do_init = 0;
+    a.active = active;
+    a.slots = m->slots_dev;
+    void *args[] = {&a};
+    GB_CUDA(cudaLaunchCooperativeKernel((const void *)ms_kernel<unsigned long long>, dim3(m->blocks),
+                                        dim3(MS_THREADS), args, 0, s));
+    note_launch();
+    GB_CUDA(cudaMemcpyAsync(host_ctl, &m->hdr->ctl[(level + 1) % 3], sizeof(MsCtl),
+                            cudaMemcpyDeviceToHost, s));
+    return GB_OK;
 }
 
 int msbfs_pick_blocks(int num_sms)

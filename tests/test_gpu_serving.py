@@ -1,0 +1,111 @@
+"""Serving: continuous batching over resident graphs.
+
+Queries that arrive while others run are admitted into free bit-slots at BFS
+level boundaries.  Every served result must equal the same query run alone:
+levels and parents bit-exact against bfs() and against the oracle (the
+batched kernel always produces the smallest-id parent).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2012_13548_gb300 as gb  # noqa: E402
+from paper_2012_13548_gb300 import workloads as W  # noqa: E402
+from tests.conftest import oracle_graph  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+SCALES = (8, 10, 12, 14)
+
+
+@pytest.fixture(scope="module")
+def resident():
+    graphs, offs = [], []
+    for s in SCALES:
+        spec = W.GraphSpec(scale=s)
+        e = gb.kron_generate(**spec.kron_args())
+        graphs.append(gb.graph_build_csr(e, s))
+        offs.append(oracle_graph(s)[1])
+    return graphs, offs
+
+
+def _check_results(srv, graphs, tickets, queries):
+    gb.bfs_set_options(canonical_parents=1)
+    for t, (gi, r) in zip(tickets, queries):
+        par, lev = srv.result(t, gi)
+        p_alone, l_alone = gb.bfs(graphs[gi], r)
+        assert torch.equal(lev, l_alone), (gi, r)
+        assert torch.equal(par, p_alone), (gi, r)
+        _, off, col = oracle_graph(SCALES[gi])
+        p_ref, l_ref = oracle.bfs(off, col, r)
+        assert np.array_equal(lev.cpu().numpy(), l_ref), (gi, r)
+        assert np.array_equal(par.cpu().numpy(), p_ref), (gi, r)
+        srv.release(t)
+    gb.bfs_set_options(canonical_parents=0)
+
+
+def test_burst_larger_than_the_slots(resident):
+    graphs, offs = resident
+    rng = np.random.default_rng(11)
+    srv = gb.Server(graphs, mem_budget=1 << 30)
+    queries = []
+    for _ in range(300):                      # > 64 per graph: slots are reused
+        gi = int(rng.integers(0, len(graphs)))
+        queries.append((gi, int(rng.integers(0, graphs[gi].n))))   # isolated roots included
+    tickets = [srv.submit(gi, r) for gi, r in queries]
+    _check_results(srv, graphs, tickets, queries)
+    srv.close()
+    gb.gb_device_status()
+
+
+def test_admission_by_memory(resident):
+    graphs, offs = resident
+    # room for the outputs of two queries on the largest graph at a time
+    budget = 2 * 8 * graphs[-1].n
+    srv = gb.Server(graphs, mem_budget=budget)
+    rng = np.random.default_rng(12)
+    queries = [(3, int(r)) for r in W.root_from_draw(offs[3], rng.integers(0, 2**62, size=40))]
+    tickets = [srv.submit(gi, r) for gi, r in queries]
+    _check_results(srv, graphs, tickets, queries)
+    srv.close()
+
+
+def test_poisson_trace_matches_alone_and_replays_identically(resident):
+    graphs, offs = resident
+    t, gid, draw = W.poisson_trace(rate=20000.0, duration_s=0.05, n_graphs=len(graphs), seed=5)
+    roots = np.array([W.root_from_draw(offs[g], np.array([d], dtype=np.uint64))[0]
+                      for g, d in zip(gid, draw)], dtype=np.int64)
+    outs = []
+    for rep in range(2):
+        srv = gb.Server(graphs, mem_budget=1 << 30)
+        lat = srv.run_trace(t, gid, roots, keep_results=True)
+        assert lat.shape == t.shape and (lat > 0).all()
+        levs = []
+        for i in range(t.size):
+            par, lev = srv.result(i, int(gid[i]))
+            levs.append((par.cpu().numpy(), lev.cpu().numpy()))
+            srv.release(i)
+        srv.close()
+        outs.append(levs)
+    gb.bfs_set_options(canonical_parents=1)
+    for i in range(t.size):
+        assert np.array_equal(outs[0][i][1], outs[1][i][1])
+        assert np.array_equal(outs[0][i][0], outs[1][i][0])
+        p_alone, l_alone = gb.bfs(graphs[int(gid[i])], int(roots[i]))
+        assert np.array_equal(outs[0][i][1], l_alone.cpu().numpy()), i
+        assert np.array_equal(outs[0][i][0], p_alone.cpu().numpy()), i
+    gb.bfs_set_options(canonical_parents=0)
+
+
+def test_submit_rejects_bad_queries(resident):
+    graphs, _ = resident
+    srv = gb.Server(graphs, mem_budget=1 << 30)
+    with pytest.raises(gb.GbError, match="RANGE"):
+        srv.submit(0, graphs[0].n)
+    with pytest.raises(gb.GbError, match="RANGE"):
+        srv.submit(len(graphs), 0)
+    srv.close()
