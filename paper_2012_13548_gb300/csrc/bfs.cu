@@ -203,28 +203,44 @@ __device__ __forceinline__ void append_next(bool won, int32_t v, int64_t dv, con
     }
 }
 
-// Warp-collective top-down visit of edge (src -> v) for the lanes with `valid`.
-__device__ __forceinline__ void td_visit(bool valid, int32_t src, int32_t v, int l,
-                                         const BfsArgs &a, unsigned *Fn, WarpBuf &wb, int &qn,
-                                         int &bn, unsigned long long &my_mf, LevelCtl *nxt,
+// Warp-collective top-down visit of TD_E edges per lane (src[t] -> v[t] where
+// valid[t]): the visited-bit tests, the claiming atomics and the winners'
+// degree loads of the TD_E edges are each issued together.
+constexpr int TD_E = 4;
+__device__ __forceinline__ void td_visit(const bool (&valid)[TD_E], const int32_t (&src)[TD_E],
+                                         const int32_t (&v)[TD_E], int l, const BfsArgs &a,
+                                         unsigned *Fn, WarpBuf &wb, int &qn, int &bn,
+                                         unsigned long long &my_mf, LevelCtl *nxt,
                                          int64_t qnext_base, int64_t bnext_base)
 {
-    bool won = false;
-    int64_t dv = 0;
-    if (valid && GB_OK_IDX(a.st, v, a.n, 205)) {
-        const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
-        if (!(ldcg_u32(&a.vis[w]) & bit)) {
-            const unsigned old = atomicOr(&a.vis[w], bit);
-            if (!(old & bit)) {
-                won = true;
-                a.parent[v] = src;
-                a.level[v] = l + 1;
-                atomicOr(&Fn[w], bit);
-                dv = a.off[v + 1] - a.off[v];
-            }
+    bool cand[TD_E], won[TD_E];
+#pragma unroll
+    for (int t = 0; t < TD_E; ++t) {
+        cand[t] = valid[t] && GB_OK_IDX(a.st, v[t], a.n, 205) &&
+                  !((ldcg_u32(&a.vis[(unsigned)v[t] >> 5]) >> (v[t] & 31)) & 1u);
+    }
+#pragma unroll
+    for (int t = 0; t < TD_E; ++t) {
+        won[t] = false;
+        if (cand[t]) {
+            const unsigned bit = 1u << (v[t] & 31);
+            won[t] = !(atomicOr(&a.vis[(unsigned)v[t] >> 5], bit) & bit);
         }
     }
-    append_next(won, v, dv, a, wb, qn, bn, my_mf, nxt, qnext_base, bnext_base);
+    int64_t dv[TD_E];
+#pragma unroll
+    for (int t = 0; t < TD_E; ++t) {
+        dv[t] = 0;
+        if (won[t]) {
+            a.parent[v[t]] = src[t];
+            a.level[v[t]] = l + 1;
+            atomicOr(&Fn[(unsigned)v[t] >> 5], 1u << (v[t] & 31));
+            dv[t] = a.off[v[t] + 1] - a.off[v[t]];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TD_E; ++t)
+        append_next(won[t], v[t], dv[t], a, wb, qn, bn, my_mf, nxt, qnext_base, bnext_base);
 }
 
 // MINB = blocks of BFS_THREADS per SM the register budget is sized for:
@@ -240,6 +256,7 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
     const int64_t n = a.n, nw = a.nw;
     WsHeader *h = a.hdr;
     const int32_t root = a.root;
+    unsigned bar_target = grid_barrier_base(&h->bar);
     __shared__ WarpBuf s_wb[BFS_WARPS];
     __shared__ unsigned long long s_mf;
     WarpBuf &wb = s_wb[threadIdx.x >> 5];
@@ -275,7 +292,7 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
             a.bigq[0] = be;
         }
     }
-    if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_BFS_BAR)) return;
+    if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_BFS_BAR)) return;
     if (gtid == 0) {
         h->t0 = globaltimer_ns();
         a.stats->init_ns = 0;
@@ -361,11 +378,18 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                         const int64_t eu = a.off[be.u + 1];
                         const int64_t e = s + BIG_CHUNK < eu ? s + BIG_CHUNK : eu;
                         if (lane == 0) my_edges += (unsigned long long)(e - s);
-                        for (int64_t b = s; b < e; b += 32) {
-                            const int64_t j = b + lane;
-                            const bool valid = j < e && GB_OK_IDX(a.st, j, a.nnz, 207);
-                            const int32_t v = valid ? a.col[j] : 0;
-                            td_visit(valid, be.u, v, l, a, Fn, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
+                        for (int64_t b = s; b < e; b += 32 * TD_E) {
+                            bool valid[TD_E];
+                            int32_t sv[TD_E], vv[TD_E];
+#pragma unroll
+                            for (int t = 0; t < TD_E; ++t) {
+                                const int64_t j = b + t * 32 + lane;
+                                valid[t] = j < e && GB_OK_IDX(a.st, j, a.nnz, 207);
+                                vv[t] = valid[t] ? __ldg(&a.col[j]) : 0;
+                                sv[t] = be.u;
+                            }
+                            td_visit(valid, sv, vv, l, a, Fn, wb, qn_buf, bn_buf, my_mf, nxt,
+                                     qnext_base, bnext_base);
                         }
                     }
                 }
@@ -387,21 +411,27 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                 const int64_t excl = incl - d;
                 my_edges += d;
                 my_touched += (i < qn);
-                for (int64_t b = 0; b < total; b += 32) {
-                    const int64_t k = b + lane;
-                    int owner = 0;
+                for (int64_t b = 0; b < total; b += 32 * TD_E) {
+                    bool valid[TD_E];
+                    int32_t sv[TD_E], vv[TD_E];
 #pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const int cand = owner + step;
-                        const int64_t ex = __shfl_sync(kFull, excl, cand);
-                        if (ex <= k) owner = cand;
+                    for (int t = 0; t < TD_E; ++t) {
+                        const int64_t k = b + t * 32 + lane;
+                        int owner = 0;
+#pragma unroll
+                        for (int step = 16; step >= 1; step >>= 1) {
+                            const int cand = owner + step;
+                            const int64_t ex = __shfl_sync(kFull, excl, cand);
+                            if (ex <= k) owner = cand;
+                        }
+                        sv[t] = __shfl_sync(kFull, u, owner);
+                        const int64_t so = __shfl_sync(kFull, s, owner);
+                        const int64_t eo = __shfl_sync(kFull, excl, owner);
+                        valid[t] = k < total && GB_OK_IDX(a.st, so + (k - eo), a.nnz, 210);
+                        vv[t] = valid[t] ? __ldg(&a.col[so + (k - eo)]) : 0;
                     }
-                    const int32_t src = __shfl_sync(kFull, u, owner);
-                    const int64_t so = __shfl_sync(kFull, s, owner);
-                    const int64_t eo = __shfl_sync(kFull, excl, owner);
-                    const bool valid = k < total && GB_OK_IDX(a.st, so + (k - eo), a.nnz, 210);
-                    const int32_t v = valid ? a.col[so + (k - eo)] : 0;
-                    td_visit(valid, src, v, l, a, Fn, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
+                    td_visit(valid, sv, vv, l, a, Fn, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base,
+                             bnext_base);
                 }
             }
         } else {
@@ -519,7 +549,7 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
         qbase += qn;
         bbase += nb;
         if (gtid == 0) atomicAdd(&h->acc[td ? 4 : 5], 1ull);
-        if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_BFS_BAR)) return;
+        if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_BFS_BAR)) return;
         if (gtid == 0 && l < kStatLevels) {
             const uint64_t now = globaltimer_ns();
             a.stats->level_ns[l] = now - h->t0;

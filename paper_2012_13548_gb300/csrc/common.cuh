@@ -53,44 +53,64 @@ __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
 
 // ---------------------------------------------------------------------------
 // Software grid barrier for cooperative (all-blocks-resident) launches.
-// Sense by generation counter; every wait is bounded by `timeout_ns` of the
-// global timer, after which the block records GB_ERR_TIMEOUT and the barrier
-// returns false in every block (blocks also leave early once any block has
-// recorded an error).
+// Arrivals only ever add to one counter: the k-th barrier of a launch is
+// passed once the counter reaches base + k * gridDim.x, so no block has to
+// reset anything and the last arrival frees the others directly.  Thread 0
+// arrives with a release add (after __syncthreads, it publishes the block's
+// writes) and waits with acquire loads.  Every wait is bounded by
+// `timeout_ns` of the global timer: on expiry the block records
+// GB_ERR_TIMEOUT, and every block leaves early once any block has recorded an
+// error; grid_sync then returns false.
 // ---------------------------------------------------------------------------
 struct GridBarrier {
     unsigned count;
-    unsigned gen;
+    unsigned pad;
 };
 
-__device__ __forceinline__ bool grid_sync(GridBarrier *b, DevStatus *st, uint64_t timeout_ns,
-                                          int site)
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The counter value this launch starts from (a multiple of gridDim.x: every
+// earlier launch on the same barrier passed all its barriers).  Call once at
+// kernel entry, before the block's first grid_sync.
+__device__ __forceinline__ unsigned grid_barrier_base(GridBarrier *b)
+{
+    __shared__ unsigned s_base;
+    if (threadIdx.x == 0) s_base = (ld_acquire_u32(&b->count) / gridDim.x) * gridDim.x;
+    __syncthreads();
+    return s_base;
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned &target, DevStatus *st,
+                                          uint64_t timeout_ns, int site)
 {
     __shared__ int s_ok;
+    target += gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned g = ld_acquire_u32(&b->gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(&b->count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(&b->count, 0u);
-            __threadfence();
-            st_release_u32(&b->gen, g + 1u);
-        } else {
-            uint64_t t0 = globaltimer_ns();
-            unsigned spins = 0;
-            while (ld_acquire_u32(&b->gen) == g) {
-                if (status_code(st) != 0) { ok = 0; break; }
-                if ((++spins & 31u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
+        red_release_add_u32(&b->count, 1u);
+        uint64_t t0 = 0;
+        unsigned spins = 0;
+        while ((int)(ld_acquire_u32(&b->count) - target) < 0) {
+            if (status_code(st) != 0) {
+                ok = 0;
+                break;
+            }
+            if ((++spins & 31u) == 0) {
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > timeout_ns) {
                     record_error(st, GB_ERR_TIMEOUT, site, (long long)blockIdx.x);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
+            __nanosleep(32);
         }
-        __threadfence();
         s_ok = ok && status_code(st) == 0;
     }
     __syncthreads();

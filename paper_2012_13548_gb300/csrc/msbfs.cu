@@ -411,6 +411,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
         s_voff[i] = i < a.ng ? s_g[i].voff : s_g[a.ng - 1].voff + s_g[a.ng - 1].n;
     __syncthreads();
     const MsSlots *S = a.slots ? &s_slots : nullptr;
+    unsigned bar_target = grid_barrier_base(&a.hdr->bar);
     MsWarpBuf &wb = s_wb[threadIdx.x >> 5];
     int qn_buf = 0, bn_buf = 0;
 
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             a.mbuf[a.mstride + i] = 0;
             a.mbuf[2 * a.mstride + i] = 0;
         }
-        if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+        if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_MS_BAR)) return;
         // roots: bit b of graph g at its root; roots that coincide share one entry
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             unsigned long long na = 0, mf = 0;
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             h->ctl[0].mf = mf;
             h->acc[2] = (unsigned long long)a.ng * (unsigned long long)a.k;  // the roots themselves
         }
-        if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+        if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_MS_BAR)) return;
     }
 
     unsigned long long my_edges = 0, my_touched = 0, reached_new = 0, my_mf = 0;
@@ -596,7 +597,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             }
             ms_flush_q(wb, qn_buf, nxt, act_next);
             ms_flush_b(wb, bn_buf, nxt, bigq_next);
-            if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+            if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_MS_BAR)) return;
             // (2) parents and levels of the vertices that gained bits
             const int64_t nn = (int64_t)ldcg_u64(&nxt->na);
             for (int64_t i0 = gwarp * 32; i0 < nn; i0 += nwarps * 32) {
@@ -679,7 +680,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             h->na_hist[l & 3] = (unsigned long long)na;
             atomicAdd(&h->acc[td ? 4 : 5], 1ull);
         }
-        if (!grid_sync(&h->bar, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+        if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_MS_BAR)) return;
     }
 
     if (!a.stats) return;

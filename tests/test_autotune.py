@@ -1,0 +1,29 @@
+"""Host logic of the autotuner: coordinate descent and the table lookup."""
+import json
+
+from paper_2012_13548_gb300 import autotune as AT
+
+
+def test_descent_finds_the_separable_optimum():
+    space = {"a": [1, 2, 3, 4], "b": [10, 20, 30]}
+    cost = lambda o: (o["a"] - 3) ** 2 + abs(o["b"] - 20) + 1.0   # noqa: E731
+    best, t, trace = AT.descend(cost, space, {"a": 1, "b": 10})
+    assert best == {"a": 3, "b": 20} and t == 1.0
+    assert all(c >= t for _, c in trace)
+
+
+def test_descent_keeps_start_when_nothing_is_better():
+    space = {"a": [1, 2, 3]}
+    best, t, _ = AT.descend(lambda o: 5.0, space, {"a": 2})
+    assert best == {"a": 2}
+
+
+def test_table_lookup_takes_the_nearest_scale(tmp_path):
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps({"plain/20": {"alpha": 8.0, "median_ms": 0.2},
+                                "plain/26": {"alpha": 2.0, "median_ms": 5.0},
+                                "multigraph": {"ms_alpha": 4.0, "median_ms": 1.0}}))
+    assert AT.tuned_options("plain", 21, str(path)) == {"alpha": 8.0}
+    assert AT.tuned_options("plain", 25, str(path)) == {"alpha": 2.0}
+    assert AT.tuned_options("multigraph", None, str(path)) == {"ms_alpha": 4.0}
+    assert AT.tuned_options("batched", 20, str(path)) == {}
