@@ -44,7 +44,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="s20", choices=["s20", "s26", "s22ms", "serve6"])
+    p.add_argument("--workload", default="s20", choices=["s20", "s26", "s22ms", "serve6", "batch32"])
+    p.add_argument("--untuned", action="store_true", help="library defaults instead of tune_table.json")
     p.add_argument("--duration", type=float, default=3.0, help="serve6: seconds of arrivals")
     p.add_argument("--rate", type=float, default=None, help="serve6: arrivals per second")
     p.add_argument("--roots", type=int, default=64)
@@ -231,6 +232,7 @@ def workload_config(args, scale):
             "scale": scale, "edgefactor": W.EDGEFACTOR, "initiator": [W.A, W.B, W.C,
                                                                      round(1 - W.A - W.B - W.C, 2)],
             "roots": args.roots, "parents": "canonical" if args.canonical else "any-valid",
+            "options": "tune_table.json" if not args.untuned else "library defaults",
             "l2": "flushed before every timed call (256 MB write)",
             "step": "kernel1 + %d single-source BFS + one %d-root batched BFS" % (args.roots, args.roots)}
 
@@ -256,7 +258,11 @@ def run_ours(args, dist):
     wl = W.WORKLOADS[args.workload]
     scale = wl["scale"]
     spec = W.GraphSpec(scale=scale)
-    gb.bfs_set_options(canonical_parents=args.canonical)
+    tuned = {}
+    if not args.untuned:
+        from paper_2012_13548_gb300 import autotune
+        tuned = dict(autotune.tuned_options("plain", scale), **autotune.tuned_options("batched", scale))
+    gb.bfs_set_options(canonical_parents=args.canonical, **tuned)
 
     edges = gb.kron_generate(**spec.kron_args())            # input: generated, untimed
     g = gb.graph_build_csr(edges, scale)
@@ -344,15 +350,7 @@ def run_ours(args, dist):
     mean_bytes = statistics.mean(alg)
     mean_ms = statistics.mean(flat_ms)
     achieved = mean_bytes / (mean_ms * 1e-3) / 1e9
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "bfs_kernel_traffic.json")
-    if os.path.exists(tp):
-        try:
-            tj = json.load(open(tp))
-            if tj.get("scale") == scale and tj.get("source_hash") == kernel_source_hash():
-                traffic = tj["bytes_per_launch"]
-        except Exception:
-            traffic = None
+    traffic = read_traffic(scale)
     k1_bytes = kernel1_bytes(edges.shape[1], scale, g.nnz, n)
 
     # end to end through the public API from pinned host memory
@@ -396,6 +394,22 @@ def kernel1_bytes(m, scale, nnz, n):
     nk = 2 * m
     passes = (2 * scale + 7) // 8
     return 16 * m + 8 * nk + 8 * nk + passes * 16 * nk + 16 * nk + 4 * nnz + 8 * (n + 1)
+
+
+def read_traffic(scale):
+    """DRAM bytes per bfs_kernel launch from the committed ncu summary, if it
+    was taken at this SCALE on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "bfs_kernel_s%d_traffic.txt" % scale)
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.lstrip().startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != kernel_source_hash():
+        return None
+    return int(kv["bytes_per_launch"])
 
 
 def kernel_source_hash():
@@ -459,6 +473,9 @@ def run_serve(args, dist):
 
     torch.cuda.set_device(dist.local)
     wl = W.WORKLOADS["serve6"]
+    if not args.untuned:
+        from paper_2012_13548_gb300 import autotune
+        gb.bfs_set_options(**autotune.tuned_options("batched", 22))
     rate = args.rate or wl["rate"]
     graphs, edges, offs = [], [], []
     for sc in wl["scales"]:
@@ -550,6 +567,86 @@ def run_serve(args, dist):
         print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------
+# Graph batch: 32 Kronecker graphs of SCALE 12..18, 8 roots each, one launch
+# ---------------------------------------------------------------------------
+
+def run_batch32(args, dist):
+    import torch
+    import paper_2012_13548_gb300 as gb
+    torch.cuda.set_device(dist.local)
+    wl = W.WORKLOADS["batch32"]
+    if not args.untuned:
+        from paper_2012_13548_gb300 import autotune
+        gb.bfs_set_options(**autotune.tuned_options("multigraph"))
+    specs = W.batch_specs(wl["graphs"], wl["scale_lo"], wl["scale_hi"])
+    graphs, roots, edges = [], [], []
+    for sp in specs:
+        e = gb.kron_generate(**sp.kron_args())
+        g = gb.graph_build_csr(e, sp.scale)
+        rs = [int(x) for x in W.select_roots(g.csr()[0].cpu().numpy(), wl["roots"], sp.seeds()[3])]
+        graphs.append(g)
+        roots.append((rs * wl["roots"])[:wl["roots"]])
+        edges.append(e)
+    r = wl["roots"]
+    P = [torch.empty((r, g.n), dtype=torch.int32, device="cuda") for g in graphs]
+    L = [torch.empty((r, g.n), dtype=torch.int32, device="cuda") for g in graphs]
+    gb.bfs_multi_graph(graphs, roots, P, L)
+    m_tot = sum(int((L[gi][b][edges[gi][0]] >= 0).sum().item())
+                for gi in range(len(graphs)) for b in range(r))
+    par = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    lev = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def one_launch():
+        flush.fill_(1)
+        a, b = ev(), ev()
+        a.record()
+        gb.bfs_multi_graph(graphs, roots, P, L)
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    def sequential():
+        flush.fill_(2)
+        a, b = ev(), ev()
+        a.record()
+        for gi, g in enumerate(graphs):
+            for x in roots[gi]:
+                gb.bfs(g, x, par[gi], lev[gi])
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    for _ in range(args.warmup):
+        one_launch()
+        sequential()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    launches0 = gb.gb_kernel_launches()
+    t_batch = [one_launch() for _ in range(args.steps)]
+    launches = gb.gb_kernel_launches() - launches0
+    clk = clocks.stop()
+    t_seq = [sequential() for _ in range(args.steps)]
+    gb.gb_device_status()
+    tb, ts = statistics.median(t_batch), statistics.median(t_seq)
+    if dist.rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": m_tot / (tb * 1e-3) / 1e9, "unit": "GTEPS",
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "graph-batch-32-kronecker-scale12-18-8roots",
+                       "scales": [sp.scale for sp in specs], "roots_per_graph": r,
+                       "l2": "flushed before every timed call (256 MB write)"},
+            "batched_one_launch": {"ms": tb, "gteps": m_tot / (tb * 1e-3) / 1e9},
+            "sequential_plain": {"ms": ts, "gteps": m_tot / (ts * 1e-3) / 1e9,
+                                 "launches": len(graphs) * r},
+            "speedup": ts / tb, "gpu_launches": launches, "clocks": clk}))
+
+
 def main():
     args = parse_args()
     dist = Dist("cpu" if args.impl == "reference" else "cuda")
@@ -558,6 +655,8 @@ def main():
             run_reference(args, dist)
         elif args.workload == "serve6":
             run_serve(args, dist)
+        elif args.workload == "batch32":
+            run_batch32(args, dist)
         else:
             run_ours(args, dist)
     finally:
