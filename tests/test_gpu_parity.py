@@ -283,3 +283,17 @@ def test_multi_graph_batch_equals_standalone(lo, hi, count):
             p_ref, l_ref = oracle_bfs(sp.scale, r, sp.index)
             assert np.array_equal(np_(L[gi][b]), l_ref), (gi, b)
             assert np.array_equal(np_(P[gi][b]), p_ref), (gi, b)
+
+
+def test_bounded_waits_report_timeout_and_the_context_survives():
+    # A 100 ns limit makes the grid-barrier waits run out: every block leaves
+    # the kernel, the status word says GB_ERR_TIMEOUT, nothing faults or hangs.
+    _, G = gpu_graph(16)
+    r = roots_for(16, 1)[0]
+    gb.bfs_set_options(timeout_ms=1e-4)
+    gb.bfs(G, r)
+    with pytest.raises(gb.GbError, match="TIMEOUT"):
+        gb.gb_device_status()
+    gb.bfs_set_options(timeout_ms=5000.0)
+    _, off_ref, col_ref = oracle_graph(16)
+    check_bfs(G, off_ref, col_ref, r, canonical=0)
