@@ -595,8 +595,33 @@ int bfs_pick_blocks(int num_sms, int minb)
     return num_sms * std::min(per_sm, minb);
 }
 
+namespace {
+struct WsLayout {
+    size_t off_vis, off_fb, off_q, off_big, total;
+    int64_t bigcap;
+};
+// one buffer: header | visited | 4 frontier bitmaps | queue | big list
+WsLayout ws_layout(const gb_graph *g, int big_deg)
+{
+    WsLayout L;
+    const int64_t n = g->n, nw = (n + 31) / 32;
+    L.bigcap = g->nnz / (big_deg + 1) + 2;
+    L.off_vis = (sizeof(WsHeader) + 255) & ~size_t(255);
+    L.off_fb = L.off_vis + ((nw * 4 + 255) & ~size_t(255));
+    L.off_q = L.off_fb + ((4 * nw * 4 + 255) & ~size_t(255));
+    L.off_big = L.off_q + ((n * 4 + 255) & ~size_t(255));
+    L.total = L.off_big + L.bigcap * sizeof(BigEnt);
+    return L;
+}
+}  // namespace
+
+size_t bfs_workspace_bytes(const gb_graph *g)
+{
+    return ws_layout(g, 1).total;  // big_degree 1 is the largest big list
+}
+
 gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level,
-                   BfsDevStats *stats, cudaStream_t s)
+                   BfsDevStats *stats, cudaStream_t s, int grid, unsigned char *given_ws)
 {
     Context *ctx = context();
     if (!ctx) return GB_ERR_CUDA;
@@ -604,15 +629,11 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     const int64_t n = g->n;
     const int64_t nw = (n + 31) / 32;
     const int big_deg = std::max(o.big_degree, 1);
-    const int64_t bigcap = g->nnz / (big_deg + 1) + 2;
-    // one allocation: header | visited | 4 frontier bitmaps | queue | big list
-    const size_t off_vis = (sizeof(WsHeader) + 255) & ~size_t(255);
-    const size_t off_fb = off_vis + ((nw * 4 + 255) & ~size_t(255));
-    const size_t off_q = off_fb + ((4 * nw * 4 + 255) & ~size_t(255));
-    const size_t off_big = off_q + ((n * 4 + 255) & ~size_t(255));
-    const size_t total = off_big + bigcap * sizeof(BigEnt);
-    unsigned char *ws = nullptr;
-    GB_CUDA(cudaMallocAsync((void **)&ws, total, s));
+    const WsLayout Lw = ws_layout(g, big_deg);
+    const int64_t bigcap = Lw.bigcap;
+    const size_t off_vis = Lw.off_vis, off_fb = Lw.off_fb, off_q = Lw.off_q, off_big = Lw.off_big;
+    unsigned char *ws = given_ws;
+    if (!ws) GB_CUDA(cudaMallocAsync((void **)&ws, Lw.total, s));
     GB_CUDA(cudaMemsetAsync(ws, 0, sizeof(WsHeader), s));
     BfsArgs a;
     a.off = g->off;
@@ -639,12 +660,13 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.timeout_ns = timeout_ns();
     void *args[] = {&a};
     const int minb = o.blocks_per_sm == 2 ? 2 : 3;
-    const int blocks = minb == 2 ? ctx->bfs_blocks2 : ctx->bfs_blocks;
+    const int full = minb == 2 ? ctx->bfs_blocks2 : ctx->bfs_blocks;
+    const int blocks = grid > 0 && grid < full ? grid : full;
     const void *kern = minb == 2 ? (const void *)bfs_kernel<2> : (const void *)bfs_kernel<3>;
     GB_CUDA(cudaLaunchCooperativeKernel(kern, dim3(blocks),
                                         dim3(BFS_THREADS), args, 0, s));
     note_launch();
-    GB_CUDA(cudaFreeAsync(ws, s));
+    if (!given_ws) GB_CUDA(cudaFreeAsync(ws, s));
     return GB_OK;
 }
 

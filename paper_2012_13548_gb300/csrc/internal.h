@@ -112,8 +112,12 @@ struct BfsDevStats {
 };
 
 // Single-source BFS (bfs.cu).
+// blocks = cooperative grid size (0: the default full-GPU grid); ws = a
+// workspace of bfs_workspace_bytes(g) bytes owned by the caller, or nullptr
+// to take one from the stream-ordered pool.
 gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level,
-                   BfsDevStats *stats, cudaStream_t s);
+                   BfsDevStats *stats, cudaStream_t s, int blocks = 0, unsigned char *ws = nullptr);
+size_t bfs_workspace_bytes(const gb_graph *g);
 int bfs_pick_blocks(int num_sms, int minb);
 
 // Multi-source BFS over one graph or a batch of graphs (msbfs.cu).

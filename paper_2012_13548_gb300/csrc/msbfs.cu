@@ -837,15 +837,18 @@ __global__ void ms_admit_clear_kernel(const uint32_t *__restrict__ nz, int64_t n
 
 struct AdmitList {
     int count;
+    int level;
     int bit[64];
     int64_t root[64];
+    int32_t *par[64];
+    int32_t *lev[64];
 };
 
 // One thread: place each admitted root into level l's frontier.
 __global__ void ms_admit_roots_kernel(MsGraph G, MsHeader *h, unsigned long long *seen,
                                       unsigned long long *Ml, int32_t *act_l,
                                       unsigned long long *bigq_l, int l, AdmitList adm,
-                                      const MsSlots *slots)
+                                      MsSlots *slots)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     MsCtl &c = h->ctl[l % 3];
@@ -853,6 +856,10 @@ __global__ void ms_admit_roots_kernel(MsGraph G, MsHeader *h, unsigned long long
         const int b = adm.bit[i];
         const int64_t r = adm.root[i];
         const unsigned long long bit = 1ull << b;
+        // the slot table entry travels in the kernel parameters: no host copy
+        slots->par[b] = adm.par[i];
+        slots->lev[b] = adm.lev[i];
+        slots->start[b] = adm.level;
         seen[r] |= bit;
         if (Ml[r] == 0) {
             act_l[c.na++] = (int32_t)r;
@@ -952,13 +959,15 @@ gb_status ms_serve_admit(MsServe *m, int level, int count, const int *bits, cons
     if (count < 1 || count > 64) return GB_OK;
     AdmitList adm;
     adm.count = count;
+    adm.level = level;
     unsigned long long fresh = 0;
     for (int i = 0; i < count; ++i) {
         adm.bit[i] = bits[i];
         adm.root[i] = roots[i];
+        adm.par[i] = table->par[bits[i]];
+        adm.lev[i] = table->lev[bits[i]];
         fresh |= 1ull << bits[i];
     }
-    GB_CUDA(cudaMemcpyAsync(m->slots_dev, table, sizeof(MsSlots), cudaMemcpyHostToDevice, s));
     ms_admit_clear_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(m->g->nz, m->g->n, m->seen, fresh);
     note_launch();
     const int64_t ntot = m->g->n;

@@ -9,16 +9,27 @@
 // vertex) fit in the memory budget.  A query admitted at level l starts from
 // its root in the frontier of level l; its levels are numbered from there, so
 // its result equals a standalone BFS from that root (bits never interact).
+//
+// Graphs of 2^21 vertices or more are served by single-source searches
+// instead: up to kPlainSlots queries per graph run at once, each a
+// direction-optimising BFS launch on its own stream with a half-GPU
+// cooperative grid, so that concurrent queries overlap their memory latency.
+// On such graphs a multi-source level scans nearly every edge while a single
+// direction-optimising search touches a small fraction of them, so one query
+// per launch costs less device time than one bit of a shared launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "gb300bfs.h"
@@ -33,6 +44,24 @@ double now_s()
 }
 
 enum QState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2, Q_RELEASED = 3 };
+
+constexpr int64_t kPlainMinN = int64_t(1) << 21;  // graphs served one query per launch
+constexpr int kPlainSlots = 2;                    // concurrent searches per such graph
+
+struct PlainSlot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    gb::BfsDevStats *stats = nullptr;  // device; the kernel's counters land here
+    unsigned char *ws = nullptr;       // the slot's own search workspace
+    int64_t q = -1;                    // query in flight, -1 if free
+};
+
+// Output buffers (parent, level) of one graph, allocated once and reused:
+// the serving loop never goes through the stream-ordered allocator.
+struct OutBuf {
+    int32_t *par = nullptr;
+    int32_t *lev = nullptr;
+};
 
 struct Query {
     int graph = 0;
@@ -57,7 +86,37 @@ struct GraphRun {
     bool in_flight = false;
     std::deque<int64_t> pending;
     gb::MsSlots slots;
+    bool plain = false;  // one query per launch (large graph)
+    // counters printed by server_destroy when GB_SERVE_DEBUG=1
+    int64_t n_launch = 0, n_admit = 0;
+    double t_launch = 0, busy_s = 0;
+    int plain_blocks = 0;
+    PlainSlot ps[kPlainSlots];
+    std::vector<OutBuf> free_out;  // reusable buffers
+    std::vector<OutBuf> all_out;   // every buffer ever made (freed at destroy)
 };
+
+namespace {
+// A free output buffer pair, making one if none is free (synchronous
+// cudaMalloc, only while the server grows to its working set).
+bool take_out(GraphRun &G, OutBuf &b)
+{
+    if (!G.free_out.empty()) {
+        b = G.free_out.back();
+        G.free_out.pop_back();
+        return true;
+    }
+    OutBuf nb;
+    if (cudaMalloc((void **)&nb.par, (size_t)G.g->n * 4) != cudaSuccess) return false;
+    if (cudaMalloc((void **)&nb.lev, (size_t)G.g->n * 4) != cudaSuccess) {
+        cudaFree(nb.par);
+        return false;
+    }
+    G.all_out.push_back(nb);
+    b = nb;
+    return true;
+}
+}  // namespace
 
 }  // namespace
 
@@ -70,6 +129,8 @@ struct gb_server {
     std::mutex mu;
     std::condition_variable cv;    // worker wake-up (new work)
     std::condition_variable done;  // a query finished
+    std::vector<int64_t> finished;  // tickets finished since the trace runner last looked
+    bool tracing = false;           // a trace runner consumes `finished`
     std::thread worker;
     std::atomic<bool> stop{false};
     gb_status fault = GB_OK;
@@ -77,6 +138,7 @@ struct gb_server {
 
     void run();
     bool step_graph(GraphRun &G);
+    bool step_plain(GraphRun &G);
 };
 
 namespace {
@@ -85,10 +147,71 @@ size_t out_bytes(const gb_graph *g) { return (size_t)g->n * 8; }
 
 }  // namespace
 
+// One pass over a large graph: finish completed searches, start new ones in
+// free slots while their outputs fit the budget.
+bool gb_server::step_plain(GraphRun &G)
+{
+    bool busy = false;
+    for (int i = 0; i < kPlainSlots; ++i) {
+        PlainSlot &P = G.ps[i];
+        if (P.q >= 0) {
+            const cudaError_t e = cudaEventQuery(P.ev);
+            if (e == cudaErrorNotReady) {
+                busy = true;
+                continue;
+            }
+            std::lock_guard<std::mutex> lk(mu);
+            if (e != cudaSuccess) {
+                fault = GB_ERR_CUDA;
+                fault_msg = std::string("server search: ") + cudaGetErrorString(e);
+                done.notify_all();
+                return false;
+            }
+            Query &x = q[(size_t)P.q];
+            x.state = Q_DONE;
+            x.t_done = now_s();
+            if (tracing) finished.push_back(P.q);
+            P.q = -1;
+            done.notify_all();
+        }
+        int64_t t = -1;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            const size_t need = out_bytes(G.g);
+            if (G.pending.empty() || used + need > budget) continue;
+            t = G.pending.front();
+            Query &x = q[(size_t)t];
+            OutBuf ob;
+            if (!take_out(G, ob)) continue;  // no device memory now: retry later
+            x.par = ob.par;
+            x.lev = ob.lev;
+            G.pending.pop_front();
+            used += need;
+            x.state = Q_RUNNING;
+        }
+        Query &x = q[(size_t)t];
+        ++G.n_launch;
+        ++G.n_admit;
+        gb_status rc = gb::bfs_impl(G.g, x.root, x.par, x.lev, P.stats, P.stream, G.plain_blocks, P.ws);
+        if (rc == GB_OK && cudaEventRecord(P.ev, P.stream) != cudaSuccess) rc = GB_ERR_CUDA;
+        if (rc != GB_OK) {
+            std::lock_guard<std::mutex> lk(mu);
+            fault = rc;
+            fault_msg = gb::last_error();
+            done.notify_all();
+            return false;
+        }
+        P.q = t;
+        busy = true;
+    }
+    return busy;
+}
+
 // One pass over a graph: collect a finished level, retire, admit, launch the
 // next level.  Returns true if the graph has work in flight.
 bool gb_server::step_graph(GraphRun &G)
 {
+    if (G.plain) return step_plain(G);
     if (G.in_flight) {
         const cudaError_t e = cudaEventQuery(G.ev);
         if (e == cudaErrorNotReady) return true;
@@ -102,6 +225,7 @@ bool gb_server::step_graph(GraphRun &G)
         }
         const unsigned long long adv = G.host_ctl->anynew;
         const double t = now_s();
+        G.busy_s += t - G.t_launch;
         std::lock_guard<std::mutex> lk(mu);
         for (int b = 0; b < 64; ++b) {
             const unsigned long long bit = 1ull << b;
@@ -110,6 +234,7 @@ bool gb_server::step_graph(GraphRun &G)
                 x.state = Q_DONE;
                 x.t_done = t;
                 x.slot = -1;
+                if (tracing) finished.push_back(G.slot_q[b]);
                 G.active &= ~bit;
                 G.slot_q[b] = -1;
             }
@@ -129,13 +254,10 @@ bool gb_server::step_graph(GraphRun &G)
             Query &x = q[(size_t)t];
             int b = 0;
             while ((G.active >> b) & 1ull) ++b;
-            if (cudaMallocAsync((void **)&x.par, (size_t)G.g->n * 4, G.stream) != cudaSuccess ||
-                cudaMallocAsync((void **)&x.lev, (size_t)G.g->n * 4, G.stream) != cudaSuccess) {
-                if (x.par) cudaFreeAsync(x.par, G.stream);
-                x.par = nullptr;
-                x.lev = nullptr;
-                break;  // no device memory now: retry at the next boundary
-            }
+            OutBuf ob;
+            if (!take_out(G, ob)) break;  // no device memory now: retry at the next boundary
+            x.par = ob.par;
+            x.lev = ob.lev;
             G.pending.pop_front();
             used += need;
             cudaMemsetAsync(x.par, 0xff, (size_t)G.g->n * 4, G.stream);  // -1 everywhere
@@ -154,7 +276,10 @@ bool gb_server::step_graph(GraphRun &G)
     }
     gb_status rc = GB_OK;
     if (nadm) rc = gb::ms_serve_admit(G.ms, G.level, nadm, bits, roots, &G.slots, G.stream);
+    G.n_admit += nadm;
     if (rc == GB_OK && G.active) {
+        G.t_launch = now_s();
+        ++G.n_launch;
         rc = gb::ms_serve_step(G.ms, G.level, G.active, G.host_ctl, G.stream);
         if (rc == GB_OK && cudaEventRecord(G.ev, G.stream) != cudaSuccess) rc = GB_ERR_CUDA;
         if (rc == GB_OK) G.in_flight = true;
@@ -172,7 +297,10 @@ bool gb_server::step_graph(GraphRun &G)
 void gb_server::run()
 {
     cudaSetDevice(device);
+    int64_t iters = 0;
+    const double t_start = now_s();
     while (!stop.load()) {
+        ++iters;
         bool busy = false;
         for (auto &G : gr) busy |= step_graph(G);
         {
@@ -183,6 +311,14 @@ void gb_server::run()
             if (!busy && !waiting) cv.wait_for(lk, std::chrono::microseconds(200));
         }
         if (busy) std::this_thread::yield();
+    }
+    if (std::getenv("GB_SERVE_DEBUG")) {
+        std::fprintf(stderr, "[server] worker iterations %lld over %.3f s\n", (long long)iters,
+                     now_s() - t_start);
+        for (size_t i = 0; i < gr.size(); ++i)
+            std::fprintf(stderr, "[server] graph %zu n=%lld %s launches %lld admits %lld busy %.3f s\n",
+                         i, (long long)gr[i].g->n, gr[i].plain ? "single" : "batched",
+                         (long long)gr[i].n_launch, (long long)gr[i].n_admit, gr[i].busy_s);
     }
 }
 
@@ -201,8 +337,15 @@ gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb
     srv->device = ctx->device;
     srv->budget = mem_budget;
     srv->gr.resize(ng);
-    int64_t ntot = 0;
-    for (int i = 0; i < ng; ++i) ntot += gs[i] ? gs[i]->n : 0;
+    // GB_SERVE_PLAIN_MIN_SCALE overrides the size from which a graph is served
+    // one query per launch (1: every graph, 31: none).
+    int64_t plain_min = kPlainMinN;
+    if (const char *env = std::getenv("GB_SERVE_PLAIN_MIN_SCALE")) {
+        const int sc = std::atoi(env);
+        if (sc >= 0 && sc <= 31) plain_min = int64_t(1) << sc;
+    }
+    int64_t ntot = 0;  // vertices of the graphs batched as bits (the small ones)
+    for (int i = 0; i < ng; ++i) ntot += (gs[i] && gs[i]->n < plain_min) ? gs[i]->n : 0;
     gb_status rc = GB_OK;
     for (int i = 0; i < ng && rc == GB_OK; ++i) {
         GraphRun &G = srv->gr[i];
@@ -218,10 +361,27 @@ gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb
             G.slots.lev[b] = nullptr;
             G.slots.start[b] = 0;
         }
-        // every graph gets a share of the GPU proportional to its size, so
-        // that the levels of several graphs run side by side
-        const int blocks = (int)std::max<int64_t>(
-            8, (int64_t)ctx->ms_blocks * G.g->n / std::max<int64_t>(ntot, 1));
+        const bool full_grid = !std::getenv("GB_SERVE_SHARE_GPU");
+        if (G.g->n >= plain_min) {
+            G.plain = true;
+            G.plain_blocks = full_grid ? ctx->bfs_blocks2 : std::max(8, ctx->bfs_blocks2 / kPlainSlots);
+            for (int k = 0; k < kPlainSlots && rc == GB_OK; ++k) {
+                PlainSlot &P = G.ps[k];
+                if (cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&P.ev, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaMalloc((void **)&P.stats, sizeof(gb::BfsDevStats)) != cudaSuccess ||
+                    cudaMalloc((void **)&P.ws, gb::bfs_workspace_bytes(G.g)) != cudaSuccess) {
+                    gb::set_error("server_create: stream/event/stats buffer");
+                    rc = GB_ERR_CUDA;
+                }
+            }
+            continue;
+        }
+        // every batched graph gets a share of the GPU proportional to its
+        // size among the batched graphs, so that their levels run side by side
+        const int blocks = full_grid ? ctx->ms_blocks
+                                     : (int)std::max<int64_t>(
+                                           8, (int64_t)ctx->ms_blocks * G.g->n / std::max<int64_t>(ntot, 1));
         if (cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost((void **)&G.host_ctl, sizeof(gb::MsCtl)) != cudaSuccess) {
@@ -233,6 +393,12 @@ gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb
     }
     if (rc != GB_OK) {
         for (auto &G : srv->gr) {
+            for (auto &P : G.ps) {
+                if (P.ws) cudaFree(P.ws);
+                if (P.stats) cudaFree(P.stats);
+                if (P.ev) cudaEventDestroy(P.ev);
+                if (P.stream) cudaStreamDestroy(P.stream);
+            }
             if (G.ms) gb::ms_serve_destroy(G.ms);
             if (G.ev) cudaEventDestroy(G.ev);
             if (G.stream) cudaStreamDestroy(G.stream);
@@ -311,8 +477,7 @@ gb_status server_release(gb_server *srv, int64_t ticket)
         return GB_ERR_BUSY;
     }
     GraphRun &G = srv->gr[x.graph];
-    cudaFreeAsync(x.par, G.stream);
-    cudaFreeAsync(x.lev, G.stream);
+    G.free_out.push_back(OutBuf{x.par, x.lev});
     x.par = x.lev = nullptr;
     x.state = Q_RELEASED;
     srv->used -= out_bytes(G.g);
@@ -329,22 +494,32 @@ gb_status server_run_trace(gb_server *srv, int64_t nq, const double *t_arrival_s
         return GB_ERR_INVALID;
     }
     std::vector<int64_t> tickets((size_t)nq, -1);
-    const double t0 = now_s();
-    int64_t next = 0;
-    while (next < nq) {
-        const double due = t0 + t_arrival_s[next];
-        double t = now_s();
-        if (t < due) {
-            if (due - t > 200e-6)
-                std::this_thread::sleep_for(std::chrono::duration<double>(due - t - 100e-6));
-            continue;
-        }
-        // submit every query that has arrived, stamped with its arrival time
+    std::unordered_map<int64_t, int64_t> index;  // ticket -> position in the trace
+    {
         std::lock_guard<std::mutex> lk(srv->mu);
+        srv->finished.clear();
+        srv->tracing = true;
+    }
+    struct TraceEnd {
+        gb_server *s;
+        ~TraceEnd()
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->tracing = false;
+            s->finished.clear();
+        }
+    } trace_end{srv};
+    const double t0 = now_s();
+    int64_t next = 0, nfin = 0;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    while (nfin < nq) {
         if (srv->fault != GB_OK) {
             gb::set_error(srv->fault_msg);
             return srv->fault;
         }
+        // submit every query that has arrived, stamped with its arrival time
+        const double t = now_s();
+        bool submitted = false;
         while (next < nq && t0 + t_arrival_s[next] <= t) {
             const int gid = graph_id[next];
             if (gid < 0 || gid >= (int)srv->gr.size() || root[next] < 0 ||
@@ -358,38 +533,41 @@ gb_status server_run_trace(gb_server *srv, int64_t nq, const double *t_arrival_s
             x.t_arrive = t0 + t_arrival_s[next];
             srv->q.push_back(x);
             tickets[(size_t)next] = (int64_t)srv->q.size() - 1;
+            index[tickets[(size_t)next]] = next;
             srv->gr[gid].pending.push_back(tickets[(size_t)next]);
             ++next;
+            submitted = true;
         }
-        srv->cv.notify_one();
-    }
-    // wait for all of them, releasing results as they finish
-    int64_t finished = 0;
-    std::vector<char> seen((size_t)nq, 0);
-    std::unique_lock<std::mutex> lk(srv->mu);
-    while (finished < nq) {
-        if (srv->fault != GB_OK) {
-            gb::set_error(srv->fault_msg);
-            return srv->fault;
-        }
-        for (int64_t i = 0; i < nq; ++i) {
-            if (seen[(size_t)i]) continue;
-            Query &x = srv->q[(size_t)tickets[(size_t)i]];
-            if (x.state != Q_DONE) continue;
-            seen[(size_t)i] = 1;
-            ++finished;
+        if (submitted) srv->cv.notify_one();
+        // record and release the finished ones, so their memory admits new queries
+        std::vector<int64_t> got;
+        got.swap(srv->finished);
+        for (const int64_t tk : got) {
+            const auto it = index.find(tk);
+            if (it == index.end()) continue;  // a query submitted outside this trace
+            const int64_t i = it->second;
+            Query &x = srv->q[(size_t)tk];
+            ++nfin;
             latency_ms[i] = (x.t_done - x.t_arrive) * 1e3;
             if (!keep_results) {
                 GraphRun &G = srv->gr[x.graph];
-                cudaFreeAsync(x.par, G.stream);
-                cudaFreeAsync(x.lev, G.stream);
+                G.free_out.push_back(OutBuf{x.par, x.lev});
                 x.par = x.lev = nullptr;
                 x.state = Q_RELEASED;
                 srv->used -= out_bytes(G.g);
-                srv->cv.notify_one();
             }
         }
-        if (finished < nq) srv->done.wait_for(lk, std::chrono::milliseconds(1));
+        if (!got.empty()) srv->cv.notify_one();
+        if (nfin >= nq) break;
+        // sleep until the next arrival or a completion, whichever comes first
+        double wait = 1e-3;
+        if (next < nq) wait = std::min(wait, std::max(0.0, t0 + t_arrival_s[next] - now_s()));
+        if (wait > 20e-6) srv->done.wait_for(lk, std::chrono::duration<double>(wait));
+        else {
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        }
     }
     return GB_OK;
 }
@@ -401,15 +579,22 @@ gb_status server_destroy(gb_server *srv)
     srv->cv.notify_all();
     if (srv->worker.joinable()) srv->worker.join();
     cudaSetDevice(srv->device);
-    for (auto &x : srv->q) {
-        cudaStream_t st = srv->gr[x.graph].stream;
-        if (x.par) cudaFreeAsync(x.par, st);
-        if (x.lev) cudaFreeAsync(x.lev, st);
-    }
     for (auto &G : srv->gr) {
         if (G.stream) cudaStreamSynchronize(G.stream);
+        for (auto &P : G.ps)
+            if (P.stream) cudaStreamSynchronize(P.stream);
     }
     for (auto &G : srv->gr) {
+        for (auto &b : G.all_out) {
+            cudaFree(b.par);
+            cudaFree(b.lev);
+        }
+        for (auto &P : G.ps) {
+            if (P.ws) cudaFree(P.ws);
+            if (P.stats) cudaFree(P.stats);
+            if (P.ev) cudaEventDestroy(P.ev);
+            if (P.stream) cudaStreamDestroy(P.stream);
+        }
         if (G.ms) gb::ms_serve_destroy(G.ms);
         if (G.ev) cudaEventDestroy(G.ev);
         if (G.stream) cudaStreamDestroy(G.stream);

@@ -109,3 +109,29 @@ def test_submit_rejects_bad_queries(resident):
     with pytest.raises(gb.GbError, match="RANGE"):
         srv.submit(len(graphs), 0)
     srv.close()
+
+
+def test_large_graphs_run_one_search_per_query():
+    # graphs of 2^21+ vertices are served by concurrent single-source searches;
+    # their results follow the canonical_parents option like bfs() itself
+    gb.bfs_set_options(canonical_parents=1)
+    big = gb.graph_build_csr(gb.kron_generate(**W.GraphSpec(scale=21).kron_args()), 21)
+    small = gb.graph_build_csr(gb.kron_generate(**W.GraphSpec(scale=12).kron_args()), 12)
+    graphs = [small, big]
+    offs = [g.csr()[0].cpu().numpy() for g in graphs]
+    rng = np.random.default_rng(21)
+    queries = []
+    for _ in range(60):
+        gi = int(rng.integers(0, 2))
+        queries.append((gi, int(W.root_from_draw(offs[gi], rng.integers(0, 2**62, size=1))[0])))
+    srv = gb.Server(graphs, mem_budget=3 * 8 * big.n)   # at most three large-graph queries at once
+    tickets = [srv.submit(gi, r) for gi, r in queries]
+    for t, (gi, r) in zip(tickets, queries):
+        par, lev = srv.result(t, gi)
+        p_alone, l_alone = gb.bfs(graphs[gi], r)
+        assert torch.equal(lev, l_alone), (gi, r)
+        assert torch.equal(par, p_alone), (gi, r)
+        srv.release(t)
+    srv.close()
+    gb.bfs_set_options(canonical_parents=0)
+    gb.gb_device_status()
