@@ -41,10 +41,8 @@ namespace gb {
 namespace {
 
 constexpr int BFS_THREADS = 512;
-constexpr int BIG_CHUNK = 256;      // edges per chunk of a big frontier vertex
-constexpr int BU_LANE_MAX = 32;     // bottom-up: rows up to this length are scanned by one lane
-constexpr int BU_LANE_FIRST = 16;   // longer rows: one lane tests the first 16, then the warp
-constexpr int BU_BATCH = 8;         // neighbours whose loads one lane issues together
+constexpr int BIG_CHUNK = 128;      // edges per chunk of a big frontier vertex (one round)
+constexpr int BU_LANE_FIRST = 4;    // bottom-up: each lane probes this many neighbours itself
 constexpr int BFS_WARPS = BFS_THREADS / 32;
 constexpr int QBUF = 256;           // per-warp buffer of discovered vertices (shared memory)
 constexpr int BBUF = 32;            // per-warp buffer of discovered big-degree vertices
@@ -243,6 +241,94 @@ __device__ __forceinline__ void td_visit(const bool (&valid)[TD_E], const int32_
         append_next(won[t], v[t], dv[t], a, wb, qn, bn, my_mf, nxt, qnext_base, bnext_base);
 }
 
+// Warp-collective: the row tails [j, e) of the lanes with `open` are scanned
+// together.  Each round deals 4 x 32 neighbour slots, an equal share to every
+// row still open (consecutive slots of a row are consecutive CSR entries), so
+// rows that find their parent leave and the loads of a round are all in
+// flight at once.  The first slot of a row whose neighbour is in the frontier
+// gives the smallest-id parent.
+__device__ __forceinline__ void bu_stream_rows(const BfsArgs &a, const unsigned *F, bool open,
+                                               int64_t j, int64_t e, int32_t &found,
+                                               unsigned long long &my_edges)
+{
+    const int lane = (int)lane_id();
+    while (true) {
+        const bool act = open && found < 0 && j < e;
+        const unsigned am = __ballot_sync(kFull, act);
+        if (!am) break;
+        const int q = 128 / __popc(am);
+        const int64_t rem = act ? e - j : 0;
+        const int len = (int)(rem < q ? rem : q);
+        const int incl = warp_inclusive_scan(len);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - len;
+        int32_t vv[4];
+        unsigned fw[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int k = t * 32 + lane;
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int c = o + step;
+                if (__shfl_sync(kFull, excl, c) <= k) o = c;
+            }
+            const int64_t jo = __shfl_sync(kFull, j, o);
+            const int eo = __shfl_sync(kFull, excl, o);
+            const int64_t pos = jo + (k - eo);
+            vv[t] = k < total && GB_OK_IDX(a.st, pos, a.nnz, 218) ? __ldg(&a.col[pos]) : -1;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            fw[t] = vv[t] >= 0 && GB_OK_IDX(a.st, vv[t], a.n, 219) ? ldcg_u32(&F[vv[t] >> 5]) : 0u;
+        // each row owner looks for the first hit among its slots, group by group
+        int32_t got = -1;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const bool h = vv[t] >= 0 && ((fw[t] >> (vv[t] & 31)) & 1u);
+            const unsigned hm = __ballot_sync(kFull, h);
+            const int a0 = excl - t * 32, a1 = excl + len - t * 32;
+            const int lo = a0 > 0 ? a0 : 0, hi = a1 < 32 ? a1 : 32;
+            unsigned seg = 0;
+            if (len > 0 && hi > lo) seg = (hi >= 32 ? kFull : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+            const unsigned mine = hm & seg;
+            const int fl = mine ? __ffs(mine) - 1 : 0;
+            const int32_t cand = __shfl_sync(kFull, vv[t], fl);
+            if (got < 0 && mine) {
+                got = cand;
+                my_edges += (unsigned long long)(32 * t + fl - excl + 1);
+            }
+        }
+        if (got >= 0) {
+            found = got;
+        } else {
+            my_edges += (unsigned long long)len;
+            j += len;
+        }
+    }
+}
+
+// Warp-collective: the lanes of visited word w that found a parent write it,
+// join the visited set and the next frontier (the warp owns the word).
+__device__ __forceinline__ void bu_commit_word(const BfsArgs &a, unsigned *Fn, int64_t w,
+                                               unsigned vw, int64_t u, int32_t found, int32_t deg,
+                                               int l, WarpBuf &wbuf, int &qn, int &bn,
+                                               unsigned long long &my_mf, LevelCtl *nxt,
+                                               int64_t qnext_base, int64_t bnext_base)
+{
+    const bool won = found >= 0 && GB_OK_IDX(a.st, u, a.n, 215);
+    if (won) {
+        a.parent[u] = found;
+        a.level[u] = l + 1;
+    }
+    const unsigned nm = __ballot_sync(kFull, won);
+    if (nm && lane_id() == 0) {
+        __stcg(&a.vis[w], vw | nm);
+        __stcg(&Fn[w], nm);
+    }
+    append_next(won, (int32_t)u, deg, a, wbuf, qn, bn, my_mf, nxt, qnext_base, bnext_base);
+}
+
 // MINB = blocks of BFS_THREADS per SM the register budget is sized for:
 // 2 (64 registers, no spills) or 3 (40 registers, more warps to hide latency).
 template <int MINB>
@@ -435,100 +521,75 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                 }
             }
         } else {
-            // bottom-up: warp w owns the 32 vertices of visited word w
-            for (int64_t w = gwarp; w < nw; w += nwarps) {
-                const unsigned vw = ldcg_u32(&a.vis[w]);
-                if (vw == kFull) continue;
-                const int64_t u = w * 32 + lane;
-                const bool cand = !((vw >> lane) & 1u);
-                int64_t s = 0, e = 0;
-                if (cand && GB_OK_IDX(a.st, u, a.n, 216)) {
-                    s = a.off[u];
-                    e = a.off[u + 1];
+            // bottom-up: a warp takes two visited words (64 vertices) at a time,
+            // lane i owning vertex i of each; both words' visited bits, row
+            // offsets and neighbour probes are issued together.
+            for (int64_t wa = gwarp; wa < nw; wa += 2 * nwarps) {
+                const int64_t wb2 = wa + nwarps;
+                const bool has_b = wb2 < nw;
+                const unsigned vwa = ldcg_u32(&a.vis[wa]);
+                const unsigned vwb = has_b ? ldcg_u32(&a.vis[wb2]) : kFull;
+                const int64_t ua = wa * 32 + lane, ub = wb2 * 32 + lane;
+                int64_t sa = 0, ea = 0, sb = 0, eb = 0;
+                if (ua < n) {
+                    sa = __ldg(&a.off[ua]);
+                    ea = __ldg(&a.off[ua + 1]);
                 }
-                const int64_t deg = e - s;
-                int32_t found = -1;
-                int64_t j = s;
-                if (cand) {
-                    // one lane, neighbours in ascending order, BU_BATCH loads in flight
-                    const int64_t jl = deg <= BU_LANE_MAX ? e : s + BU_LANE_FIRST;
-                    int64_t hit = -1;
-                    while (j < jl) {
-                        int32_t vv[BU_BATCH];
-                        unsigned fw[BU_BATCH];
+                if (has_b && ub < n) {
+                    sb = __ldg(&a.off[ub]);
+                    eb = __ldg(&a.off[ub + 1]);
+                }
+                if (vwa == kFull && vwb == kFull) continue;
+                const bool ca = !((vwa >> lane) & 1u) && GB_OK_IDX(a.st, ua, a.n, 216);
+                const bool cb = !((vwb >> lane) & 1u) && GB_OK_IDX(a.st, ub, a.n, 217);
+                if (!ca) sa = ea = 0;
+                if (!cb) sb = eb = 0;
+                my_touched += (unsigned)ca + (unsigned)cb;
+                // one lane probes both rows in ascending order, 4 + 4 loads in flight
+                const int32_t da = (int32_t)(ea - sa), db = (int32_t)(eb - sb);
+                const int32_t la = da < BU_LANE_FIRST ? da : BU_LANE_FIRST;
+                const int32_t lb = db < BU_LANE_FIRST ? db : BU_LANE_FIRST;
+                int32_t fa = -1, fb = -1, ja = 0, jb = 0;
+                while ((fa < 0 && ja < la) || (fb < 0 && jb < lb)) {
+                    int32_t vv[8];
+                    unsigned fw[8];
 #pragma unroll
-                        for (int t = 0; t < BU_BATCH; ++t)
-                            vv[t] = j + t < jl && GB_OK_IDX(a.st, j + t, a.nnz, 211) ? __ldg(&a.col[j + t]) : -1;
-#pragma unroll
-                        for (int t = 0; t < BU_BATCH; ++t)
-                            fw[t] = vv[t] >= 0 && GB_OK_IDX(a.st, vv[t], a.n, 212) ? ldcg_u32(&F[vv[t] >> 5]) : 0u;
-#pragma unroll
-                        for (int t = 0; t < BU_BATCH; ++t)
-                            if (hit < 0 && vv[t] >= 0 && ((fw[t] >> (vv[t] & 31)) & 1u)) {
-                                hit = j + t;
-                                found = vv[t];
-                            }
-                        if (hit >= 0) break;
-                        j += BU_BATCH;
+                    for (int t = 0; t < 4; ++t) {
+                        vv[t] = fa < 0 && ja + t < la && GB_OK_IDX(a.st, sa + ja + t, a.nnz, 211)
+                                    ? __ldg(&a.col[sa + ja + t]) : -1;
+                        vv[4 + t] = fb < 0 && jb + t < lb && GB_OK_IDX(a.st, sb + jb + t, a.nnz, 211)
+                                        ? __ldg(&a.col[sb + jb + t]) : -1;
                     }
-                    if (j > jl) j = jl;
-                    my_edges += hit >= 0 ? (unsigned long long)(hit - s + 1) : (unsigned long long)(j - s);
-                }
-                my_touched += cand;
-                // rows left unresolved: the whole warp scans the rest, 32 per round
-                unsigned bigm = __ballot_sync(kFull, cand && found < 0 && j < e);
-                while (bigm) {
-                    const int jl = __ffs(bigm) - 1;
-                    bigm &= bigm - 1;
-                    const int64_t sj = __shfl_sync(kFull, j, jl);
-                    const int64_t ej = __shfl_sync(kFull, e, jl);
-                    int32_t fj = -1;
-                    int64_t scanned = 0;
-                    for (int64_t b = sj; b < ej; b += 128) {
-                        // lane i tests entries b+4i .. b+4i+3: 128 loads in flight per round
-                        int32_t vv[4];
-                        unsigned fw[4];
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const int64_t jj = b + 4 * lane + t;
-                            vv[t] = jj < ej && GB_OK_IDX(a.st, jj, a.nnz, 213) ? __ldg(&a.col[jj]) : -1;
-                        }
+                    for (int t = 0; t < 8; ++t)
+                        fw[t] = vv[t] >= 0 && GB_OK_IDX(a.st, vv[t], a.n, 212) ? ldcg_u32(&F[vv[t] >> 5]) : 0u;
+                    int32_t ha = -1, hb = -1;
 #pragma unroll
-                        for (int t = 0; t < 4; ++t)
-                            fw[t] = vv[t] >= 0 && GB_OK_IDX(a.st, vv[t], a.n, 214) ? ldcg_u32(&F[vv[t] >> 5]) : 0u;
-                        int first = -1;
-                        int32_t hv = 0;
-#pragma unroll
-                        for (int t = 0; t < 4; ++t)
-                            if (first < 0 && vv[t] >= 0 && ((fw[t] >> (vv[t] & 31)) & 1u)) {
-                                first = t;
-                                hv = vv[t];
-                            }
-                        const unsigned hb = __ballot_sync(kFull, first >= 0);
-                        if (hb) {
-                            const int fl = __ffs(hb) - 1;
-                            fj = __shfl_sync(kFull, hv, fl);
-                            scanned += 4 * fl + __shfl_sync(kFull, first, fl) + 1;
-                            break;
-                        }
-                        scanned += (ej - b < 128 ? ej - b : 128);
+                    for (int t = 0; t < 4; ++t) {
+                        if (ha < 0 && vv[t] >= 0 && ((fw[t] >> (vv[t] & 31)) & 1u)) ha = t;
+                        if (hb < 0 && vv[4 + t] >= 0 && ((fw[4 + t] >> (vv[4 + t] & 31)) & 1u)) hb = t;
                     }
-                    if ((int)lane == jl) {
-                        found = fj;
-                        my_edges += scanned;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {  // select without indexing registers
+                        if (ha == t) fa = vv[t];
+                        if (hb == t) fb = vv[4 + t];
                     }
+                    if (fa < 0 && ja < la) ja += 4;
+                    else if (ha >= 0) ja += ha + 1;
+                    if (fb < 0 && jb < lb) jb += 4;
+                    else if (hb >= 0) jb += hb + 1;
                 }
-                const bool won = found >= 0 && GB_OK_IDX(a.st, u, a.n, 215);
-                if (won) {
-                    a.parent[u] = found;
-                    a.level[u] = l + 1;
-                }
-                const unsigned nm = __ballot_sync(kFull, won);
-                if (nm && lane == 0) {
-                    __stcg(&a.vis[w], vw | nm);
-                    __stcg(&Fn[w], nm);
-                }
-                append_next(won, (int32_t)u, deg, a, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
+                ja = ja < la ? ja : la;
+                jb = jb < lb ? jb : lb;
+                my_edges += (unsigned long long)(ja + jb);
+                // rows left unresolved: scanned together as one stream
+                bu_stream_rows(a, F, ca && fa < 0 && la < da, sa + la, ea, fa, my_edges);
+                bu_stream_rows(a, F, cb && fb < 0 && lb < db, sb + lb, eb, fb, my_edges);
+                bu_commit_word(a, Fn, wa, vwa, ua, fa, da, l, wb, qn_buf, bn_buf, my_mf, nxt,
+                               qnext_base, bnext_base);
+                if (has_b)
+                    bu_commit_word(a, Fn, wb2, vwb, ub, fb, db, l, wb, qn_buf, bn_buf, my_mf, nxt,
+                                   qnext_base, bnext_base);
             }
         }
         // end of level: flush the staged vertices and add the block's degree sum
