@@ -215,6 +215,7 @@ gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *
             if (g->off) cudaFree(g->off);
             if (g->col) cudaFree(g->col);
             if (g->nz) cudaFree(g->nz);
+            if (g->hub) cudaFree(g->hub);
             delete g;
             return rc;
         }
@@ -270,12 +271,13 @@ gb_status graph_from_csr(const int64_t *off, const int32_t *col, int64_t n, int6
             delete g;
             return cuda_fail(e, "graph_from_csr");
         }
-        gb_status rc = build_nz_bitmap(g, st);
+        gb_status rc = build_graph_aux(g, st);
         if (rc == GB_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "graph_from_csr");
         if (rc != GB_OK) {
             cudaFree(g->off);
             cudaFree(g->col);
             if (g->nz) cudaFree(g->nz);
+            if (g->hub) cudaFree(g->hub);
             delete g;
             return rc;
         }
@@ -292,9 +294,11 @@ gb_status graph_free(gb_graph *g)
         if (g->off) cudaFree(g->off);
         if (g->col) cudaFree(g->col);
         if (g->nz) cudaFree(g->nz);
+        if (g->hub) cudaFree(g->hub);
         g->off = nullptr;
         g->col = nullptr;
         g->nz = nullptr;
+        g->hub = nullptr;
         delete g;
         return GB_OK;
     });

@@ -84,6 +84,7 @@ struct BfsArgs {
     const int64_t *off;
     const int32_t *col;
     const uint32_t *nz;  // degree >= 1 bitmap
+    const int32_t *hub;  // per vertex a neighbour of largest degree (-1: none); null: unused
     int64_t n;
     int64_t nnz;
     int32_t root;
@@ -522,34 +523,46 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
             }
         } else {
             // bottom-up: a warp takes two visited words (64 vertices) at a time,
-            // lane i owning vertex i of each; both words' visited bits, row
-            // offsets and neighbour probes are issued together.
+            // lane i owning vertex i of each; both words' row offsets, then
+            // their neighbour probes, are issued together.
             for (int64_t wa = gwarp; wa < nw; wa += 2 * nwarps) {
                 const int64_t wb2 = wa + nwarps;
                 const bool has_b = wb2 < nw;
                 const unsigned vwa = ldcg_u32(&a.vis[wa]);
                 const unsigned vwb = has_b ? ldcg_u32(&a.vis[wb2]) : kFull;
+                if (vwa == kFull && vwb == kFull) continue;
                 const int64_t ua = wa * 32 + lane, ub = wb2 * 32 + lane;
+                // row offsets of unvisited lanes only: late levels, where most
+                // vertices are visited, then skip most of the offset array
+                const bool ca = !((vwa >> lane) & 1u) && GB_OK_IDX(a.st, ua, a.n, 216);
+                const bool cb = !((vwb >> lane) & 1u) && GB_OK_IDX(a.st, ub, a.n, 217);
                 int64_t sa = 0, ea = 0, sb = 0, eb = 0;
-                if (ua < n) {
+                if (ca) {
                     sa = __ldg(&a.off[ua]);
                     ea = __ldg(&a.off[ua + 1]);
                 }
-                if (has_b && ub < n) {
+                if (cb) {
                     sb = __ldg(&a.off[ub]);
                     eb = __ldg(&a.off[ub + 1]);
                 }
-                if (vwa == kFull && vwb == kFull) continue;
-                const bool ca = !((vwa >> lane) & 1u) && GB_OK_IDX(a.st, ua, a.n, 216);
-                const bool cb = !((vwb >> lane) & 1u) && GB_OK_IDX(a.st, ub, a.n, 217);
-                if (!ca) sa = ea = 0;
-                if (!cb) sb = eb = 0;
+                // the hub first: a hit is a parent at the cost of one L2 lookup,
+                // and the row's first neighbours need not be fetched from DRAM
+                int32_t fa = -1, fb = -1;
+                if (a.hub) {
+                    const int32_t hua = ca ? __ldg(&a.hub[ua]) : -1;
+                    const int32_t hub_b = cb ? __ldg(&a.hub[ub]) : -1;
+                    const unsigned fha = hua >= 0 && GB_OK_IDX(a.st, hua, a.n, 220) ? ldcg_u32(&F[hua >> 5]) : 0u;
+                    const unsigned fhb = hub_b >= 0 && GB_OK_IDX(a.st, hub_b, a.n, 221) ? ldcg_u32(&F[hub_b >> 5]) : 0u;
+                    if (hua >= 0 && ((fha >> (hua & 31)) & 1u)) fa = hua;
+                    if (hub_b >= 0 && ((fhb >> (hub_b & 31)) & 1u)) fb = hub_b;
+                    my_edges += (unsigned long long)(hua >= 0) + (unsigned long long)(hub_b >= 0);
+                }
                 my_touched += (unsigned)ca + (unsigned)cb;
                 // one lane probes both rows in ascending order, 4 + 4 loads in flight
                 const int32_t da = (int32_t)(ea - sa), db = (int32_t)(eb - sb);
                 const int32_t la = da < BU_LANE_FIRST ? da : BU_LANE_FIRST;
                 const int32_t lb = db < BU_LANE_FIRST ? db : BU_LANE_FIRST;
-                int32_t fa = -1, fb = -1, ja = 0, jb = 0;
+                int32_t ja = 0, jb = 0;
                 while ((fa < 0 && ja < la) || (fb < 0 && jb < lb)) {
                     int32_t vv[8];
                     unsigned fw[8];
@@ -700,6 +713,8 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.off = g->off;
     a.col = g->col;
     a.nz = g->nz;
+    // the hub test finds some parent, not the smallest-id one
+    a.hub = o.canonical_parents ? nullptr : g->hub;
     a.n = n;
     a.nnz = g->nnz;
     a.root = (int32_t)root;
@@ -839,6 +854,7 @@ gb_status bfs_noalloc_impl(const int64_t *off, const int32_t *col, int64_t n, in
     a.off = off;
     a.col = col;
     a.nz = reinterpret_cast<const uint32_t *>(ws + kNaNz);
+    a.hub = nullptr;
     a.n = n;
     a.nnz = nnz;
     a.root = (int32_t)root;

@@ -10,6 +10,11 @@
 //   4. the write pass stores the columns and, at every change of row between
 //      neighbouring keys, the offsets of all rows in between: an empty row
 //      repeats the previous offset and off[n] = nnz (Sec. 2.2).
+//
+// Two per-vertex arrays that the search consults are derived from the CSR:
+// the degree >= 1 bitmap, and for every row of degree <= HUB_MAX_DEG one of
+// its neighbours of largest degree (the "hub" that the bottom-up step tests
+// first: a neighbour with many edges is the likeliest to sit in the frontier).
 #include "common.cuh"
 #include "internal.h"
 
@@ -159,9 +164,87 @@ __global__ void nz_bitmap_kernel(const int64_t *__restrict__ off, int64_t n,
     }
 }
 
+constexpr int HUB_THREADS = 256;
+constexpr int64_t HUB_MAX_DEG = 4096;  // longer rows get no hub (hubs are visited early)
+
+// An 8-bit increasing key of the degree: 8 * floor(log2 d) + the next three
+// bits of d, plus one (0 for an empty row).
+__global__ void deg_key_kernel(const int64_t *__restrict__ off, int64_t n, uint8_t *__restrict__ key)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t d = off[v + 1] - off[v];
+        unsigned k = 0;
+        if (d > 0) {
+            const int e = 63 - __clzll(d);
+            const unsigned m = e >= 3 ? (unsigned)(d >> (e - 3)) & 7u : (unsigned)(d << (3 - e)) & 7u;
+            k = (unsigned)e * 8u + m + 1u;
+            if (k > 255u) k = 255u;
+        }
+        key[v] = (uint8_t)k;
+    }
+}
+
+// hub[u] = the neighbour of u with the largest degree key, the smallest id
+// among equals; -1 for an empty row or one longer than HUB_MAX_DEG.  A warp
+// takes 32 rows and streams their edges as one sequence (lane k of a round
+// reads entry k), each edge folded into its row's slot with a shared-memory
+// atomic max of (key << 32 | ~v).
+__global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const int64_t *__restrict__ off,
+                                                          const int32_t *__restrict__ col,
+                                                          const uint8_t *__restrict__ key, int64_t n,
+                                                          int64_t nnz, int32_t *__restrict__ hub,
+                                                          DevStatus *st)
+{
+    __shared__ unsigned long long s_best[HUB_THREADS];
+    const unsigned lane = threadIdx.x & 31u;
+    const int wbase = threadIdx.x & ~31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = gwarp * 32; r0 < n; r0 += nwarps * 32) {
+        const int64_t r = r0 + lane;
+        int64_t s0 = 0, d = 0;
+        if (r < n) {
+            s0 = off[r];
+            d = off[r + 1] - s0;
+            if (d > HUB_MAX_DEG || d < 0 || s0 < 0 || s0 + d > nnz) d = 0;
+        }
+        s_best[threadIdx.x] = 0;
+        __syncwarp();
+        const int64_t incl = warp_inclusive_scan(d);
+        const int64_t total = __shfl_sync(kFull, incl, 31);
+        const int64_t excl = incl - d;
+        for (int64_t b = 0; b < total; b += 32) {
+            const int64_t k = b + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int cand = owner + step;
+                if (__shfl_sync(kFull, excl, cand) <= k) owner = cand;
+            }
+            const int64_t so = __shfl_sync(kFull, s0, owner);
+            const int64_t eo = __shfl_sync(kFull, excl, owner);
+            if (k < total) {
+                const int32_t v = col[so + (k - eo)];
+                if (v >= 0 && v < n) {
+                    const unsigned long long kv = ((unsigned long long)key[v] << 32) |
+                                                  (unsigned long long)(0xffffffffu - (uint32_t)v);
+                    atomicMax(&s_best[wbase + owner], kv);
+                } else {
+                    record_error(st, GB_ERR_RANGE, 12, v);
+                }
+            }
+        }
+        __syncwarp();
+        const unsigned long long best = s_best[threadIdx.x];
+        if (r < n) hub[r] = best ? (int32_t)(0xffffffffu - (uint32_t)(best & 0xffffffffull)) : -1;
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
-gb_status build_nz_bitmap(gb_graph *g, cudaStream_t s)
+gb_status build_graph_aux(gb_graph *g, cudaStream_t s)
 {
     Context *ctx = context();
     if (!ctx) return GB_ERR_CUDA;
@@ -170,6 +253,16 @@ gb_status build_nz_bitmap(gb_graph *g, cudaStream_t s)
     nz_bitmap_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->off, g->n, g->nz, nw);
     note_launch();
     GB_CUDA(cudaGetLastError());
+    GB_CUDA(cudaMalloc(&g->hub, std::max<int64_t>(g->n, 1) * sizeof(int32_t)));
+    uint8_t *key = nullptr;
+    GB_CUDA(alloc_async(&key, (size_t)g->n, s));
+    deg_key_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->off, g->n, key);
+    note_launch();
+    hub_kernel<<<ctx->num_sms * 8, HUB_THREADS, 0, s>>>(g->off, g->col, key, g->n, g->nnz, g->hub,
+                                                        ctx->status);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
+    GB_CUDA(cudaFreeAsync(key, s));
     return GB_OK;
 }
 
@@ -188,7 +281,7 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
         GB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(int64_t)));
         GB_CUDA(cudaMalloc(&g->col, 16));
         GB_CUDA(cudaMemsetAsync(g->off, 0, (n + 1) * sizeof(int64_t), s));
-        gb_status r0 = build_nz_bitmap(g, s);
+        gb_status r0 = build_graph_aux(g, s);
         if (r0 != GB_OK) return r0;
         GB_CUDA(cudaStreamSynchronize(s));
         return GB_OK;
@@ -239,7 +332,7 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
     GB_CUDA(cudaFreeAsync(k1, s));
     GB_CUDA(cudaFreeAsync(tcnt, s));
     GB_CUDA(cudaFreeAsync(tbase, s));
-    return build_nz_bitmap(g, s);
+    return build_graph_aux(g, s);
 }
 
 }  // namespace gb

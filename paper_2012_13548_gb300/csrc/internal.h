@@ -81,6 +81,7 @@ struct gb_graph {
     int64_t *off = nullptr;  // device [n+1]
     int32_t *col = nullptr;  // device [nnz]
     uint32_t *nz = nullptr;  // device [ceil(n/32)]: bit v set iff degree(v) >= 1
+    int32_t *hub = nullptr;  // device [n]: a neighbour of v of largest degree, or -1
     int device = -1;
 };
 
@@ -88,8 +89,8 @@ namespace gb {
 
 // Kernel 1 pieces (csr.cu).
 gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s);
-// The degree >= 1 bitmap of a graph whose off array is in place (csr.cu).
-gb_status build_nz_bitmap(gb_graph *g, cudaStream_t s);
+// The degree >= 1 bitmap and the hub array of a graph whose CSR is in place (csr.cu).
+gb_status build_graph_aux(gb_graph *g, cudaStream_t s);
 
 // Kronecker generator (gen.cu).
 gb_status kron_generate_impl(int scale, int edgefactor, double a, double b, double c,
