@@ -27,7 +27,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_TABLE = os.path.join(HERE, "tune_table.json")
 
 PLAIN_SPACE = {
-    "alpha": [2.0, 4.0, 8.0, 14.0, 32.0, 64.0],
+    "alpha": [2.0, 4.0, 8.0, 14.0, 32.0, 64.0, 128.0, 256.0, 1024.0],
     "beta": [6.0, 12.0, 24.0, 64.0, 256.0],
     "big_degree": [64, 256, 1024, 4096],
     "blocks_per_sm": [2, 3],
