@@ -276,13 +276,16 @@ def run_ours(args, dist):
     L = torch.empty((len(roots), n), dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
-    # TEPS numerators and per-root counters (bookkeeping, outside the timed region)
-    m_r, stats = [], []
-    src = edges[0]
+    # TEPS numerators, per-root counters and the Graph500 validation of every
+    # root's tree on the device (bookkeeping, outside the timed region)
+    m_r, stats, invalid = [], [], []
     for r in roots:
         gb.bfs(g, int(r), parent, level)
         stats.append(gb.bfs_last_stats())
-        m_r.append(int((level[src] >= 0).sum().item()))
+        v = gb.bfs_validate(g, int(r), parent, level, edges)
+        m_r.append(v["teps_edges"])
+        if v["code"] != 0:
+            invalid.append((int(r), v["code"], v["where"]))
     gb.gb_device_status()
 
     def step(rec):
@@ -330,6 +333,14 @@ def run_ours(args, dist):
     total_ms = t_all0.elapsed_time(t_all1)
     for r in rec:
         r[5].free()
+
+    # the batched search's rows (from the last timed step) validated too
+    batch_invalid = []
+    for i, r in enumerate(roots):
+        v = gb.bfs_validate(g, int(r), P[i], L[i])
+        if v["code"] != 0:
+            batch_invalid.append((int(r), v["code"], v["where"]))
+    n_invalid = int(dist.max(float(len(invalid) + len(batch_invalid))))
 
     bfs_ms = [[a.elapsed_time(b) for (a, b) in r[2]] for r in rec]
     k1_ms = [r[0].elapsed_time(r[1]) for r in rec]
@@ -379,6 +390,9 @@ def run_ours(args, dist):
                 "kernel1": {"ms": statistics.median(k1_ms),
                             "gbs": k1_bytes / (statistics.median(k1_ms) * 1e-3) / 1e9,
                             "alg_bytes": k1_bytes},
+                "validation": {"on": "device (bfs_validate, Graph500 rules 1-7)",
+                               "trees": 2 * len(roots) * dist.world, "invalid_max_per_rank": n_invalid,
+                               "first_failures": (invalid + batch_invalid)[:4]},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                "p99": float(np.percentile(lat, 99))},
                 "graph": {"n": n, "nnz": g.nnz, "m": int(edges.shape[1]),

@@ -241,6 +241,52 @@ typedef struct gb_bfs_stats {
 gb_status bfs_last_stats(gb_bfs_stats *out);
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 2 outline step 5: validation of a search and its TEPS numerator.     */
+/* ------------------------------------------------------------------------ */
+
+/* Verdict of bfs_validate.
+ *   code  0 if the output is a valid BFS of g from root, else the first
+ *         failing rule of the Graph500 result validation, in the order a
+ *         serial check over the vertices, the vertices again and then the
+ *         CSR entries meets them:
+ *           1  parent(root) != root or level(root) != 0
+ *           2  parent(v) = -1 while level(v) != -1, or the reverse
+ *           3  a reached v != root whose parent is not a neighbour
+ *           4  a reached v != root with level(parent(v)) != level(v) - 1
+ *           5  a graph edge with exactly one reached endpoint
+ *           6  a graph edge whose endpoint levels differ by more than one
+ *           7  root outside [0, n), a parent outside [-1, n) or a level < -1
+ *   where  the vertex (rules 1-4, 7) or CSR entry index (5, 6) of that
+ *          failure, -1 if code is 0
+ *   reached          vertices with level >= 0
+ *   component_edges  undirected simple edges among the reached vertices
+ *                    (half the CSR entries of their rows)
+ *   teps_edges       input tuples whose start vertex is reached, duplicates
+ *                    and self-loops included (Sec. 4.3, the Graph500 TEPS
+ *                    numerator); -1 when no tuples were given
+ *   max_level        largest level, -1 if none */
+typedef struct gb_validation {
+    int32_t code;
+    int32_t max_level;
+    int64_t where;
+    int64_t reached;
+    int64_t component_edges;
+    int64_t teps_edges;
+} gb_validation;
+
+/* Check parent and level (device int32 [n], as written by bfs or one row of
+ * bfs_batch) against g and root on the device, and count the TEPS numerator
+ * over edges (device int64 [2][m] input tuples; NULL with m = 0 to skip).
+ * Rows of g must be sorted (every graph this library builds is).  Values
+ * outside their range are reported as rule 7, never dereferenced.
+ * Synchronises s; *out (host) receives the verdict.  Returns GB_OK whenever
+ * the check ran, whatever its verdict; GB_ERR_INVALID for NULL arguments or
+ * m < 0. */
+gb_status bfs_validate(const gb_graph *g, int64_t root, const int32_t *parent,
+                       const int32_t *level, const int64_t *edges, int64_t m,
+                       gb_validation *out, gb_stream s);
+
+/* ------------------------------------------------------------------------ */
 /* Serving: resident graphs, BFS queries admitted as they arrive.            */
 /* ------------------------------------------------------------------------ */
 

@@ -45,6 +45,12 @@ class gb_bfs_stats(ctypes.Structure):
                                   ("level_dir", ctypes.c_int32 * GB_STAT_LEVELS)]
 
 
+class gb_validation(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int32), ("max_level", ctypes.c_int32), ("where", ctypes.c_int64),
+                ("reached", ctypes.c_int64), ("component_edges", ctypes.c_int64),
+                ("teps_edges", ctypes.c_int64)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -81,6 +87,8 @@ def lib():
                                                ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
             "bfs_last_stats": (ctypes.c_int, [ctypes.POINTER(gb_bfs_stats)]),
             "bfs_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp]),
+            "bfs_validate": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp, _i64,
+                                            ctypes.POINTER(gb_validation), _vp]),
             "server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t,
                                              ctypes.POINTER(_vp)]),
             "server_submit": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.POINTER(_i64)]),
@@ -102,7 +110,7 @@ def exported_symbols():
     return ["gb_last_error", "gb_abi_version", "gb_kernel_launches", "gb_device_status", "kron_generate",
             "graph_build_csr", "graph_from_csr", "graph_free", "graph_info", "graph_csr_view",
             "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
-            "bfs_last_stats", "bfs_noalloc", "server_create", "server_submit", "server_poll", "server_release",
+            "bfs_last_stats", "bfs_noalloc", "bfs_validate", "server_create", "server_submit", "server_poll", "server_release",
             "server_run_trace", "server_destroy"]
 
 
@@ -296,6 +304,27 @@ def bfs_noalloc(off, col, root, parent, level, stream=None):
                              n, col.numel(), int(root), _dev(parent, torch.int32, "parent"),
                              _dev(level, torch.int32, "level"), _stream(stream)))
     return parent, level
+
+
+def bfs_validate(graph, root, parent, level, edges=None, stream=None):
+    """Graph500 validation of one search on the device (synchronises the
+    stream).  parent/level: int32 [n] CUDA tensors; edges: the int64 [2, m]
+    input tuples for the TEPS numerator, or None.  Returns a dict with code
+    (0 = valid, else the first failing rule 1..7), where, reached,
+    component_edges, teps_edges (-1 without edges) and max_level."""
+    if parent.numel() != graph.n or level.numel() != graph.n:
+        raise ValueError("parent/level must have n = %d entries" % graph.n)
+    if edges is not None:
+        if edges.dim() != 2 or edges.shape[0] != 2:
+            raise ValueError("edges must be a [2, m] tensor")
+        ep, m = _dev(edges, torch.int64, "edges"), int(edges.shape[1])
+    else:
+        ep, m = ctypes.c_void_p(None), 0
+    out = gb_validation()
+    _check(lib().bfs_validate(graph.handle, int(root), _dev(parent, torch.int32, "parent"),
+                              _dev(level, torch.int32, "level"), ep, m, ctypes.byref(out),
+                              _stream(stream)))
+    return {f: getattr(out, f) for f, _ in gb_validation._fields_}
 
 
 def bfs_last_stats():

@@ -418,6 +418,19 @@ gb_status bfs_multi_graph(const gb_graph *const *gs, int ng, const int64_t *root
     });
 }
 
+gb_status bfs_validate(const gb_graph *g, int64_t root, const int32_t *parent,
+                       const int32_t *level, const int64_t *edges, int64_t m,
+                       gb_validation *out, gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        if (!g || !parent || !level || !out || m < 0 || (m > 0 && !edges)) {
+            set_error("bfs_validate: need g, parent, level, out != NULL, m >= 0, edges != NULL if m > 0");
+            return GB_ERR_INVALID;
+        }
+        return validate_impl(g, root, parent, level, m > 0 ? edges : nullptr, m, out, as_stream(s));
+    });
+}
+
 gb_status bfs_last_stats(gb_bfs_stats *out)
 {
     return guarded([&]() -> gb_status {

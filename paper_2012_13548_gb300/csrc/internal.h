@@ -116,6 +116,9 @@ struct BfsDevStats {
 // blocks = cooperative grid size (0: the default full-GPU grid); ws = a
 // workspace of bfs_workspace_bytes(g) bytes owned by the caller, or nullptr
 // to take one from the stream-ordered pool.
+// Device validation of one search and its TEPS numerator (validate.cu).
+gb_status validate_impl(const gb_graph *g, int64_t root, const int32_t *parent, const int32_t *level,
+                        const int64_t *edges, int64_t m, gb_validation *out, cudaStream_t s);
 gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level,
                    BfsDevStats *stats, cudaStream_t s, int blocks = 0, unsigned char *ws = nullptr);
 size_t bfs_workspace_bytes(const gb_graph *g);
