@@ -230,9 +230,9 @@ typedef struct gb_bfs_stats {
     int64_t reached;
     int64_t td_levels;
     int64_t bu_levels;
-    /* single-source bfs() only, first GB_STAT_LEVELS levels: device time of
-     * each level in ns, its frontier size, and its step (1 top-down,
-     * 2 bottom-up); zero for the batched calls */
+    /* first GB_STAT_LEVELS levels: device time of each level in ns, its
+     * frontier size (batched calls: vertices active for any root), and its
+     * step (1 top-down, 2 bottom-up) */
     int64_t level_ns[GB_STAT_LEVELS];
     int64_t level_frontier[GB_STAT_LEVELS];
     int32_t level_dir[GB_STAT_LEVELS];

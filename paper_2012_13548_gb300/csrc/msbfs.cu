@@ -9,10 +9,12 @@
 //
 //  top-down level: (1) every active vertex v ORs M_l[v] & ~seen[u] into
 //    M_{l+1}[u] for its neighbours u (one atomic per edge that adds bits);
-//    the first writer of a vertex appends it to the next active list;
-//    (2) after a grid barrier each new vertex scans its sorted adjacency list
-//    for, per new bit, the first neighbour carrying that bit in M_l -- the
-//    smallest-id parent -- and writes levels and parents.
+//    the first writer of a vertex appends it to the next active list, and
+//    the bits an atomic sets first have v as a valid parent, which is
+//    written there unless canonical parents are asked for; (2) after a grid
+//    barrier, in canonical mode, each new vertex scans its sorted adjacency
+//    list for, per new bit, the first neighbour carrying that bit in M_l --
+//    the smallest-id parent -- and writes levels and parents.
 //  bottom-up level: every vertex with unseen bits scans its sorted adjacency
 //    list, collecting M_l bits until all its unseen bits are found; the first
 //    neighbour to supply a bit is its parent.
@@ -68,6 +70,7 @@ struct MsHeader {
     MsCtl ctl[3];
     unsigned long long acc[6];
     unsigned long long na_hist[4];  // active-list length of each level (ring)
+    unsigned long long t0;          // global timer at the start of the current level
 };
 
 namespace {
@@ -92,6 +95,7 @@ struct MsArgs {
     float ms_alpha;
     float ms_beta;
     uint64_t timeout_ns;
+    int canonical;          // 1: smallest-id parents; 0: any valid parent
     int l0;                 // first level to run
     int max_levels;         // levels to run in this launch, 0 = until the frontier is empty
     int do_init;            // 1: clear state and place the roots first (batch calls)
@@ -278,8 +282,13 @@ __device__ __forceinline__ void ms_append(bool on, int64_t gid, int64_t deg, MsW
 }
 
 // Top-down expansion of one edge (gv -> gu) carrying frontier bits f.
+// Top-down visit of edge (v, gu), v the frontier vertex (local id pv) with
+// mask f.  The bits this atomic sets first are gu's new bits with v as their
+// parent: outside canonical mode that parent and the level are written here,
+// once per bit, and gu's row is never scanned for them.
 template <typename T>
-__device__ __forceinline__ void ms_td_edge(bool valid, T f, int64_t gu, const MsArgs<T> &a, T *Mn,
+__device__ __forceinline__ void ms_td_edge(bool valid, T f, int64_t gu, int32_t pv, int l,
+                                           const MsArgs<T> &a, const MsSlots *S, T *Mn,
                                            const MsGraph *s_g, const int64_t *s_voff, MsWarpBuf &wb,
                                            int &qn, int &bn, unsigned long long &my_mf,
                                            MsCtl *nxt, int32_t *act_next,
@@ -291,11 +300,18 @@ __device__ __forceinline__ void ms_td_edge(bool valid, T f, int64_t gu, const Ms
         const T m = f & (T)~ld_mask(&a.seen[gu]);
         if (m) {
             const T old = atomic_or_mask(&Mn[gu], m);
-            if (old == 0) {
-                first = true;
+            const T newb = m & (T)~old;
+            if (old == 0 || (!a.canonical && newb)) {
                 const int g = find_graph(s_voff, a.ng, gu);
                 const int64_t lu = gu - s_g[g].voff;
-                deg = s_g[g].off[lu + 1] - s_g[g].off[lu];
+                if (!a.canonical && newb) {
+                    write_parents(s_g[g], S, lu, newb, pv);
+                    write_levels(s_g[g], S, lu, newb, l + 1);
+                }
+                if (old == 0) {
+                    first = true;
+                    deg = s_g[g].off[lu + 1] - s_g[g].off[lu];
+                }
             }
         }
     }
@@ -480,6 +496,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
         }
         if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_MS_BAR)) return;
     }
+    if (a.stats && gtid == 0) h->t0 = globaltimer_ns();
 
     unsigned long long my_edges = 0, my_touched = 0, reached_new = 0, my_mf = 0;
     T my_any = 0;
@@ -550,8 +567,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                             const int64_t j = b + lane;
                             const bool valid = j < e;
                             const int64_t gu = valid ? G.voff + G.col[j] : 0;
-                            ms_td_edge(valid, f, gu, a, Mn, s_g, s_voff, wb, qn_buf, bn_buf, my_mf,
-                                       nxt, act_next, bigq_next);
+                            ms_td_edge(valid, f, gu, (int32_t)lv, l, a, S, Mn, s_g, s_voff, wb,
+                                       qn_buf, bn_buf, my_mf, nxt, act_next, bigq_next);
                         }
                     }
                 }
@@ -591,14 +608,17 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                     const T fo = shfl_mask(f, owner);
                     const bool valid = kk < total;
                     const int64_t gu = valid ? vvo + s_g[og].col[so + (kk - eo)] : 0;
-                    ms_td_edge(valid, fo, gu, a, Mn, s_g, s_voff, wb, qn_buf, bn_buf, my_mf, nxt,
-                               act_next, bigq_next);
+                    const int32_t pvo = (int32_t)(__shfl_sync(kFull, gv, owner) - vvo);
+                    ms_td_edge(valid, fo, gu, pvo, l, a, S, Mn, s_g, s_voff, wb, qn_buf, bn_buf,
+                               my_mf, nxt, act_next, bigq_next);
                 }
             }
             ms_flush_q(wb, qn_buf, nxt, act_next);
             ms_flush_b(wb, bn_buf, nxt, bigq_next);
             if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_MS_BAR)) return;
-            // (2) parents and levels of the vertices that gained bits
+            // (2) the vertices that gained bits join `seen`; in canonical mode
+            // each also scans its row for its smallest-id parents and writes
+            // its levels (otherwise both were written in (1))
             const int64_t nn = (int64_t)ldcg_u64(&nxt->na);
             for (int64_t i0 = gwarp * 32; i0 < nn; i0 += nwarps * 32) {
                 const int64_t i = i0 + lane;
@@ -610,12 +630,14 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                     g = find_graph(s_voff, a.ng, gu);
                     lu = gu - s_g[g].voff;
                     nw = ld_mask(&Mn[gu]);
-                    rs = s_g[g].off[lu];
-                    re = s_g[g].off[lu + 1];
+                    if (a.canonical) {
+                        rs = s_g[g].off[lu];
+                        re = s_g[g].off[lu + 1];
+                    }
                 }
-                ms_rows(s_g, S, M, g, lu, rs, re, nw, my_edges);
+                if (a.canonical) ms_rows(s_g, S, M, g, lu, rs, re, nw, my_edges);
                 if (i < nn) {
-                    write_levels(s_g[g], S, lu, nw, l + 1);
+                    if (a.canonical) write_levels(s_g[g], S, lu, nw, l + 1);
                     st_mask(&a.seen[gu], (T)(ld_mask(&a.seen[gu]) | nw));
                     reached_new += __popcll((unsigned long long)nw);
                     my_any |= nw;
@@ -681,6 +703,14 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             atomicAdd(&h->acc[td ? 4 : 5], 1ull);
         }
         if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_MS_BAR)) return;
+        // per-level device time, active vertices and step
+        if (a.stats && gtid == 0 && l - a.l0 < kStatLevels) {
+            const uint64_t now = globaltimer_ns();
+            a.stats->level_ns[l - a.l0] = now - h->t0;
+            a.stats->level_frontier[l - a.l0] = na;
+            a.stats->level_dir[l - a.l0] = td ? 1 : 2;
+            h->t0 = now;
+        }
     }
 
     if (!a.stats) return;
@@ -705,11 +735,6 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             st.reached = ldcg_u64(&h->acc[2]);
             st.td_levels = ldcg_u64(&h->acc[4]);
             st.bu_levels = ldcg_u64(&h->acc[5]);
-            for (int i = 0; i < kStatLevels; ++i) {
-                st.level_ns[i] = 0;
-                st.level_frontier[i] = 0;
-                st.level_dir[i] = 0;
-            }
         }
     }
 }
@@ -767,6 +792,7 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     a.ms_alpha = (float)o.ms_alpha;
     a.ms_beta = (float)o.ms_beta;
     a.timeout_ns = timeout_ns();
+    a.canonical = o.canonical_parents;
     a.l0 = 0;
     a.max_levels = 0;
     a.do_init = 1;
@@ -1006,6 +1032,7 @@ gb_status ms_serve_step(MsServe *m, int level, unsigned long long active, MsCtl 
     a.ms_alpha = (float)o.ms_alpha;
     a.ms_beta = (float)o.ms_beta;
     a.timeout_ns = timeout_ns();
+    a.canonical = o.canonical_parents;
     a.l0 = level;
     a.max_levels = 1;
     a.do_init = 0;

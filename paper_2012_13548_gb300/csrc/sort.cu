@@ -21,10 +21,12 @@
 namespace gb {
 namespace {
 
-constexpr int RS_THREADS = 256;
+constexpr int RS_THREADS = 512;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 keys
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // keys per tile
+#define RS_MINB(vals) ((vals) ? 3 * 256 / RS_THREADS : 4 * 256 / RS_THREADS)
+static_assert(RS_THREADS % 256 == 0, "threads 0..255 own one digit each");
 constexpr int64_t RS_PORTION = int64_t(1) << 28;
 constexpr unsigned FLAG_AGG = 1u << 30;
 constexpr unsigned FLAG_INCL = 2u << 30;
@@ -71,8 +73,11 @@ __global__ void rs_scan_kernel(const unsigned long long *__restrict__ hist, int 
     }
 }
 
+// Register budget: keys-only passes (kernel 1) keep 1024 threads per SM
+// resident, passes that carry values 768 (rounded down to whole blocks); both
+// are latency-bound, so resident warps matter.
 template <bool VALS>
-__global__ void __launch_bounds__(RS_THREADS) rs_onesweep_kernel(
+__global__ void __launch_bounds__(RS_THREADS, RS_MINB(VALS)) rs_onesweep_kernel(
     const uint64_t *__restrict__ kin, uint64_t *__restrict__ kout, const uint32_t *__restrict__ vin,
     uint32_t *__restrict__ vout, int64_t begin, int64_t count, int shift, int ntiles,
     const unsigned long long *__restrict__ base_in, unsigned long long *__restrict__ base_out,
@@ -129,56 +134,60 @@ __global__ void __launch_bounds__(RS_THREADS) rs_onesweep_kernel(
     }
     __syncthreads();
 
-    // Thread d owns digit d: per-warp exclusive offsets and the tile total.
+    // Thread d < 256 owns digit d: per-warp exclusive offsets and the tile total.
     const int d = tid;
-    unsigned total = 0;
+    const bool owner = tid < 256;
+    unsigned total = 0, incl = 0;
+    volatile unsigned *my_status = status + 1 + (size_t)tile * 256 + (owner ? d : 0);
+    if (owner) {
 #pragma unroll
-    for (int w = 0; w < RS_WARPS; ++w) {
-        const unsigned c = s_whist[w][d];
-        s_whist[w][d] = (unsigned short)total;
-        total += c;
-    }
-    volatile unsigned *my_status = status + 1 + (size_t)tile * 256 + d;
-    *my_status = (tile == 0 ? FLAG_INCL : FLAG_AGG) | total;
-
-    // Exclusive scan of the tile totals over digits.
-    const unsigned incl = warp_inclusive_scan(total);
-    if (lane == 31) s_wsum[warp] = incl;
-    __syncthreads();
-    unsigned woff = 0;
-    for (int w = 0; w < warp; ++w) woff += s_wsum[w];
-    s_excl[d] = woff + incl - total;
-
-    // Decoupled look-back over earlier tiles for this digit.
-    unsigned long long prefix = 0;
-    if (tile > 0) {
-        int t = tile - 1;
-        unsigned spins = 0;
-        uint64_t t0 = 0;
-        while (true) {
-            const unsigned sv = *(volatile const unsigned *)(status + 1 + (size_t)t * 256 + d);
-            if ((sv & ~VAL_MASK) == 0) {
-                if (((++spins) & 63u) == 0) {
-                    const uint64_t now = globaltimer_ns();
-                    if (t0 == 0) t0 = now;
-                    else if (now - t0 > timeout_ns) {
-                        record_error(st, GB_ERR_TIMEOUT, 100, (long long)tile);
-                        s_bad = 1;
-                        break;
-                    }
-                }
-                continue;
-            }
-            prefix += sv & VAL_MASK;
-            if (sv & FLAG_INCL) break;
-            --t;
-            if (t < 0) break;  // tile 0 always publishes FLAG_INCL
+        for (int w = 0; w < RS_WARPS; ++w) {
+            const unsigned c = s_whist[w][d];
+            s_whist[w][d] = (unsigned short)total;
+            total += c;
         }
-        *my_status = FLAG_INCL | (unsigned)((prefix + total) & VAL_MASK);
+        *my_status = (tile == 0 ? FLAG_INCL : FLAG_AGG) | total;
+        // exclusive scan of the tile totals over digits (warps 0..7)
+        incl = warp_inclusive_scan(total);
+        if (lane == 31) s_wsum[warp] = incl;
     }
-    const unsigned long long gstart = base_in[d] + prefix;
-    if (tile == ntiles - 1) base_out[d] = gstart + total;
-    s_adj[d] = (long long)gstart - (long long)s_excl[d];
+    __syncthreads();
+    if (owner) {
+        unsigned woff = 0;
+        for (int w = 0; w < warp; ++w) woff += s_wsum[w];
+        s_excl[d] = woff + incl - total;
+
+        // Decoupled look-back over earlier tiles for this digit.
+        unsigned long long prefix = 0;
+        if (tile > 0) {
+            int t = tile - 1;
+            unsigned spins = 0;
+            uint64_t t0 = 0;
+            while (true) {
+                const unsigned sv = *(volatile const unsigned *)(status + 1 + (size_t)t * 256 + d);
+                if ((sv & ~VAL_MASK) == 0) {
+                    if (((++spins) & 63u) == 0) {
+                        const uint64_t now = globaltimer_ns();
+                        if (t0 == 0) t0 = now;
+                        else if (now - t0 > timeout_ns) {
+                            record_error(st, GB_ERR_TIMEOUT, 100, (long long)tile);
+                            s_bad = 1;
+                            break;
+                        }
+                    }
+                    continue;
+                }
+                prefix += sv & VAL_MASK;
+                if (sv & FLAG_INCL) break;
+                --t;
+                if (t < 0) break;  // tile 0 always publishes FLAG_INCL
+            }
+            *my_status = FLAG_INCL | (unsigned)((prefix + total) & VAL_MASK);
+        }
+        const unsigned long long gstart = base_in[d] + prefix;
+        if (tile == ntiles - 1) base_out[d] = gstart + total;
+        s_adj[d] = (long long)gstart - (long long)s_excl[d];
+    }
     __syncthreads();
 
     // Scatter into shared memory in digit order, then write each run out.

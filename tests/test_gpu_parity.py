@@ -235,10 +235,20 @@ MS_SWITCHES = {"default": {}, "top_down": dict(ms_alpha=1e-9, ms_beta=1e-9),
                "bottom_up": dict(ms_alpha=1e9, ms_beta=1e9)}
 
 
+def check_row(off, col, r, par, lev, p_ref, l_ref, canonical, what):
+    """Levels bit-exact; parents bit-exact in canonical mode, else a valid tree."""
+    assert np.array_equal(lev, l_ref), what
+    if canonical:
+        assert np.array_equal(par, p_ref), what
+    else:
+        assert oracle.validate(off, col, r, par, lev) == 0, what
+
+
+@pytest.mark.parametrize("canonical", [0, 1])
 @pytest.mark.parametrize("mode", list(MS_SWITCHES))
 @pytest.mark.parametrize("scale,k", [(6, 64), (10, 1), (10, 7), (12, 64), (16, 64)])
-def test_msbfs_rows_equal_single_source(scale, k, mode):
-    gb.bfs_set_options(**MS_SWITCHES[mode])
+def test_msbfs_rows_equal_single_source(scale, k, mode, canonical):
+    gb.bfs_set_options(canonical_parents=canonical, **MS_SWITCHES[mode])
     _, off_ref, col_ref = oracle_graph(scale)
     _, G = gpu_graph(scale)
     roots = roots_for(scale, k)
@@ -247,11 +257,12 @@ def test_msbfs_rows_equal_single_source(scale, k, mode):
     P, L = gb.bfs_batch(G, roots)
     for i, r in enumerate(roots):
         p_ref, l_ref = oracle_bfs(scale, r)
-        assert np.array_equal(np_(L[i]), l_ref), (i, r)
-        assert np.array_equal(np_(P[i]), p_ref), (i, r)
+        check_row(off_ref, col_ref, r, np_(P[i]), np_(L[i]), p_ref, l_ref, canonical, (i, r))
 
 
-def test_msbfs_repeated_roots_and_random_graphs():
+@pytest.mark.parametrize("canonical", [0, 1])
+def test_msbfs_repeated_roots_and_random_graphs(canonical):
+    gb.bfs_set_options(canonical_parents=canonical)
     rng = np.random.default_rng(9)
     for trial in range(6):
         n = int(rng.integers(2, 300))
@@ -262,12 +273,13 @@ def test_msbfs_repeated_roots_and_random_graphs():
         P, L = gb.bfs_batch(G, roots)
         for i, r in enumerate(roots):
             p_ref, l_ref = oracle.bfs(off, col, r)
-            assert np.array_equal(np_(L[i]), l_ref)
-            assert np.array_equal(np_(P[i]), p_ref)
+            check_row(off, col, r, np_(P[i]), np_(L[i]), p_ref, l_ref, canonical, (trial, i, r))
 
 
+@pytest.mark.parametrize("canonical", [0, 1])
 @pytest.mark.parametrize("lo,hi,count", [(4, 9, 32), (12, 18, 32)])
-def test_multi_graph_batch_equals_standalone(lo, hi, count):
+def test_multi_graph_batch_equals_standalone(lo, hi, count, canonical):
+    gb.bfs_set_options(canonical_parents=canonical)
     specs = W.batch_specs(count, lo, hi)
     graphs, roots = [], []
     for sp in specs:
@@ -279,10 +291,11 @@ def test_multi_graph_batch_equals_standalone(lo, hi, count):
         roots.append(rs)
     P, L = gb.bfs_multi_graph(graphs, roots)
     for gi, sp in enumerate(specs):
+        _, off_ref, col_ref = oracle_graph(sp.scale, sp.index)
         for b, r in enumerate(roots[gi]):
             p_ref, l_ref = oracle_bfs(sp.scale, r, sp.index)
-            assert np.array_equal(np_(L[gi][b]), l_ref), (gi, b)
-            assert np.array_equal(np_(P[gi][b]), p_ref), (gi, b)
+            check_row(off_ref, col_ref, r, np_(P[gi][b]), np_(L[gi][b]), p_ref, l_ref, canonical,
+                      (gi, b))
 
 
 def test_bounded_waits_report_timeout_and_the_context_survives():

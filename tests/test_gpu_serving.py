@@ -2,8 +2,9 @@
 
 Queries that arrive while others run are admitted into free bit-slots at BFS
 level boundaries.  Every served result must equal the same query run alone:
-levels and parents bit-exact against bfs() and against the oracle (the
-batched kernel always produces the smallest-id parent).
+levels bit-exact against bfs() and against the oracle always, parents too in
+canonical mode (the smallest-id parent is unique); outside it any valid tree
+is allowed, so parents pass the Graph500 validation instead.
 """
 import numpy as np
 import pytest
@@ -33,23 +34,26 @@ def resident():
     return graphs, offs
 
 
-def _check_results(srv, graphs, tickets, queries):
-    gb.bfs_set_options(canonical_parents=1)
+def _check_results(srv, graphs, tickets, queries, canonical):
     for t, (gi, r) in zip(tickets, queries):
         par, lev = srv.result(t, gi)
-        p_alone, l_alone = gb.bfs(graphs[gi], r)
+        _, l_alone = gb.bfs(graphs[gi], r)
         assert torch.equal(lev, l_alone), (gi, r)
-        assert torch.equal(par, p_alone), (gi, r)
         _, off, col = oracle_graph(SCALES[gi])
         p_ref, l_ref = oracle.bfs(off, col, r)
-        assert np.array_equal(lev.cpu().numpy(), l_ref), (gi, r)
-        assert np.array_equal(par.cpu().numpy(), p_ref), (gi, r)
+        par, lev = par.cpu().numpy(), lev.cpu().numpy()
+        assert np.array_equal(lev, l_ref), (gi, r)
+        if canonical:
+            assert np.array_equal(par, p_ref), (gi, r)
+        else:
+            assert oracle.validate(off, col, r, par, lev) == 0, (gi, r)
         srv.release(t)
-    gb.bfs_set_options(canonical_parents=0)
 
 
-def test_burst_larger_than_the_slots(resident):
+@pytest.mark.parametrize("canonical", [0, 1])
+def test_burst_larger_than_the_slots(resident, canonical):
     graphs, offs = resident
+    gb.bfs_set_options(canonical_parents=canonical)
     rng = np.random.default_rng(11)
     srv = gb.Server(graphs, mem_budget=1 << 30)
     queries = []
@@ -57,8 +61,9 @@ def test_burst_larger_than_the_slots(resident):
         gi = int(rng.integers(0, len(graphs)))
         queries.append((gi, int(rng.integers(0, graphs[gi].n))))   # isolated roots included
     tickets = [srv.submit(gi, r) for gi, r in queries]
-    _check_results(srv, graphs, tickets, queries)
+    _check_results(srv, graphs, tickets, queries, canonical)
     srv.close()
+    gb.bfs_set_options(canonical_parents=0)
     gb.gb_device_status()
 
 
@@ -70,12 +75,14 @@ def test_admission_by_memory(resident):
     rng = np.random.default_rng(12)
     queries = [(3, int(r)) for r in W.root_from_draw(offs[3], rng.integers(0, 2**62, size=40))]
     tickets = [srv.submit(gi, r) for gi, r in queries]
-    _check_results(srv, graphs, tickets, queries)
+    _check_results(srv, graphs, tickets, queries, canonical=False)
     srv.close()
 
 
-def test_poisson_trace_matches_alone_and_replays_identically(resident):
+@pytest.mark.parametrize("canonical", [0, 1])
+def test_poisson_trace_matches_alone_and_replays_identically(resident, canonical):
     graphs, offs = resident
+    gb.bfs_set_options(canonical_parents=canonical)
     t, gid, draw = W.poisson_trace(rate=20000.0, duration_s=0.05, n_graphs=len(graphs), seed=5)
     roots = np.array([W.root_from_draw(offs[g], np.array([d], dtype=np.uint64))[0]
                       for g, d in zip(gid, draw)], dtype=np.int64)
@@ -91,13 +98,18 @@ def test_poisson_trace_matches_alone_and_replays_identically(resident):
             srv.release(i)
         srv.close()
         outs.append(levs)
-    gb.bfs_set_options(canonical_parents=1)
     for i in range(t.size):
-        assert np.array_equal(outs[0][i][1], outs[1][i][1])
-        assert np.array_equal(outs[0][i][0], outs[1][i][0])
-        p_alone, l_alone = gb.bfs(graphs[int(gid[i])], int(roots[i]))
-        assert np.array_equal(outs[0][i][1], l_alone.cpu().numpy()), i
-        assert np.array_equal(outs[0][i][0], p_alone.cpu().numpy()), i
+        g, r = int(gid[i]), int(roots[i])
+        p_alone, l_alone = gb.bfs(graphs[g], r)
+        for rep in range(2):
+            assert np.array_equal(outs[rep][i][1], l_alone.cpu().numpy()), i
+        if canonical:   # the unique tree: identical in both replays and alone
+            assert np.array_equal(outs[0][i][0], outs[1][i][0])
+            assert np.array_equal(outs[0][i][0], p_alone.cpu().numpy()), i
+        else:
+            _, off, col = oracle_graph(SCALES[g])
+            for rep in range(2):
+                assert oracle.validate(off, col, r, outs[rep][i][0], outs[rep][i][1]) == 0, i
     gb.bfs_set_options(canonical_parents=0)
 
 
