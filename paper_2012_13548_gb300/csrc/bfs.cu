@@ -43,6 +43,8 @@ namespace {
 constexpr int BFS_THREADS = 512;
 constexpr int BIG_CHUNK = 128;      // edges per chunk of a big frontier vertex (one round)
 constexpr int BU_LANE_FIRST = 4;    // bottom-up: each lane probes this many neighbours itself
+constexpr int BU_WORDS = 4;         // bottom-up hub pass: visited words per warp iteration
+constexpr int PBUF = 64;            // per-warp list of vertices left for the row pass
 constexpr int BFS_WARPS = BFS_THREADS / 32;
 constexpr int QBUF = 256;           // per-warp buffer of discovered vertices (shared memory)
 constexpr int BBUF = 32;            // per-warp buffer of discovered big-degree vertices
@@ -130,6 +132,9 @@ __device__ __forceinline__ unsigned nchunks(int64_t deg)
 struct WarpBuf {
     int32_t q[QBUF];
     unsigned long long b[BBUF];  // v | nchunks << 32
+    int64_t ps[PBUF];            // bottom-up row pass: row starts,
+    int32_t pu[PBUF];            // vertices
+    int32_t pd[PBUF];            // and degrees
 };
 
 // Warp-collective: move the staged queue entries to the next level's queue.
@@ -330,6 +335,55 @@ __device__ __forceinline__ void bu_commit_word(const BfsArgs &a, unsigned *Fn, i
     append_next(won, (int32_t)u, deg, a, wbuf, qn, bn, my_mf, nxt, qnext_base, bnext_base);
 }
 
+// Warp-collective bottom-up row pass over the first `cnt` (<= 32) vertices of
+// the warp's pending list, lane i taking entry i: the lane probes the first
+// BU_LANE_FIRST neighbours of its row, rows still open are streamed by the
+// warp; the first frontier neighbour in row order is the parent.  Entries come
+// from several visited words, so the visited and next-frontier bits are set
+// with atomics.
+__device__ __forceinline__ void bu_row_pass(const BfsArgs &a, const unsigned *F, unsigned *Fn,
+                                            int cnt, int l, WarpBuf &wb, int &qn, int &bn,
+                                            unsigned long long &my_mf,
+                                            unsigned long long &my_edges, LevelCtl *nxt,
+                                            int64_t qnext_base, int64_t bnext_base)
+{
+    const int lane = (int)lane_id();
+    __syncwarp();  // the entries, and the commits of their words, are visible to the warp
+    const bool act = lane < cnt;
+    const int32_t u = act ? wb.pu[lane] : 0;
+    const int64_t s = act ? wb.ps[lane] : 0;
+    const int32_t d = act ? wb.pd[lane] : 0;
+    __syncwarp();  // read before the list is refilled
+    const int32_t la = d < BU_LANE_FIRST ? d : BU_LANE_FIRST;
+    int32_t vv[BU_LANE_FIRST];
+    unsigned fw[BU_LANE_FIRST];
+#pragma unroll
+    for (int t = 0; t < BU_LANE_FIRST; ++t)
+        vv[t] = t < la && GB_OK_IDX(a.st, s + t, a.nnz, 222) ? __ldg(&a.col[s + t]) : -1;
+#pragma unroll
+    for (int t = 0; t < BU_LANE_FIRST; ++t)
+        fw[t] = vv[t] >= 0 && GB_OK_IDX(a.st, vv[t], a.n, 223) ? ldcg_u32(&F[vv[t] >> 5]) : 0u;
+    int hit = -1;
+#pragma unroll
+    for (int t = 0; t < BU_LANE_FIRST; ++t)
+        if (hit < 0 && vv[t] >= 0 && ((fw[t] >> (vv[t] & 31)) & 1u)) hit = t;
+    int32_t found = -1;
+#pragma unroll
+    for (int t = 0; t < BU_LANE_FIRST; ++t)  // select without indexing registers
+        if (hit == t) found = vv[t];
+    my_edges += (unsigned long long)(hit >= 0 ? hit + 1 : la);
+    bu_stream_rows(a, F, act && found < 0 && la < d, s + la, s + d, found, my_edges);
+    const bool won = act && found >= 0 && GB_OK_IDX(a.st, u, a.n, 224);
+    if (won) {
+        a.parent[u] = found;
+        a.level[u] = l + 1;
+        const unsigned bit = 1u << (u & 31);
+        atomicOr(&a.vis[(unsigned)u >> 5], bit);
+        atomicOr(&Fn[(unsigned)u >> 5], bit);
+    }
+    append_next(won, u, d, a, wb, qn, bn, my_mf, nxt, qnext_base, bnext_base);
+}
+
 // MINB = blocks of BFS_THREADS per SM the register budget is sized for:
 // 2 (64 registers, no spills) or 3 (40 registers, more warps to hide latency).
 template <int MINB>
@@ -522,88 +576,89 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                 }
             }
         } else {
-            // bottom-up: a warp takes two visited words (64 vertices) at a time,
-            // lane i owning vertex i of each; both words' row offsets, then
-            // their neighbour probes, are issued together.
-            for (int64_t wa = gwarp; wa < nw; wa += 2 * nwarps) {
-                const int64_t wb2 = wa + nwarps;
-                const bool has_b = wb2 < nw;
-                const unsigned vwa = ldcg_u32(&a.vis[wa]);
-                const unsigned vwb = has_b ? ldcg_u32(&a.vis[wb2]) : kFull;
-                if (vwa == kFull && vwb == kFull) continue;
-                const int64_t ua = wa * 32 + lane, ub = wb2 * 32 + lane;
-                // row offsets of unvisited lanes only: late levels, where most
-                // vertices are visited, then skip most of the offset array
-                const bool ca = !((vwa >> lane) & 1u) && GB_OK_IDX(a.st, ua, a.n, 216);
-                const bool cb = !((vwb >> lane) & 1u) && GB_OK_IDX(a.st, ub, a.n, 217);
-                int64_t sa = 0, ea = 0, sb = 0, eb = 0;
-                if (ca) {
-                    sa = __ldg(&a.off[ua]);
-                    ea = __ldg(&a.off[ua + 1]);
-                }
-                if (cb) {
-                    sb = __ldg(&a.off[ub]);
-                    eb = __ldg(&a.off[ub + 1]);
-                }
-                // the hub first: a hit is a parent at the cost of one L2 lookup,
-                // and the row's first neighbours need not be fetched from DRAM
-                int32_t fa = -1, fb = -1;
-                if (a.hub) {
-                    const int32_t hua = ca ? __ldg(&a.hub[ua]) : -1;
-                    const int32_t hub_b = cb ? __ldg(&a.hub[ub]) : -1;
-                    const unsigned fha = hua >= 0 && GB_OK_IDX(a.st, hua, a.n, 220) ? ldcg_u32(&F[hua >> 5]) : 0u;
-                    const unsigned fhb = hub_b >= 0 && GB_OK_IDX(a.st, hub_b, a.n, 221) ? ldcg_u32(&F[hub_b >> 5]) : 0u;
-                    if (hua >= 0 && ((fha >> (hua & 31)) & 1u)) fa = hua;
-                    if (hub_b >= 0 && ((fhb >> (hub_b & 31)) & 1u)) fb = hub_b;
-                    my_edges += (unsigned long long)(hua >= 0) + (unsigned long long)(hub_b >= 0);
-                }
-                my_touched += (unsigned)ca + (unsigned)cb;
-                // one lane probes both rows in ascending order, 4 + 4 loads in flight
-                const int32_t da = (int32_t)(ea - sa), db = (int32_t)(eb - sb);
-                const int32_t la = da < BU_LANE_FIRST ? da : BU_LANE_FIRST;
-                const int32_t lb = db < BU_LANE_FIRST ? db : BU_LANE_FIRST;
-                int32_t ja = 0, jb = 0;
-                while ((fa < 0 && ja < la) || (fb < 0 && jb < lb)) {
-                    int32_t vv[8];
-                    unsigned fw[8];
+            // bottom-up, in two passes over this warp's visited words.  Hub pass:
+            // BU_WORDS words per iteration, lane i owning vertex i of each; an
+            // unvisited vertex tests its hub (fast mode) against the frontier
+            // bitmap, and the words are committed.  Row offsets are loaded for
+            // unvisited lanes only.  The vertices left open queue up in the
+            // warp's pending list, and every 32 of them take a row pass (one
+            // vertex per lane), so the row probes run with full warps.
+            int pn = 0;  // warp-uniform fill of the pending list
+            for (int64_t w0 = gwarp * BU_WORDS; w0 < nw; w0 += nwarps * BU_WORDS) {
+                unsigned vw[BU_WORDS];
+                bool any = false;
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        vv[t] = fa < 0 && ja + t < la && GB_OK_IDX(a.st, sa + ja + t, a.nnz, 211)
-                                    ? __ldg(&a.col[sa + ja + t]) : -1;
-                        vv[4 + t] = fb < 0 && jb + t < lb && GB_OK_IDX(a.st, sb + jb + t, a.nnz, 211)
-                                        ? __ldg(&a.col[sb + jb + t]) : -1;
+                for (int t = 0; t < BU_WORDS; ++t) {
+                    vw[t] = w0 + t < nw ? ldcg_u32(&a.vis[w0 + t]) : kFull;
+                    any |= vw[t] != kFull;
+                }
+                if (!any) continue;
+                int64_t rs[BU_WORDS];
+                int32_t dg[BU_WORDS], hb[BU_WORDS];
+#pragma unroll
+                for (int t = 0; t < BU_WORDS; ++t) {
+                    const int64_t u = (w0 + t) * 32 + lane;
+                    const bool cand = !((vw[t] >> lane) & 1u) && GB_OK_IDX(a.st, u, a.n, 216);
+                    rs[t] = 0;
+                    dg[t] = 0;
+                    hb[t] = -1;
+                    if (cand) {
+                        rs[t] = __ldg(&a.off[u]);
+                        dg[t] = (int32_t)(__ldg(&a.off[u + 1]) - rs[t]);
+                        if (a.hub) hb[t] = __ldg(&a.hub[u]);
                     }
-#pragma unroll
-                    for (int t = 0; t < 8; ++t)
-                        fw[t] = vv[t] >= 0 && GB_OK_IDX(a.st, vv[t], a.n, 212) ? ldcg_u32(&F[vv[t] >> 5]) : 0u;
-                    int32_t ha = -1, hb = -1;
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        if (ha < 0 && vv[t] >= 0 && ((fw[t] >> (vv[t] & 31)) & 1u)) ha = t;
-                        if (hb < 0 && vv[4 + t] >= 0 && ((fw[4 + t] >> (vv[4 + t] & 31)) & 1u)) hb = t;
-                    }
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {  // select without indexing registers
-                        if (ha == t) fa = vv[t];
-                        if (hb == t) fb = vv[4 + t];
-                    }
-                    if (fa < 0 && ja < la) ja += 4;
-                    else if (ha >= 0) ja += ha + 1;
-                    if (fb < 0 && jb < lb) jb += 4;
-                    else if (hb >= 0) jb += hb + 1;
                 }
-                ja = ja < la ? ja : la;
-                jb = jb < lb ? jb : lb;
-                my_edges += (unsigned long long)(ja + jb);
-                // rows left unresolved: scanned together as one stream
-                bu_stream_rows(a, F, ca && fa < 0 && la < da, sa + la, ea, fa, my_edges);
-                bu_stream_rows(a, F, cb && fb < 0 && lb < db, sb + lb, eb, fb, my_edges);
-                bu_commit_word(a, Fn, wa, vwa, ua, fa, da, l, wb, qn_buf, bn_buf, my_mf, nxt,
-                               qnext_base, bnext_base);
-                if (has_b)
-                    bu_commit_word(a, Fn, wb2, vwb, ub, fb, db, l, wb, qn_buf, bn_buf, my_mf, nxt,
-                                   qnext_base, bnext_base);
+                unsigned fh[BU_WORDS];
+#pragma unroll
+                for (int t = 0; t < BU_WORDS; ++t)
+                    fh[t] = hb[t] >= 0 && GB_OK_IDX(a.st, hb[t], a.n, 220) ? ldcg_u32(&F[hb[t] >> 5]) : 0u;
+#pragma unroll
+                for (int t = 0; t < BU_WORDS; ++t) {
+                    if (vw[t] == kFull) continue;  // warp-uniform
+                    const int64_t w = w0 + t;
+                    const int64_t u = w * 32 + lane;
+                    const bool cand = !((vw[t] >> lane) & 1u) && u < n;
+                    const int32_t found = hb[t] >= 0 && ((fh[t] >> (hb[t] & 31)) & 1u) ? hb[t] : -1;
+                    my_touched += (unsigned)cand;
+                    my_edges += (unsigned long long)(hb[t] >= 0);
+                    bu_commit_word(a, Fn, w, vw[t], u, found, dg[t], l, wb, qn_buf, bn_buf, my_mf,
+                                   nxt, qnext_base, bnext_base);
+                    const bool pend = cand && found < 0 && dg[t] > 0;
+                    const unsigned pm = __ballot_sync(kFull, pend);
+                    if (pend) {
+                        const int pos = pn + __popc(pm & lanemask_lt());
+                        if (GB_OK_IDX(a.st, pos, PBUF, 225)) {
+                            wb.pu[pos] = (int32_t)u;
+                            wb.ps[pos] = rs[t];
+                            wb.pd[pos] = dg[t];
+                        }
+                    }
+                    pn += __popc(pm);
+                    if (pn >= 32) {
+                        bu_row_pass(a, F, Fn, 32, l, wb, qn_buf, bn_buf, my_mf, my_edges, nxt,
+                                    qnext_base, bnext_base);
+                        // move the entries past the first 32 to the front
+                        const int rest = pn - 32;
+                        int32_t tu = 0, td2 = 0;
+                        int64_t ts = 0;
+                        if (lane < rest) {
+                            tu = wb.pu[32 + lane];
+                            ts = wb.ps[32 + lane];
+                            td2 = wb.pd[32 + lane];
+                        }
+                        __syncwarp();
+                        if (lane < rest) {
+                            wb.pu[lane] = tu;
+                            wb.ps[lane] = ts;
+                            wb.pd[lane] = td2;
+                        }
+                        pn = rest;
+                    }
+                }
             }
+            if (pn > 0)
+                bu_row_pass(a, F, Fn, pn, l, wb, qn_buf, bn_buf, my_mf, my_edges, nxt, qnext_base,
+                            bnext_base);
         }
         // end of level: flush the staged vertices and add the block's degree sum
         flush_queue(wb, qn_buf, a, nxt, qnext_base);
