@@ -44,7 +44,7 @@ constexpr int BFS_THREADS = 512;
 constexpr int BIG_CHUNK = 128;      // edges per chunk of a big frontier vertex (one round)
 constexpr int BU_LANE_FIRST = 4;    // bottom-up: each lane probes this many neighbours itself
 constexpr int BU_WORDS = 4;         // bottom-up hub pass: visited words per warp iteration
-constexpr int PBUF = 64;            // per-warp list of vertices left for the row pass
+constexpr int PBUF = 256;           // per-warp ring of vertices left for the row pass
 constexpr int BFS_WARPS = BFS_THREADS / 32;
 constexpr int QBUF = 256;           // per-warp buffer of discovered vertices (shared memory)
 constexpr int BBUF = 32;            // per-warp buffer of discovered big-degree vertices
@@ -132,9 +132,7 @@ __device__ __forceinline__ unsigned nchunks(int64_t deg)
 struct WarpBuf {
     int32_t q[QBUF];
     unsigned long long b[BBUF];  // v | nchunks << 32
-    int64_t ps[PBUF];            // bottom-up row pass: row starts,
-    int32_t pu[PBUF];            // vertices
-    int32_t pd[PBUF];            // and degrees
+    int32_t pu[PBUF];            // bottom-up: vertices waiting for a row pass
 };
 
 // Warp-collective: move the staged queue entries to the next level's queue.
@@ -335,14 +333,14 @@ __device__ __forceinline__ void bu_commit_word(const BfsArgs &a, unsigned *Fn, i
     append_next(won, (int32_t)u, deg, a, wbuf, qn, bn, my_mf, nxt, qnext_base, bnext_base);
 }
 
-// Warp-collective bottom-up row pass over the first `cnt` (<= 32) vertices of
-// the warp's pending list, lane i taking entry i: the lane probes the first
+// Warp-collective bottom-up row pass over `cnt` (<= 32) vertices of the warp's
+// pending ring from position `head`, lane i taking entry head + i: the lane probes the first
 // BU_LANE_FIRST neighbours of its row, rows still open are streamed by the
 // warp; the first frontier neighbour in row order is the parent.  Entries come
 // from several visited words, so the visited and next-frontier bits are set
 // with atomics.
 __device__ __forceinline__ void bu_row_pass(const BfsArgs &a, const unsigned *F, unsigned *Fn,
-                                            int cnt, int l, WarpBuf &wb, int &qn, int &bn,
+                                            int head, int cnt, int l, WarpBuf &wb, int &qn, int &bn,
                                             unsigned long long &my_mf,
                                             unsigned long long &my_edges, LevelCtl *nxt,
                                             int64_t qnext_base, int64_t bnext_base)
@@ -350,10 +348,11 @@ __device__ __forceinline__ void bu_row_pass(const BfsArgs &a, const unsigned *F,
     const int lane = (int)lane_id();
     __syncwarp();  // the entries, and the commits of their words, are visible to the warp
     const bool act = lane < cnt;
-    const int32_t u = act ? wb.pu[lane] : 0;
-    const int64_t s = act ? wb.ps[lane] : 0;
-    const int32_t d = act ? wb.pd[lane] : 0;
-    __syncwarp();  // read before the list is refilled
+    const int32_t u = act ? wb.pu[(head + lane) & (PBUF - 1)] : 0;
+    __syncwarp();  // read before the ring is refilled
+    // the offsets were read by this warp in the hub pass: L1 hits
+    const int64_t s = act ? __ldg(&a.off[u]) : 0;
+    const int32_t d = act ? (int32_t)(__ldg(&a.off[u + 1]) - s) : 0;
     const int32_t la = d < BU_LANE_FIRST ? d : BU_LANE_FIRST;
     int32_t vv[BU_LANE_FIRST];
     unsigned fw[BU_LANE_FIRST];
@@ -583,7 +582,7 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
             // unvisited lanes only.  The vertices left open queue up in the
             // warp's pending list, and every 32 of them take a row pass (one
             // vertex per lane), so the row probes run with full warps.
-            int pn = 0;  // warp-uniform fill of the pending list
+            int ph = 0, pt = 0;  // warp-uniform head and tail of the pending ring
             for (int64_t w0 = gwarp * BU_WORDS; w0 < nw; w0 += nwarps * BU_WORDS) {
                 unsigned vw[BU_WORDS];
                 bool any = false;
@@ -593,18 +592,15 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                     any |= vw[t] != kFull;
                 }
                 if (!any) continue;
-                int64_t rs[BU_WORDS];
                 int32_t dg[BU_WORDS], hb[BU_WORDS];
 #pragma unroll
                 for (int t = 0; t < BU_WORDS; ++t) {
                     const int64_t u = (w0 + t) * 32 + lane;
                     const bool cand = !((vw[t] >> lane) & 1u) && GB_OK_IDX(a.st, u, a.n, 216);
-                    rs[t] = 0;
                     dg[t] = 0;
                     hb[t] = -1;
                     if (cand) {
-                        rs[t] = __ldg(&a.off[u]);
-                        dg[t] = (int32_t)(__ldg(&a.off[u + 1]) - rs[t]);
+                        dg[t] = (int32_t)(__ldg(&a.off[u + 1]) - __ldg(&a.off[u]));
                         if (a.hub) hb[t] = __ldg(&a.hub[u]);
                     }
                 }
@@ -625,40 +621,19 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                                    nxt, qnext_base, bnext_base);
                     const bool pend = cand && found < 0 && dg[t] > 0;
                     const unsigned pm = __ballot_sync(kFull, pend);
-                    if (pend) {
-                        const int pos = pn + __popc(pm & lanemask_lt());
-                        if (GB_OK_IDX(a.st, pos, PBUF, 225)) {
-                            wb.pu[pos] = (int32_t)u;
-                            wb.ps[pos] = rs[t];
-                            wb.pd[pos] = dg[t];
-                        }
-                    }
-                    pn += __popc(pm);
-                    if (pn >= 32) {
-                        bu_row_pass(a, F, Fn, 32, l, wb, qn_buf, bn_buf, my_mf, my_edges, nxt,
-                                    qnext_base, bnext_base);
-                        // move the entries past the first 32 to the front
-                        const int rest = pn - 32;
-                        int32_t tu = 0, td2 = 0;
-                        int64_t ts = 0;
-                        if (lane < rest) {
-                            tu = wb.pu[32 + lane];
-                            ts = wb.ps[32 + lane];
-                            td2 = wb.pd[32 + lane];
-                        }
-                        __syncwarp();
-                        if (lane < rest) {
-                            wb.pu[lane] = tu;
-                            wb.ps[lane] = ts;
-                            wb.pd[lane] = td2;
-                        }
-                        pn = rest;
-                    }
+                    if (pend) wb.pu[(pt + __popc(pm & lanemask_lt())) & (PBUF - 1)] = (int32_t)u;
+                    pt += __popc(pm);
+                }
+                // row passes, 32 pending vertices at a time (at most 31 stay behind)
+                while (pt - ph >= 32) {
+                    bu_row_pass(a, F, Fn, ph, 32, l, wb, qn_buf, bn_buf, my_mf, my_edges, nxt,
+                                qnext_base, bnext_base);
+                    ph += 32;
                 }
             }
-            if (pn > 0)
-                bu_row_pass(a, F, Fn, pn, l, wb, qn_buf, bn_buf, my_mf, my_edges, nxt, qnext_base,
-                            bnext_base);
+            if (pt > ph)
+                bu_row_pass(a, F, Fn, ph, pt - ph, l, wb, qn_buf, bn_buf, my_mf, my_edges, nxt,
+                            qnext_base, bnext_base);
         }
         // end of level: flush the staged vertices and add the block's degree sum
         flush_queue(wb, qn_buf, a, nxt, qnext_base);
