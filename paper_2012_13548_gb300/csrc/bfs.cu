@@ -583,7 +583,17 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
             // warp's pending list, and every 32 of them take a row pass (one
             // vertex per lane), so the row probes run with full warps.
             int ph = 0, pt = 0;  // warp-uniform head and tail of the pending ring
+            // the next group's hub entries and row offsets are bulk-prefetched
+            // into L2 while this group is processed (16-byte aligned arrays only:
+            // the library's own are; a caller's offsets may not be)
+            const bool bulk_pf = ((reinterpret_cast<uintptr_t>(a.off) |
+                                   reinterpret_cast<uintptr_t>(a.hub)) & 15u) == 0;
             for (int64_t w0 = gwarp * BU_WORDS; w0 < nw; w0 += nwarps * BU_WORDS) {
+                const int64_t wn = w0 + nwarps * BU_WORDS;
+                if (bulk_pf && lane == 0 && (wn + BU_WORDS) * 32 <= n) {
+                    if (a.hub) prefetch_l2_bulk(a.hub + wn * 32, BU_WORDS * 32 * sizeof(int32_t));
+                    prefetch_l2_bulk(a.off + wn * 32, BU_WORDS * 32 * sizeof(int64_t));
+                }
                 unsigned vw[BU_WORDS];
                 bool any = false;
 #pragma unroll

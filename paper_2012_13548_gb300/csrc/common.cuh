@@ -158,4 +158,12 @@ __device__ __forceinline__ unsigned long long ldcg_u64(const unsigned long long 
     return __ldcg(p);
 }
 
+// A hint (TMA bulk prefetch) that brings `bytes` bytes at p into L2; it
+// neither waits nor changes any value.  p and bytes must be multiples of 16
+// and the range must lie inside one allocation.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 }  // namespace gb
