@@ -489,7 +489,9 @@ def run_serve(args, dist):
     wl = W.WORKLOADS["serve6"]
     if not args.untuned:
         from paper_2012_13548_gb300 import autotune
-        gb.bfs_set_options(**autotune.tuned_options("batched", 22))
+        # the multi-source engine serves the graphs below 2^21 vertices, single-source
+        # searches the larger ones: tuned options for each side
+        gb.bfs_set_options(**autotune.tuned_options("batched", 20), **autotune.tuned_options("plain", 22))
     rate = args.rate or wl["rate"]
     graphs, edges, offs = [], [], []
     for sc in wl["scales"]:
@@ -567,7 +569,10 @@ def run_serve(args, dist):
                 "config": {"workload": "serving-6-resident-kronecker-graphs-scale14-24-poisson",
                            "scales": list(wl["scales"]), "rate_per_s": rate,
                            "duration_s": args.duration, "queries": int(t.size),
-                           "batch": "up to 64 queries per graph per launch, admitted per level",
+                           "batch": "queries admitted as slots free up and run concurrently: two "
+                                    "single-source searches per graph, each on half the SMs "
+                                    "(graphs of 2^14+ vertices; smaller ones: 64 query bits "
+                                    "of one multi-source search, admitted per level)",
                            "mem_budget_bytes": budget},
                 "serving": {"p50_ms": float(np.percentile(lat, 50)),
                             "p99_ms": float(np.percentile(lat, 99)),

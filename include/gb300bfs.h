@@ -291,11 +291,14 @@ gb_status bfs_validate(const gb_graph *g, int64_t root, const int32_t *parent,
 /* ------------------------------------------------------------------------ */
 
 /* Create a server over ng resident graphs (borrowed; they must outlive the
- * server).  Up to 64 queries per graph run together as bits of one
- * multi-source BFS; a query is admitted at the next level boundary once a
- * bit is free and its output buffers (8 * n_graph bytes) fit within
- * mem_budget bytes of device memory.  The server runs its own host thread
- * and one CUDA stream per graph. */
+ * server).  Queries are admitted as they arrive, whenever a slot is free and
+ * their output buffers (8 * n_graph bytes) fit within mem_budget bytes of
+ * device memory; admitted queries run concurrently on the device.  On a graph
+ * of 2^14 or more vertices a slot is one of two concurrent single-source
+ * searches, each on its own stream and half of the SMs; on a smaller graph
+ * up to 64 queries run together as the bits of one multi-source BFS, a query
+ * joining at the next level boundary.  The server runs its own host thread.
+ * Results follow the canonical_parents option like bfs(). */
 gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb_server **out);
 
 /* Queue a query (graph index, root).  *ticket identifies it.  Never blocks;

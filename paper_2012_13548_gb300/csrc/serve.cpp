@@ -1,22 +1,24 @@
-// Serving loop: resident graphs, BFS queries admitted as they arrive
-// (continuous batching at level granularity).
+// Serving loop: resident graphs, BFS queries admitted as they arrive and run
+// concurrently on the device (continuous batching).
 //
-// Every resident graph keeps one multi-source search state (msbfs.cu) whose
-// 64 bits are query slots.  A worker thread runs each graph one BFS level per
-// launch on the graph's own stream.  At every level boundary it retires the
-// queries whose bit stopped advancing (their BFS is complete), and admits
-// waiting queries into free bits as long as their output buffers (8 bytes per
-// vertex) fit in the memory budget.  A query admitted at level l starts from
-// its root in the frontier of level l; its levels are numbered from there, so
-// its result equals a standalone BFS from that root (bits never interact).
+// Graphs of 2^14 vertices or more are served by single-source searches: up
+// to kPlainSlots queries per graph run at once, each a direction-optimising
+// BFS launch on its own stream with an equal share of the SMs, so that the
+// searches of all graphs overlap; a query takes the next free slot once its
+// output buffers fit in the memory budget.  Measured at 5000 Poisson arrivals
+// per second over graphs of SCALE 14-24, this beats both a FIFO of whole-GPU
+// searches and multi-source batching: a multi-source level with up to 64 open
+// bits scans nearly every edge (its rows rarely complete early), while one
+// direction-optimising search touches a small fraction of them.
 //
-// Graphs of 2^21 vertices or more are served by single-source searches
-// instead: up to kPlainSlots queries per graph run at once, each a
-// direction-optimising BFS launch on its own stream with a half-GPU
-// cooperative grid, so that concurrent queries overlap their memory latency.
-// On such graphs a multi-source level scans nearly every edge while a single
-// direction-optimising search touches a small fraction of them, so one query
-// per launch costs less device time than one bit of a shared launch.
+// Smaller graphs keep one multi-source search state (msbfs.cu) whose 64 bits
+// are query slots.  A worker thread runs such a graph one BFS level per launch
+// on the graph's own stream.  At every level boundary it retires the queries
+// whose bit stopped advancing (their BFS is complete), and admits waiting
+// queries into free bits as long as their output buffers (8 bytes per vertex)
+// fit in the memory budget.  A query admitted at level l starts from its root
+// in the frontier of level l; its levels are numbered from there, so its
+// result equals a standalone BFS from that root (bits never interact).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,8 +47,9 @@ double now_s()
 
 enum QState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2, Q_RELEASED = 3 };
 
-constexpr int64_t kPlainMinN = int64_t(1) << 21;  // graphs served one query per launch
+constexpr int64_t kPlainMinN = int64_t(1) << 14;  // graphs served one query per launch
 constexpr int kPlainSlots = 2;                    // concurrent searches per such graph
+constexpr int kMaxPlainSlots = 8;
 
 struct PlainSlot {
     cudaStream_t stream = nullptr;
@@ -91,7 +94,8 @@ struct GraphRun {
     int64_t n_launch = 0, n_admit = 0;
     double t_launch = 0, busy_s = 0;
     int plain_blocks = 0;
-    PlainSlot ps[kPlainSlots];
+    PlainSlot ps[kMaxPlainSlots];
+    int nplain = 0;  // slots in use
     std::vector<OutBuf> free_out;  // reusable buffers
     std::vector<OutBuf> all_out;   // every buffer ever made (freed at destroy)
 };
@@ -152,7 +156,7 @@ size_t out_bytes(const gb_graph *g) { return (size_t)g->n * 8; }
 bool gb_server::step_plain(GraphRun &G)
 {
     bool busy = false;
-    for (int i = 0; i < kPlainSlots; ++i) {
+    for (int i = 0; i < G.nplain; ++i) {
         PlainSlot &P = G.ps[i];
         if (P.q >= 0) {
             const cudaError_t e = cudaEventQuery(P.ev);
@@ -344,6 +348,14 @@ gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb
         const int sc = std::atoi(env);
         if (sc >= 0 && sc <= 31) plain_min = int64_t(1) << sc;
     }
+    // GB_SERVE_SLOTS: concurrent single-source searches per graph (1..8), each
+    // on an equal share of the device's SMs (GB_SERVE_FULL_GRID=1: whole grid each)
+    int nplain = kPlainSlots;
+    if (const char *env = std::getenv("GB_SERVE_SLOTS")) {
+        const int k = std::atoi(env);
+        if (k >= 1 && k <= kMaxPlainSlots) nplain = k;
+    }
+    const bool full_grid = std::getenv("GB_SERVE_FULL_GRID") != nullptr;
     int64_t ntot = 0;  // vertices of the graphs batched as bits (the small ones)
     for (int i = 0; i < ng; ++i) ntot += (gs[i] && gs[i]->n < plain_min) ? gs[i]->n : 0;
     gb_status rc = GB_OK;
@@ -361,11 +373,11 @@ gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb
             G.slots.lev[b] = nullptr;
             G.slots.start[b] = 0;
         }
-        const bool full_grid = !std::getenv("GB_SERVE_SHARE_GPU");
         if (G.g->n >= plain_min) {
             G.plain = true;
-            G.plain_blocks = full_grid ? ctx->bfs_blocks2 : std::max(8, ctx->bfs_blocks2 / kPlainSlots);
-            for (int k = 0; k < kPlainSlots && rc == GB_OK; ++k) {
+            G.nplain = nplain;
+            G.plain_blocks = full_grid ? ctx->bfs_blocks2 : std::max(8, ctx->bfs_blocks2 / nplain);
+            for (int k = 0; k < nplain && rc == GB_OK; ++k) {
                 PlainSlot &P = G.ps[k];
                 if (cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking) != cudaSuccess ||
                     cudaEventCreateWithFlags(&P.ev, cudaEventDisableTiming) != cudaSuccess ||

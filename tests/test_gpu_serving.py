@@ -124,7 +124,7 @@ def test_submit_rejects_bad_queries(resident):
 
 
 def test_large_graphs_run_one_search_per_query():
-    # graphs of 2^21+ vertices are served by concurrent single-source searches;
+    # graphs of 2^14+ vertices are served by concurrent single-source searches;
     # their results follow the canonical_parents option like bfs() itself
     gb.bfs_set_options(canonical_parents=1)
     big = gb.graph_build_csr(gb.kron_generate(**W.GraphSpec(scale=21).kron_args()), 21)
