@@ -147,8 +147,10 @@ gb_status graph_csr_view(const gb_graph *g, const int64_t **off, const int32_t *
  *   timeout_ms         limit of every device-side wait (grid barriers, the
  *                      radix-sort look-back); on expiry the kernel records
  *                      GB_ERR_TIMEOUT and returns.
- *   blocks_per_sm      2 or 3: resident blocks of the single-source kernel
- *                      per SM (3 trades register spills for more warps). */
+ *   blocks_per_sm      1, 2 or 3: blocks of the single-source kernel per SM
+ *                      (3 trades register spills for more warps; 1 halves the
+ *                      grid of 2, which makes the per-level grid barrier
+ *                      cheaper on small graphs). */
 typedef struct gb_bfs_options {
     int canonical_parents;
     double alpha;

@@ -30,7 +30,7 @@ PLAIN_SPACE = {
     "alpha": [2.0, 4.0, 8.0, 14.0, 32.0, 64.0, 128.0, 256.0, 1024.0],
     "beta": [6.0, 12.0, 24.0, 64.0, 256.0],
     "big_degree": [64, 256, 1024, 4096],
-    "blocks_per_sm": [2, 3],
+    "blocks_per_sm": [1, 2, 3],
 }
 MS_SPACE = {
     "ms_alpha": [1.0, 4.0, 16.0, 64.0, 256.0],

@@ -336,9 +336,9 @@ gb_status bfs_set_options(const gb_bfs_options *opt)
 {
     if (!opt || !(opt->alpha > 0) || !(opt->beta > 0) || opt->big_degree < 1 ||
         !(opt->ms_alpha > 0) || !(opt->ms_beta > 0) || !(opt->timeout_ms > 0) ||
-        (opt->blocks_per_sm != 2 && opt->blocks_per_sm != 3)) {
+        opt->blocks_per_sm < 1 || opt->blocks_per_sm > 3) {
         set_error("bfs_set_options: alpha, beta, ms_alpha, ms_beta, timeout_ms must be > 0, "
-                  "big_degree >= 1 and blocks_per_sm 2 or 3");
+                  "big_degree >= 1 and blocks_per_sm 1, 2 or 3");
         return GB_ERR_INVALID;
     }
     options() = *opt;

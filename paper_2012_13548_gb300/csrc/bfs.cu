@@ -775,8 +775,10 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.canonical = o.canonical_parents;
     a.timeout_ns = timeout_ns();
     void *args[] = {&a};
-    const int minb = o.blocks_per_sm == 2 ? 2 : 3;
-    const int full = minb == 2 ? ctx->bfs_blocks2 : ctx->bfs_blocks;
+    // 1 block per SM runs the 2-per-SM kernel on half its grid
+    const int minb = o.blocks_per_sm == 3 ? 3 : 2;
+    const int full = minb == 3 ? ctx->bfs_blocks
+                               : (o.blocks_per_sm == 1 ? std::max(1, ctx->bfs_blocks2 / 2) : ctx->bfs_blocks2);
     const int blocks = grid > 0 && grid < full ? grid : full;
     const void *kern = minb == 2 ? (const void *)bfs_kernel<2> : (const void *)bfs_kernel<3>;
     GB_CUDA(cudaLaunchCooperativeKernel(kern, dim3(blocks),

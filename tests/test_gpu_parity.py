@@ -168,6 +168,7 @@ SWITCHES = {
     "flip_flop": dict(alpha=1e9, beta=1e-9),
     "tiny_big_degree": dict(big_degree=1),
     "three_blocks_per_sm": dict(blocks_per_sm=3),
+    "one_block_per_sm": dict(blocks_per_sm=1),
 }
 
 
