@@ -25,8 +25,14 @@ def main():
     p.add_argument("--alpha", type=float, default=None)
     p.add_argument("--beta", type=float, default=None)
     p.add_argument("--blocks-per-sm", type=int, default=None)
+    p.add_argument("--tuned", action="store_true",
+                   help="apply tune_table.json's options for this SCALE first (as bench.py does)")
     a = p.parse_args()
     spec = W.GraphSpec(scale=a.scale)
+    if a.tuned:
+        from . import autotune
+        autotune.apply_tuned("plain", a.scale)
+        autotune.apply_tuned("batched", a.scale)
     opts = dict(canonical_parents=a.canonical)
     if a.alpha is not None:
         opts["alpha"] = a.alpha
