@@ -22,6 +22,14 @@
 //  round, with a prefix-OR over the lanes so that each bit is credited to its
 //  first (smallest-id) neighbour.
 //
+// Outputs of batch calls: as bits are found their parents and levels go to
+// vertex-major staging arrays ([n][k]: the bits of one vertex share a few
+// cache lines), and after the last level the same kernel writes the [k][n]
+// outputs from them, every entry once (-1 where the vertex's seen mask lacks
+// the bit).  Written straight into the [k][n] rows, each found bit was its
+// own partially written sector in a different row; that cost ~70% of a
+// 64-root search.
+//
 // The same kernel runs a batch of graphs: vertex ids are made global by
 // per-graph offsets, every graph's roots use the low bits, and since the
 // graphs share no edges their searches cannot mix.  Masks are uint64 for up
@@ -59,6 +67,9 @@ struct MsGraph {
     int64_t n;
     int32_t *par;  // [k][n]
     int32_t *lev;  // [k][n]
+    int32_t *pst;  // batch calls: parents staged vertex-major, [n][kst]
+    int32_t *lst;  // and levels
+    int64_t kst;
 };
 
 }  // namespace
@@ -193,7 +204,7 @@ __device__ __forceinline__ void write_parents(const MsGraph &G, const MsSlots *S
         const int b = __ffsll((unsigned long long)bits) - 1;
         bits &= bits - 1;
         if (S) S->par[b][local] = p;
-        else G.par[(int64_t)b * G.n + local] = p;
+        else G.pst[local * G.kst + b] = p;
     }
 }
 
@@ -206,7 +217,7 @@ __device__ __forceinline__ void write_levels(const MsGraph &G, const MsSlots *S,
         const int b = __ffsll((unsigned long long)bits) - 1;
         bits &= bits - 1;
         if (S) S->lev[b][local] = lvl - S->start[b];
-        else G.lev[(int64_t)b * G.n + local] = lvl;
+        else G.lst[local * G.kst + b] = lvl;
     }
 }
 
@@ -443,24 +454,10 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
     MsHeader *h = a.hdr;
 
     if (a.do_init) {
-        // ---- outputs -1, masks clear; isolated vertices start fully seen: no
-        // search reaches them and the bottom-up step skips them
-        for (int g = 0; g < a.ng; ++g) {
-            const MsGraph G = s_g[g];
-            const int64_t cnt = (int64_t)a.k * G.n;
-            for (int64_t i = gtid; i < cnt; i += gthreads) {
-                G.par[i] = -1;
-                G.lev[i] = -1;
-            }
-        }
+        // ---- masks clear (the outputs are written once, at the end, from the
+        // staged values; a bit is in seen iff its search reached the vertex)
         for (int64_t i = gtid; i < a.mstride; i += gthreads) {
-            T s0 = 0;
-            if (i < ntot) {
-                const int g = find_graph(s_voff, a.ng, i);
-                const int64_t lu = i - s_g[g].voff;
-                if (!((s_g[g].nz[lu >> 5] >> (lu & 31)) & 1u)) s0 = all;
-            }
-            a.seen[i] = s0;
+            a.seen[i] = 0;
             a.mbuf[i] = 0;
             a.mbuf[a.mstride + i] = 0;
             a.mbuf[2 * a.mstride + i] = 0;
@@ -486,8 +483,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                     }
                     a.mbuf[gid] |= (T)((T)1 << b);
                     a.seen[gid] |= (T)((T)1 << b);
-                    G.par[(int64_t)b * G.n + r] = (int32_t)r;
-                    G.lev[(int64_t)b * G.n + r] = 0;
+                    G.pst[r * G.kst + b] = (int32_t)r;
+                    G.lst[r * G.kst + b] = 0;
                 }
             }
             h->ctl[0].na = na;
@@ -713,6 +710,25 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
         }
     }
 
+    // ---- batch calls: the [k][n] outputs from the staged values, each entry
+    // written once; a warp takes 32 consecutive vertices, so for every bit the
+    // warp's stores fill one contiguous run of the output row
+    if (!a.slots) {
+        for (int64_t v0 = gwarp * 32; v0 < ntot; v0 += nwarps * 32) {
+            const int64_t gv = v0 + lane;
+            if (gv >= ntot) continue;
+            const int g = find_graph(s_voff, a.ng, gv);
+            const MsGraph &G = s_g[g];
+            const int64_t lu = gv - G.voff;
+            const T sn = ld_mask(&a.seen[gv]);
+            for (int b = 0; b < a.k; ++b) {
+                const bool has = (sn >> b) & 1;
+                G.par[(int64_t)b * G.n + lu] = has ? G.pst[lu * G.kst + b] : -1;
+                G.lev[(int64_t)b * G.n + lu] = has ? G.lst[lu * G.kst + b] : -1;
+            }
+        }
+    }
+
     if (!a.stats) return;
     my_edges = warp_sum(my_edges);
     my_touched = warp_sum(my_touched);
@@ -769,6 +785,14 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     const size_t total = o_big + 2 * bigcap * sizeof(unsigned long long);
     unsigned char *ws = nullptr;
     GB_CUDA(cudaMallocAsync((void **)&ws, total, s));
+    // vertex-major staging of parents and levels, [ntot][k] each
+    int32_t *stage = nullptr;
+    GB_CUDA(cudaMallocAsync((void **)&stage, 2 * (size_t)ntot * k * sizeof(int32_t), s));
+    for (int i = 0; i < ng; ++i) {
+        gs[i].pst = stage + gs[i].voff * k;
+        gs[i].lst = stage + (size_t)ntot * k + gs[i].voff * k;
+        gs[i].kst = k;
+    }
     GB_CUDA(cudaMemsetAsync(ws, 0, sizeof(MsHeader), s));
     GB_CUDA(cudaMemcpyAsync(ws + o_g, gs.data(), ng * sizeof(MsGraph), cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaMemcpyAsync(ws + o_r, roots.data(), (size_t)ng * k * sizeof(int64_t),
@@ -803,6 +827,7 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
                                         dim3(MS_THREADS), args, 0, s));
     note_launch();
     GB_CUDA(cudaFreeAsync(ws, s));
+    GB_CUDA(cudaFreeAsync(stage, s));
     return GB_OK;
 }
 
@@ -959,6 +984,9 @@ gb_status ms_serve_create(const gb_graph *g, int blocks, MsServe **out, cudaStre
     G.n = n;
     G.par = nullptr;
     G.lev = nullptr;
+    G.pst = nullptr;  // serving writes into the per-query slots instead
+    G.lst = nullptr;
+    G.kst = 0;
     m->graph_host = G;
     GB_CUDA(cudaMemsetAsync(m->ws, 0, o_big, s));
     GB_CUDA(cudaMemcpyAsync(m->graph_dev, &m->graph_host, sizeof(MsGraph), cudaMemcpyHostToDevice, s));
