@@ -56,6 +56,7 @@ constexpr int MS_BIG_DEG = 256;
 constexpr int MS_WARPS = MS_THREADS / 32;
 constexpr int MS_QBUF = 256;  // per-warp staging of newly active vertices
 constexpr int MS_BBUF = 32;   // per-warp staging of newly active big vertices
+constexpr int MS_HIST = 8;    // batch calls: levels whose reached-bit masks are kept
 constexpr int SITE_MS_BAR = 30;
 constexpr int SITE_MS_LEVELS = 31;
 
@@ -97,6 +98,8 @@ struct MsArgs {
     const int64_t *roots;   // device [ng][k]: local root ids
     T *seen;
     T *mbuf;                // 3 masks of ntot (ring)
+    T *hist;                // batch calls: bits first reached at levels 0..MS_HIST-1,
+                            // [MS_HIST][mstride]; nullptr in serving
     int32_t *act;           // 3 active lists of ntot (ring)
     unsigned long long *bigq;  // chunk list of big active vertices (gid | cbase << 32)
     int64_t bigcap;
@@ -217,7 +220,7 @@ __device__ __forceinline__ void write_levels(const MsGraph &G, const MsSlots *S,
         const int b = __ffsll((unsigned long long)bits) - 1;
         bits &= bits - 1;
         if (S) S->lev[b][local] = lvl - S->start[b];
-        else G.lst[local * G.kst + b] = lvl;
+        else if (lvl >= MS_HIST) G.lst[local * G.kst + b] = lvl;  // earlier levels: the mask history
     }
 }
 
@@ -483,8 +486,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                     }
                     a.mbuf[gid] |= (T)((T)1 << b);
                     a.seen[gid] |= (T)((T)1 << b);
+                    a.hist[gid] |= (T)((T)1 << b);  // level 0
                     G.pst[r * G.kst + b] = (int32_t)r;
-                    G.lst[r * G.kst + b] = 0;
                 }
             }
             h->ctl[0].na = na;
@@ -636,6 +639,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                 if (i < nn) {
                     if (a.canonical) write_levels(s_g[g], S, lu, nw, l + 1);
                     st_mask(&a.seen[gu], (T)(ld_mask(&a.seen[gu]) | nw));
+                    if (a.hist && l + 1 < MS_HIST) a.hist[(size_t)(l + 1) * a.mstride + gu] = nw;
                     reached_new += __popcll((unsigned long long)nw);
                     my_any |= nw;
                 }
@@ -669,6 +673,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                     write_levels(s_g[g], S, lu, found, l + 1);
                     st_mask(&a.seen[gu], (T)(sn | found));
                     st_mask(&Mn[gu], found);
+                    if (a.hist && l + 1 < MS_HIST) a.hist[(size_t)(l + 1) * a.mstride + gu] = found;
                     reached_new += __popcll((unsigned long long)found);
                     my_any |= found;
                 }
@@ -721,10 +726,18 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             const MsGraph &G = s_g[g];
             const int64_t lu = gv - G.voff;
             const T sn = ld_mask(&a.seen[gv]);
+            T hm[MS_HIST];
+#pragma unroll
+            for (int j = 0; j < MS_HIST; ++j) hm[j] = a.hist[(size_t)j * a.mstride + gv];
             for (int b = 0; b < a.k; ++b) {
                 const bool has = (sn >> b) & 1;
+                int32_t lvl = -1;
+#pragma unroll
+                for (int j = 0; j < MS_HIST; ++j)
+                    if ((hm[j] >> b) & 1) lvl = j;
+                if (has && lvl < 0) lvl = G.lst[lu * G.kst + b];
                 G.par[(int64_t)b * G.n + lu] = has ? G.pst[lu * G.kst + b] : -1;
-                G.lev[(int64_t)b * G.n + lu] = has ? G.lst[lu * G.kst + b] : -1;
+                G.lev[(int64_t)b * G.n + lu] = has ? lvl : -1;
             }
         }
     }
@@ -788,6 +801,9 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     // vertex-major staging of parents and levels, [ntot][k] each
     int32_t *stage = nullptr;
     GB_CUDA(cudaMallocAsync((void **)&stage, 2 * (size_t)ntot * k * sizeof(int32_t), s));
+    T *hist = nullptr;  // reached-bit masks of the first MS_HIST levels
+    GB_CUDA(cudaMallocAsync((void **)&hist, (size_t)MS_HIST * np * sizeof(T), s));
+    GB_CUDA(cudaMemsetAsync(hist, 0, (size_t)MS_HIST * np * sizeof(T), s));
     for (int i = 0; i < ng; ++i) {
         gs[i].pst = stage + gs[i].voff * k;
         gs[i].lst = stage + (size_t)ntot * k + gs[i].voff * k;
@@ -807,6 +823,7 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     a.roots = reinterpret_cast<const int64_t *>(ws + o_r);
     a.seen = reinterpret_cast<T *>(ws + o_seen);
     a.mbuf = reinterpret_cast<T *>(ws + o_m);
+    a.hist = hist;
     a.act = reinterpret_cast<int32_t *>(ws + o_act);
     a.bigq = reinterpret_cast<unsigned long long *>(ws + o_big);
     a.bigcap = bigcap;
@@ -828,6 +845,7 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     note_launch();
     GB_CUDA(cudaFreeAsync(ws, s));
     GB_CUDA(cudaFreeAsync(stage, s));
+    GB_CUDA(cudaFreeAsync(hist, s));
     return GB_OK;
 }
 
@@ -1051,6 +1069,7 @@ gb_status ms_serve_step(MsServe *m, int level, unsigned long long active, MsCtl 
     a.roots = nullptr;
     a.seen = m->seen;
     a.mbuf = m->mbuf;
+    a.hist = nullptr;  // serving writes levels into the per-query slots
     a.act = m->act;
     a.bigq = m->bigq;
     a.bigcap = m->bigcap;
