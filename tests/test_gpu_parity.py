@@ -277,6 +277,33 @@ def test_msbfs_repeated_roots_and_random_graphs(canonical):
             check_row(off, col, r, np_(P[i]), np_(L[i]), p_ref, l_ref, canonical, (trial, i, r))
 
 
+def _path_and_cycle_csr():
+    # a 200-vertex path and a 150-vertex cycle: searches 100+ levels deep
+    e = [(i, i + 1) for i in range(199)] + [(200 + i, 200 + (i + 1) % 150) for i in range(150)]
+    e = np.array(e, dtype=np.int64).T.copy()
+    off, col = oracle.csr_build(e, 9)
+    return off[: 350 + 1].copy(), col
+
+
+@pytest.mark.parametrize("canonical", [0, 1])
+def test_batched_searches_deeper_than_the_level_history(canonical):
+    # levels past the batched kernel's mask history take its per-bit path
+    gb.bfs_set_options(canonical_parents=canonical)
+    off, col = _path_and_cycle_csr()
+    G = gb.graph_from_csr(torch.as_tensor(off).cuda(), torch.as_tensor(col).cuda())
+    roots = [0, 199, 100, 57, 200, 275, 349, 3]
+    P, L = gb.bfs_batch(G, roots)
+    for i, r in enumerate(roots):
+        p_ref, l_ref = oracle.bfs(off, col, r)
+        assert int(l_ref.max()) >= 74
+        check_row(off, col, r, np_(P[i]), np_(L[i]), p_ref, l_ref, canonical, (i, r))
+    P2, L2 = gb.bfs_multi_graph([G, G], [roots[:4], roots[4:]])
+    for gi, rs in enumerate([roots[:4], roots[4:]]):
+        for b, r in enumerate(rs):
+            p_ref, l_ref = oracle.bfs(off, col, r)
+            check_row(off, col, r, np_(P2[gi][b]), np_(L2[gi][b]), p_ref, l_ref, canonical, (gi, b))
+
+
 @pytest.mark.parametrize("canonical", [0, 1])
 @pytest.mark.parametrize("lo,hi,count", [(4, 9, 32), (12, 18, 32)])
 def test_multi_graph_batch_equals_standalone(lo, hi, count, canonical):
