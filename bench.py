@@ -334,6 +334,25 @@ def run_ours(args, dist):
     for r in rec:
         r[5].free()
 
+    # generator and kernel 1 fused (no edge list) against the generator plus kernel 1,
+    # outside the timed region
+    def once(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), out
+    gen_ms, fused_ms = [], []
+    for _ in range(2):
+        t, e2 = once(lambda: gb.kron_generate(**spec.kron_args()))
+        gen_ms.append(t)
+        del e2
+        t, g3 = once(lambda: gb.graph_generate_csr(**spec.kron_args()))
+        fused_ms.append(t)
+        g3.free()
+    torch.cuda.empty_cache()
+
     # the batched search's rows (from the last timed step) validated too
     batch_invalid = []
     for i, r in enumerate(roots):
@@ -389,7 +408,9 @@ def run_ours(args, dist):
                             "vs_plain": batched_gteps / hm, "roots": len(roots)},
                 "kernel1": {"ms": statistics.median(k1_ms),
                             "gbs": k1_bytes / (statistics.median(k1_ms) * 1e-3) / 1e9,
-                            "alg_bytes": k1_bytes},
+                            "alg_bytes": k1_bytes,
+                            "generator_ms": min(gen_ms),
+                            "fused_generate_build_ms": min(fused_ms)},
                 "validation": {"on": "device (bfs_validate, Graph500 rules 1-7)",
                                "trees": 2 * len(roots) * dist.world, "invalid_max_per_rank": n_invalid,
                                "first_failures": (invalid + batch_invalid)[:4]},

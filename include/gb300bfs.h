@@ -110,6 +110,19 @@ gb_status kron_generate(int scale, int edgefactor, double a, double b, double c,
 gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph **out,
                           gb_stream s);
 
+/* Sec. 2.1 and Sec. 2.2 fused: the graph graph_build_csr builds from the
+ * tuples of kron_generate(scale, edgefactor, a, b, c, seed_gen, seed_perm,
+ * any seed_shuf), bit for bit, without the edge list: each generated tuple,
+ * relabelled, goes straight into kernel 1's sort as its two symmetric keys.
+ * The shuffle of Sec. 2.1 only reorders tuples, which the CSR does not see,
+ * so it is skipped (there is no seed_shuf).  The same argument ranges and
+ * errors as kron_generate.  Synchronises `s`; temporary device memory about
+ * 32 * m bytes (the two separate calls need 16 * m more, for the edge list).
+ * *out receives a library-owned graph; free it with graph_free. */
+gb_status graph_generate_csr(int scale, int edgefactor, double a, double b, double c,
+                             uint64_t seed_gen, uint64_t seed_perm, gb_graph **out,
+                             gb_stream s);
+
 /* Wrap a caller-built CSR (device arrays off int64 [n+1], col int32 [nnz]):
  * the arrays are copied into library-owned memory.  The rows must be sorted
  * ascending, free of self-loops and duplicates, and symmetric; only

@@ -5,8 +5,10 @@
 
 For each SCALE it builds the seeded Kronecker graph, then improves the options
 by coordinate descent: one option at a time takes each of its candidate values
-while the others stay fixed, and the fastest value (median CUDA-event time over
-the tuning roots, L2 flushed before every timed call) is kept.  Three call
+while the others stay fixed, and the fastest value (CUDA-event time over the
+tuning roots, L2 flushed before every timed call: the mean over 16 roots for
+single-source searches, whose harmonic-mean rate the slow roots govern; the
+median of repeated launches for the batched calls) is kept.  Three call
 kinds are tuned:
 
   plain       bfs(): alpha, beta (direction switch), big_degree (frontier
@@ -91,14 +93,18 @@ def tune_scale(scale, roots=8, kinds=("plain", "batched")):
     out = {}
 
     if "plain" in kinds:
+        # the mean time over the roots: a harmonic mean of per-root rates (the
+        # reported GTEPS) is governed by the slow roots, which a median hides
+        prs = [int(r) for r in W.select_roots(off.cpu().numpy(), max(roots, 16), spec.seeds()[3])]
+
         def ev_plain(opts):
             gb.bfs_set_options(**opts)
-            for r in rs[:2]:
+            for r in prs[:2]:
                 gb.bfs(g, r, parent, level)          # warm-up
-            return statistics.median(timed(lambda r=r: gb.bfs(g, r, parent, level)) for r in rs)
+            return statistics.mean(timed(lambda r=r: gb.bfs(g, r, parent, level)) for r in prs)
         start = {k: base[k] for k in PLAIN_SPACE}
         best, t, _ = descend(ev_plain, PLAIN_SPACE, start)
-        out["plain/%d" % scale] = dict(best, median_ms=round(t, 4))
+        out["plain/%d" % scale] = dict(best, mean_ms=round(t, 4))
         gb.bfs_set_options(**base)
 
     if "batched" in kinds:
@@ -166,7 +172,7 @@ def tuned_options(kind, scale=None, path=DEFAULT_TABLE):
             return {}
         best = min(keys, key=lambda k: abs(int(k.split("/")[1]) - (scale or 0)))
         ent = table[best]
-    return {k: v for k, v in ent.items() if k != "median_ms"}
+    return {k: v for k, v in ent.items() if k not in ("median_ms", "mean_ms")}
 
 
 def apply_tuned(kind, scale=None, path=DEFAULT_TABLE):

@@ -75,6 +75,9 @@ def lib():
                                              ctypes.c_uint64, ctypes.c_uint64, _vp, _vp]),
             "graph_build_csr": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.POINTER(_vp), _vp]),
             "graph_from_csr": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.POINTER(_vp), _vp]),
+            "graph_generate_csr": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                                  ctypes.c_uint64, ctypes.POINTER(_vp), _vp]),
             "graph_free": (ctypes.c_int, [_vp]),
             "graph_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
             "graph_csr_view": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
@@ -108,7 +111,7 @@ def lib():
 def exported_symbols():
     """Names of the C-ABI functions this binding wraps."""
     return ["gb_last_error", "gb_abi_version", "gb_kernel_launches", "gb_device_status", "kron_generate",
-            "graph_build_csr", "graph_from_csr", "graph_free", "graph_info", "graph_csr_view",
+            "graph_build_csr", "graph_from_csr", "graph_generate_csr", "graph_free", "graph_info", "graph_csr_view",
             "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
             "bfs_last_stats", "bfs_noalloc", "bfs_validate", "server_create", "server_submit", "server_poll", "server_release",
             "server_run_trace", "server_destroy"]
@@ -211,6 +214,17 @@ def graph_build_csr(edges, scale, stream=None):
     h = _vp()
     _check(lib().graph_build_csr(_dev(edges, torch.int64, "edges"), edges.shape[1], scale,
                                  ctypes.byref(h), _stream(stream)))
+    return Graph(h.value)
+
+
+def graph_generate_csr(scale, edgefactor, a, b, c, seed_gen, seed_perm, seed_shuf=None,
+                       stream=None):
+    """Generator and kernel 1 fused: the Graph that graph_build_csr(kron_generate(...))
+    gives for the same parameters, built without the edge list (seed_shuf, which
+    only orders the tuples, is accepted and ignored)."""
+    h = ctypes.c_void_p()
+    _check(lib().graph_generate_csr(int(scale), int(edgefactor), float(a), float(b), float(c),
+                                    int(seed_gen), int(seed_perm), ctypes.byref(h), _stream(stream)))
     return Graph(h.value)
 
 

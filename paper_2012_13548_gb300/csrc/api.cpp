@@ -224,6 +224,34 @@ gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *
     });
 }
 
+gb_status graph_generate_csr(int scale, int edgefactor, double a, double b, double c,
+                             uint64_t seed_gen, uint64_t seed_perm, gb_graph **out, gb_stream s)
+{
+    return guarded([&]() {
+        if (!out) {
+            set_error("graph_generate_csr: out == NULL");
+            return GB_ERR_INVALID;
+        }
+        if (!(a >= 0 && b >= 0 && c >= 0 && a + b + c <= 1.0 + 1e-12)) {
+            set_error("graph_generate_csr: initiator probabilities must be >= 0 with a+b+c <= 1");
+            return GB_ERR_INVALID;
+        }
+        *out = nullptr;
+        gb_graph *g = new gb_graph();
+        gb_status rc = kron_csr(scale, edgefactor, a, b, c, seed_gen, seed_perm, g, as_stream(s));
+        if (rc != GB_OK) {
+            if (g->off) cudaFree(g->off);
+            if (g->col) cudaFree(g->col);
+            if (g->nz) cudaFree(g->nz);
+            if (g->hub) cudaFree(g->hub);
+            delete g;
+            return rc;
+        }
+        *out = g;
+        return GB_OK;
+    });
+}
+
 gb_status graph_from_csr(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
                          gb_graph **out, gb_stream s)
 {

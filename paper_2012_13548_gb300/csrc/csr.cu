@@ -266,35 +266,22 @@ gb_status build_graph_aux(gb_graph *g, cudaStream_t s)
     return GB_OK;
 }
 
-gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s)
+namespace {
+
+// Stages 2-4 on the symmetrised keys k0[0..nk) (k1: the sort's second buffer
+// of nk keys); both buffers are freed here, on every path.
+gb_status csr_from_keys(uint64_t *k0, uint64_t *k1, int64_t nk, int scale, gb_graph *g,
+                        cudaStream_t s)
 {
     Context *ctx = context();
-    if (!ctx) return GB_ERR_CUDA;
-    const int64_t n = int64_t(1) << scale;
-    const int64_t nk = 2 * m;
-    g->n = n;
-    g->scale = scale;
-    g->device = ctx->device;
-    GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
-    if (nk == 0) {
-        g->nnz = 0;
-        GB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(int64_t)));
-        GB_CUDA(cudaMalloc(&g->col, 16));
-        GB_CUDA(cudaMemsetAsync(g->off, 0, (n + 1) * sizeof(int64_t), s));
-        gb_status r0 = build_graph_aux(g, s);
-        if (r0 != GB_OK) return r0;
-        GB_CUDA(cudaStreamSynchronize(s));
-        return GB_OK;
-    }
-    uint64_t *k0 = nullptr, *k1 = nullptr, *ks = nullptr;
-    GB_CUDA(alloc_async(&k0, (size_t)nk, s));
-    GB_CUDA(alloc_async(&k1, (size_t)nk, s));
-    k1_sym_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(edges, m, scale,
-                                                   reinterpret_cast<ulonglong2 *>(k0), ctx->status);
-    note_launch();
-    GB_CUDA(cudaGetLastError());
+    const int64_t n = g->n;
+    uint64_t *ks = nullptr;
     gb_status rc = radix_sort(k0, k1, nullptr, nullptr, nk, 0, 2 * scale, &ks, nullptr, s);
-    if (rc != GB_OK) return rc;
+    if (rc != GB_OK) {
+        cudaFreeAsync(k0, s);
+        cudaFreeAsync(k1, s);
+        return rc;
+    }
     const int64_t ntiles = (nk + FIN_TILE - 1) / FIN_TILE;
     unsigned *tcnt = nullptr;
     unsigned long long *tbase = nullptr;
@@ -333,6 +320,71 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
     GB_CUDA(cudaFreeAsync(tcnt, s));
     GB_CUDA(cudaFreeAsync(tbase, s));
     return build_graph_aux(g, s);
+}
+
+// The graph with no tuples: every row empty.
+gb_status empty_csr(gb_graph *g, cudaStream_t s)
+{
+    g->nnz = 0;
+    GB_CUDA(cudaMalloc(&g->off, (g->n + 1) * sizeof(int64_t)));
+    GB_CUDA(cudaMalloc(&g->col, 16));
+    GB_CUDA(cudaMemsetAsync(g->off, 0, (g->n + 1) * sizeof(int64_t), s));
+    gb_status r0 = build_graph_aux(g, s);
+    if (r0 != GB_OK) return r0;
+    GB_CUDA(cudaStreamSynchronize(s));
+    return GB_OK;
+}
+
+}  // namespace
+
+gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    const int64_t nk = 2 * m;
+    g->n = int64_t(1) << scale;
+    g->scale = scale;
+    g->device = ctx->device;
+    GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
+    if (nk == 0) return empty_csr(g, s);
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    GB_CUDA(alloc_async(&k0, (size_t)nk, s));
+    GB_CUDA(alloc_async(&k1, (size_t)nk, s));
+    k1_sym_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(edges, m, scale,
+                                                   reinterpret_cast<ulonglong2 *>(k0), ctx->status);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
+    return csr_from_keys(k0, k1, nk, scale, g, s);
+}
+
+gb_status kron_csr(int scale, int edgefactor, double a, double b, double c, uint64_t seed_gen,
+                   uint64_t seed_perm, gb_graph *g, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    if (scale < 1 || scale > 30 || edgefactor < 1) {
+        set_error("graph_generate_csr: need 1 <= scale <= 30, edgefactor >= 1");
+        return GB_ERR_INVALID;
+    }
+    if ((int64_t(1) << scale) * edgefactor > (int64_t(1) << 32)) {
+        set_error("graph_generate_csr: more than 2^32 tuples");
+        return GB_ERR_RANGE;
+    }
+    const int64_t nk = 2 * ((int64_t(1) << scale) * edgefactor);
+    g->n = int64_t(1) << scale;
+    g->scale = scale;
+    g->device = ctx->device;
+    GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    GB_CUDA(alloc_async(&k0, (size_t)nk, s));
+    GB_CUDA(alloc_async(&k1, (size_t)nk, s));
+    gb_status rc = kron_keys_impl(scale, edgefactor, a, b, c, seed_gen, seed_perm, k0, s);
+    if (rc != GB_OK) {
+        cudaFreeAsync(k0, s);
+        cudaFreeAsync(k1, s);
+        return rc;
+    }
+    return csr_from_keys(k0, k1, nk, scale, g, s);
 }
 
 }  // namespace gb

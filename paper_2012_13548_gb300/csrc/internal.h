@@ -89,10 +89,16 @@ namespace gb {
 
 // Kernel 1 pieces (csr.cu).
 gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s);
+// Generator and kernel 1 fused: the CSR of the Kronecker graph with no edge list (csr.cu).
+gb_status kron_csr(int scale, int edgefactor, double a, double b, double c, uint64_t seed_gen,
+                   uint64_t seed_perm, gb_graph *g, cudaStream_t s);
 // The degree >= 1 bitmap and the hub array of a graph whose CSR is in place (csr.cu).
 gb_status build_graph_aux(gb_graph *g, cudaStream_t s);
 
 // Kronecker generator (gen.cu).
+// The 2m symmetrised kernel-1 keys of the Kronecker tuples, written to keys (gen.cu).
+gb_status kron_keys_impl(int scale, int edgefactor, double a, double b, double c,
+                         uint64_t seed_gen, uint64_t seed_perm, uint64_t *keys, cudaStream_t s);
 gb_status kron_generate_impl(int scale, int edgefactor, double a, double b, double c,
                              uint64_t seed_gen, uint64_t seed_perm, uint64_t seed_shuf,
                              int64_t *edges, cudaStream_t s);

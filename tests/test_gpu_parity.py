@@ -72,6 +72,40 @@ def test_csr_bit_exact(scale):
     assert np.array_equal(np_(col), col_ref)
 
 
+@pytest.mark.parametrize("scale", [1, 2, 5, 8, 12, 16, 20])
+def test_fused_generate_csr_equals_the_two_step_build(scale):
+    # generator + kernel 1 without the edge list: the same CSR, bit for bit,
+    # as the oracle's build of the oracle's tuples
+    spec = W.GraphSpec(scale=scale)
+    kw = spec.kron_args()
+    G = gb.graph_generate_csr(**kw)
+    _, off_ref, col_ref = oracle_graph(scale)
+    off, col = G.csr()
+    assert np.array_equal(np_(off), off_ref)
+    assert np.array_equal(np_(col), col_ref)
+    # and the search over it is the search over the two-step graph
+    r = roots_for(scale, 1)[0]
+    gb.bfs_set_options(canonical_parents=1)
+    parent, level = gb.bfs(G, r)
+    p_ref, l_ref = oracle_bfs(scale, r)
+    assert np.array_equal(np_(level), l_ref) and np.array_equal(np_(parent), p_ref)
+    G.free()
+
+
+def test_fused_generate_csr_other_initiators_and_bad_arguments():
+    for (a, b, c, ef) in [(0.25, 0.25, 0.25, 4), (0.45, 0.15, 0.15, 8), (1.0, 0.0, 0.0, 2)]:
+        kw = dict(scale=9, edgefactor=ef, a=a, b=b, c=c, seed_gen=11, seed_perm=12, seed_shuf=13)
+        G = gb.graph_generate_csr(**kw)
+        off_ref, col_ref = oracle.csr_build(oracle.kron_generate(**kw), 9)
+        off, col = G.csr()
+        assert np.array_equal(np_(off), off_ref) and np.array_equal(np_(col), col_ref), (a, b, c, ef)
+        G.free()
+    with pytest.raises(gb.GbError, match="INVALID"):
+        gb.graph_generate_csr(0, 16, 0.57, 0.19, 0.19, 1, 2)
+    with pytest.raises(gb.GbError, match="INVALID"):
+        gb.graph_generate_csr(10, 16, 0.6, 0.3, 0.3, 1, 2)
+
+
 def test_generator_other_initiators_and_edgefactors():
     for (a, b, c, ef, scale) in [(0.25, 0.25, 0.25, 1, 9), (0.45, 0.15, 0.15, 3, 11),
                                  (1.0, 0.0, 0.0, 2, 5), (0.0, 0.0, 0.0, 2, 5)]:
