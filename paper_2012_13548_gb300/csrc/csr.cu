@@ -12,9 +12,10 @@
 //      repeats the previous offset and off[n] = nnz (Sec. 2.2).
 //
 // Two per-vertex arrays that the search consults are derived from the CSR:
-// the degree >= 1 bitmap, and for every row of degree <= HUB_MAX_DEG one of
-// its neighbours of largest degree (the "hub" that the bottom-up step tests
-// first: a neighbour with many edges is the likeliest to sit in the frontier).
+// the degree >= 1 bitmap, and for every row one of its neighbours of largest
+// degree (the "hub" that the bottom-up step tests first: a neighbour with many
+// edges is the likeliest to sit in the frontier; rows longer than HUB_SCAN
+// are sampled by their first HUB_SCAN entries).
 #include "common.cuh"
 #include "internal.h"
 
@@ -105,6 +106,11 @@ __global__ void __launch_bounds__(1024) k1_scan_tiles_kernel(const unsigned *__r
     if (tid == blockDim.x - 1) base[ntiles] = run;
 }
 
+// Warp-striped: warp w of the tile takes keys [t0 + w*WARP_KEYS, +WARP_KEYS),
+// lane i of round j the key t0 + w*WARP_KEYS + 32 j + i, so that loads and
+// column stores are coalesced; a key's predecessor comes from the next-lower
+// lane (lane 0: the previous round's lane 31, or memory at the warp's start).
+constexpr int WARP_KEYS = FIN_TILE / (FIN_THREADS / 32);  // 512
 __global__ void __launch_bounds__(FIN_THREADS) k1_write_kernel(
     const uint64_t *__restrict__ keys, int64_t nk, int scale,
     const unsigned long long *__restrict__ tile_base, int64_t n, int64_t *__restrict__ off,
@@ -114,38 +120,53 @@ __global__ void __launch_bounds__(FIN_THREADS) k1_write_kernel(
     const uint64_t vmask = (uint64_t(1) << scale) - 1;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    // blocked: thread t owns keys [t0 + t*ITEMS, t0 + (t+1)*ITEMS)
-    const int64_t i0 = (int64_t)blockIdx.x * FIN_TILE + (int64_t)threadIdx.x * FIN_ITEMS;
-    uint64_t k[FIN_ITEMS];
-    unsigned keep = 0, c = 0;
+    const int64_t w0 = (int64_t)blockIdx.x * FIN_TILE + (int64_t)warp * WARP_KEYS;
+    constexpr int ROUNDS = WARP_KEYS / 32;
+    // pass 1: the warp's kept keys (self-loops and repeats dropped)
+    uint64_t k[ROUNDS];
+    unsigned total = 0;
+    uint64_t prev = w0 > 0 && w0 - 1 < nk ? keys[w0 - 1] : ~0ull;  // predecessor of the warp's first key
 #pragma unroll
-    for (int j = 0; j < FIN_ITEMS; ++j) {
-        const int64_t i = i0 + j;
+    for (int j = 0; j < ROUNDS; ++j) {
+        const int64_t i = w0 + 32 * j + lane;
         k[j] = i < nk ? keys[i] : 0;
-        const bool kp = i < nk && k1_keep(keys, i, k[j], scale, vmask);
-        keep |= (unsigned)kp << j;
-        c += kp;
+        uint64_t kp = __shfl_up_sync(kFull, k[j], 1);
+        if (lane == 0) kp = prev;
+        prev = __shfl_sync(kFull, k[j], 31);
+        const bool keep = i < nk && (k[j] >> scale) != (k[j] & vmask) && (i == 0 || kp != k[j]);
+        total += __popc(__ballot_sync(kFull, keep));
     }
-    const unsigned incl = warp_inclusive_scan(c);
-    if (lane == 31) s_w[warp] = incl;
+    if (lane == 0) s_w[warp] = total;
     __syncthreads();
     unsigned woff = 0;
     for (int w = 0; w < warp; ++w) woff += s_w[w];
-    int64_t pos = (int64_t)tile_base[blockIdx.x] + woff + incl - c;
+    int64_t base = (int64_t)tile_base[blockIdx.x] + woff;
+    // pass 2: columns at their positions; every change of row writes the
+    // offsets of the rows it passes (an empty row repeats the offset)
+    prev = w0 > 0 && w0 - 1 < nk ? keys[w0 - 1] : ~0ull;
 #pragma unroll
-    for (int j = 0; j < FIN_ITEMS; ++j) {
-        const int64_t i = i0 + j;
-        if (i >= nk) break;
-        const int64_t r = (int64_t)(k[j] >> scale);
-        const int64_t rp = i == 0 ? -1 : (int64_t)(keys[i - 1] >> scale);
-        for (int64_t x = rp + 1; x <= r; ++x) off[x] = pos;  // rows rp+1..r start here
-        if ((keep >> j) & 1u) {
-            if (pos < nnz) col[pos] = (int32_t)(k[j] & vmask);
-            else record_error(st, GB_ERR_RANGE, 11, pos);
-            ++pos;
+    for (int j = 0; j < ROUNDS; ++j) {
+        const int64_t i = w0 + 32 * j + lane;
+        uint64_t kp = __shfl_up_sync(kFull, k[j], 1);
+        if (lane == 0) kp = prev;
+        prev = __shfl_sync(kFull, k[j], 31);
+        const bool keep = i < nk && (k[j] >> scale) != (k[j] & vmask) && (i == 0 || kp != k[j]);
+        const unsigned keepm = __ballot_sync(kFull, keep);
+        const int64_t pos = base + __popc(keepm & lanemask_lt());
+        if (i < nk) {
+            const int64_t r = (int64_t)(k[j] >> scale);
+            const int64_t rp = i == 0 ? -1 : (int64_t)(kp >> scale);
+            for (int64_t x = rp + 1; x <= r; ++x) off[x] = pos;  // rows rp+1..r start here
+            if (keep) {
+                if (pos < nnz) col[pos] = (int32_t)(k[j] & vmask);
+                else record_error(st, GB_ERR_RANGE, 11, pos);
+            }
+            if (i == nk - 1) {
+                const int64_t end = pos + (keep ? 1 : 0);
+                for (int64_t x = r + 1; x <= n; ++x) off[x] = end;  // trailing empty rows, off[n]
+            }
         }
-        if (i == nk - 1)
-            for (int64_t x = r + 1; x <= n; ++x) off[x] = pos;  // trailing empty rows, off[n]
+        base += __popc(keepm);
     }
 }
 
@@ -165,7 +186,7 @@ __global__ void nz_bitmap_kernel(const int64_t *__restrict__ off, int64_t n,
 }
 
 constexpr int HUB_THREADS = 256;
-constexpr int64_t HUB_MAX_DEG = 4096;  // longer rows get no hub (hubs are visited early)
+constexpr int64_t HUB_SCAN = 128;  // entries of a row examined for its hub
 
 // An 8-bit increasing key of the degree: 8 * floor(log2 d) + the next three
 // bits of d, plus one (0 for an empty row).
@@ -185,8 +206,11 @@ __global__ void deg_key_kernel(const int64_t *__restrict__ off, int64_t n, uint8
     }
 }
 
-// hub[u] = the neighbour of u with the largest degree key, the smallest id
-// among equals; -1 for an empty row or one longer than HUB_MAX_DEG.  A warp
+// hub[u] = among the first HUB_SCAN neighbours of u (all of them for a shorter
+// row) the one with the largest degree key, the smallest id among equals; -1
+// for an empty row.  The hub is a heuristic (the bottom-up step tests it
+// first), so long rows, whose vertices are reached early anyway, are only
+// sampled: every row costs at most HUB_SCAN entries.  A warp
 // takes 32 rows and streams their edges as one sequence (lane k of a round
 // reads entry k), each edge folded into its row's slot with a shared-memory
 // atomic max of (key << 32 | ~v).
@@ -207,7 +231,8 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const int64_t *__restr
         if (r < n) {
             s0 = off[r];
             d = off[r + 1] - s0;
-            if (d > HUB_MAX_DEG || d < 0 || s0 < 0 || s0 + d > nnz) d = 0;
+            if (d < 0 || s0 < 0 || s0 + d > nnz) d = 0;
+            if (d > HUB_SCAN) d = HUB_SCAN;
         }
         s_best[threadIdx.x] = 0;
         __syncwarp();
