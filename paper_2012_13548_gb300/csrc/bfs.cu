@@ -206,8 +206,9 @@ __device__ __forceinline__ void append_next(bool won, int32_t v, int64_t dv, con
 }
 
 // Warp-collective top-down visit of TD_E edges per lane (src[t] -> v[t] where
-// valid[t]): the visited-bit tests, the claiming atomics and the winners'
-// degree loads of the TD_E edges are each issued together.
+// valid[t]): the visited-bit tests of the TD_E edges are issued together, then
+// the claiming atomics together with the candidates' degree loads (a winner
+// needs its degree for the next frontier's counters).
 constexpr int TD_E = 4;
 __device__ __forceinline__ void td_visit(const bool (&valid)[TD_E], const int32_t (&src)[TD_E],
                                          const int32_t (&v)[TD_E], int l, const BfsArgs &a,
@@ -221,6 +222,10 @@ __device__ __forceinline__ void td_visit(const bool (&valid)[TD_E], const int32_
         cand[t] = valid[t] && GB_OK_IDX(a.st, v[t], a.n, 205) &&
                   !((ldcg_u32(&a.vis[(unsigned)v[t] >> 5]) >> (v[t] & 31)) & 1u);
     }
+    // the candidates' degrees are loaded with the claims, not after them
+    int64_t dv[TD_E];
+#pragma unroll
+    for (int t = 0; t < TD_E; ++t) dv[t] = cand[t] ? __ldg(&a.off[v[t] + 1]) - __ldg(&a.off[v[t]]) : 0;
 #pragma unroll
     for (int t = 0; t < TD_E; ++t) {
         won[t] = false;
@@ -229,15 +234,14 @@ __device__ __forceinline__ void td_visit(const bool (&valid)[TD_E], const int32_
             won[t] = !(atomicOr(&a.vis[(unsigned)v[t] >> 5], bit) & bit);
         }
     }
-    int64_t dv[TD_E];
 #pragma unroll
     for (int t = 0; t < TD_E; ++t) {
-        dv[t] = 0;
         if (won[t]) {
             a.parent[v[t]] = src[t];
             a.level[v[t]] = l + 1;
             atomicOr(&Fn[(unsigned)v[t] >> 5], 1u << (v[t] & 31));
-            dv[t] = a.off[v[t] + 1] - a.off[v[t]];
+        } else {
+            dv[t] = 0;
         }
     }
 #pragma unroll
