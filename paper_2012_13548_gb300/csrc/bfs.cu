@@ -387,6 +387,34 @@ __device__ __forceinline__ void bu_row_pass(const BfsArgs &a, const unsigned *F,
     append_next(won, u, d, a, wb, qn, bn, my_mf, nxt, qnext_base, bnext_base);
 }
 
+// Canonical mode: the vertices claimed top-down at the previous level (queue
+// entries [qbase, qbase + qn)) get as parent their smallest-id neighbour in
+// that level's frontier Fp, the first one in row order.  32 vertices per warp,
+// their rows streamed together, so that a long row (a hub claimed next to the
+// root) is scanned by the whole warp rather than by one thread.  Kept out of
+// line: the fast path does not carry its code.
+__device__ __noinline__ void canonical_rescan(const BfsArgs &a, const unsigned *Fp, int64_t qbase,
+                                              int64_t qn, int64_t gwarp, int64_t nwarps)
+{
+    const int lane = (int)lane_id();
+    unsigned long long examined = 0;
+    for (int64_t i0 = gwarp * 32; i0 < qn; i0 += nwarps * 32) {
+        const int64_t i = i0 + lane;
+        int32_t u = 0;
+        int64_t s = 0, e = 0;
+        if (i < qn && GB_OK_IDX(a.st, qbase + i, a.n, 226)) {
+            u = ldcg_i32(&a.queue[qbase + i]);
+            if (GB_OK_IDX(a.st, u, a.n, 227)) {
+                s = a.off[u];
+                e = a.off[u + 1];
+            }
+        }
+        int32_t found = -1;
+        bu_stream_rows(a, Fp, i < qn && e > s, s, e, found, examined);
+        if (i < qn && found >= 0) a.parent[u] = found;
+    }
+}
+
 // MINB = blocks of BFS_THREADS per SM the register budget is sized for:
 // 2 (64 registers, no spills) or 3 (40 registers, more warps to hide latency).
 template <int MINB>
@@ -483,19 +511,7 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
         }
 
         // Canonical parents of vertices claimed top-down at level l-1.
-        if (a.canonical && l > 0 && prev_td) {
-            for (int64_t i = gtid; i < qn; i += gthreads) {
-                const int32_t u = ldcg_i32(&a.queue[qbase + i]);
-                const int64_t e = a.off[u + 1];
-                for (int64_t j = a.off[u]; j < e; ++j) {
-                    const int32_t v = a.col[j];
-                    if ((ldcg_u32(&Fp[v >> 5]) >> (v & 31)) & 1u) {
-                        a.parent[u] = v;
-                        break;
-                    }
-                }
-            }
-        }
+        if (a.canonical && l > 0 && prev_td) canonical_rescan(a, Fp, qbase, qn, gwarp, nwarps);
 
         if (td) {
             // (a) chunks of big frontier vertices, a contiguous range per warp
