@@ -27,3 +27,24 @@ def test_table_lookup_takes_the_nearest_scale(tmp_path):
     assert AT.tuned_options("plain", 25, str(path)) == {"alpha": 2.0}
     assert AT.tuned_options("multigraph", None, str(path)) == {"ms_alpha": 4.0}
     assert AT.tuned_options("batched", 20, str(path)) == {}
+
+
+def test_table_lookup_strips_both_timing_fields(tmp_path):
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps({"plain/20": {"alpha": 32.0, "blocks_per_sm": 1, "mean_ms": 0.1},
+                                "batched/20": {"ms_alpha": 1.0, "median_ms": 1.9}}))
+    assert AT.tuned_options("plain", 20, str(path)) == {"alpha": 32.0, "blocks_per_sm": 1}
+    assert AT.tuned_options("batched", 22, str(path)) == {"ms_alpha": 1.0}
+
+
+def test_committed_table_holds_only_library_options():
+    # every entry of the shipped table must be accepted by bfs_set_options
+    names = {"canonical_parents", "alpha", "beta", "big_degree", "ms_alpha", "ms_beta",
+             "timeout_ms", "blocks_per_sm"}
+    table = AT.load_table()
+    assert table, "tune_table.json is missing"
+    for key, ent in table.items():
+        opts = AT.tuned_options(key.split("/")[0], int(key.split("/")[1]) if "/" in key else None)
+        assert set(opts) <= names, (key, opts)
+        if "blocks_per_sm" in opts:
+            assert opts["blocks_per_sm"] in (1, 2, 3)

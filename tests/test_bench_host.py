@@ -1,0 +1,51 @@
+"""Host logic of bench.py that decides what the JSON line reports (CPU only)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_traffic_summary_is_used_only_for_the_current_kernel_source(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "bfs_kernel_s20_traffic.txt").write_text(
+        "# a comment = ignored\nscale = 20\nbytes_per_launch = 1234\nsource_hash = %s\n" % h)
+    (prof / "bfs_kernel_s22_traffic.txt").write_text(
+        "scale = 22\nbytes_per_launch = 99\nsource_hash = 0000000000000000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    assert bench.read_traffic(20) == 1234
+    assert bench.read_traffic(22) is None   # measured on another kernel source
+    assert bench.read_traffic(24) is None   # no summary
+
+
+def test_committed_traffic_summaries_parse():
+    for scale in (20, 26):
+        path = os.path.join(ROOT, "profiles", "bfs_kernel_s%d_traffic.txt" % scale)
+        assert os.path.exists(path), path
+        kv = {}
+        for line in open(path):
+            if "=" in line and not line.lstrip().startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+        assert int(kv["scale"]) == scale
+        assert int(kv["bytes_per_launch"]) > 0
+        assert len(kv["source_hash"]) == 16
+
+
+def test_shard_roots_gives_disjoint_blocks():
+    roots = list(range(64))
+    parts = [bench.shard_roots(roots, r, 4, 16) for r in range(4)]
+    flat = [x for p in parts for x in p]
+    assert sorted(flat) == roots and all(len(p) == 16 for p in parts)
+
+
+def test_harmonic_mean():
+    assert bench.harmonic_mean([1.0, 1.0]) == pytest.approx(1.0)
+    assert bench.harmonic_mean([1.0, 3.0]) == pytest.approx(1.5)
