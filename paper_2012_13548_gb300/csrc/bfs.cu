@@ -12,10 +12,13 @@
 //    and appends the vertex to the next queue with one atomic per warp.
 //    Frontier vertices of degree <= big_degree are expanded 32 at a time by a
 //    warp that gathers their adjacency lists as one contiguous stream of
-//    edges; larger ones are cut into 256-edge chunks spread over all warps.
+//    edges; larger ones are cut into 128-edge chunks spread over all warps.
 //  bottom-up (Beamer, Asanovic, Patterson, SC 2012): every unvisited vertex
 //    scans its sorted adjacency list and stops at the first neighbour in the
-//    frontier bitmap, which is therefore the smallest-id parent.
+//    frontier bitmap, which is therefore the smallest-id parent.  Outside
+//    canonical mode it first tests its hub (a neighbour of largest degree,
+//    built with the graph): a hub in the frontier is a valid parent, found
+//    without reading the row.
 //
 // The switch follows Beamer: top-down -> bottom-up when the frontier's edges
 // exceed (edges of unvisited vertices) / alpha, back when the frontier is
