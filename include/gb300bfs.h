@@ -101,12 +101,15 @@ gb_status kron_generate(int scale, int edgefactor, double a, double b, double c,
  * kron_generate; read only, may be freed after the call returns) over
  * n = 2^scale vertices.  Row u holds, ascending, every v != u such that
  * (u,v) or (v,u) is a tuple: the graph is symmetrised, self-loops and
- * duplicate edges are dropped (Sec. 2.1 "may be ignored in the subsequent
- * kernels").  Offsets are int64 [n+1]: an empty row repeats the previous
+ * duplicate edges are dropped (Sec. 2.1 lets the kernels after generation
+ * disregard them).  Offsets are int64 [n+1]: an empty row repeats the previous
  * offset and off[n] = nnz (Sec. 2.2).  Columns are int32 [nnz].
  * Synchronises `s` (the column count is needed on the host).  Returns
  * GB_ERR_RANGE if an endpoint is outside [0, 2^scale).  *out receives a
- * library-owned graph; free it with graph_free. */
+ * library-owned graph; free it with graph_free.  Besides the CSR every graph
+ * holds two arrays the search reads: a degree >= 1 bitmap (n/8 bytes) and a
+ * hub per vertex (4 * n bytes: a neighbour of largest degree among the first
+ * 128 of its row, tested first by the bottom-up step). */
 gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph **out,
                           gb_stream s);
 

@@ -22,8 +22,8 @@
  *     SplitMix64 counter generator (Steele, Lea, Flood, OOPSLA 2014) are
  *     used, with integer thresholds so that every implementation decides each
  *     bit identically;
- *   - "randomly permuted" / "randomly shuffled" are read as sort-by-hash:
- *     ascending (SplitMix64(seed, id), id);
+ *   - the random vertex relabelling and the random tuple order of Sec. 2.1
+ *     are read as sort-by-hash: ascending (SplitMix64(seed, id), id);
  *   - Algorithm "Sequential BFS" marks a vertex visited only when it is
  *     dequeued, so a vertex can be enqueued twice and get a too-large level
  *     (triangle r-a-b from r gives level(b)=2).  The oracle marks on enqueue,
@@ -123,8 +123,8 @@ int gbo_hash_order(int64_t count, uint64_t seed, int64_t *order)
     return GBO_OK;
 }
 
-/* Vertex permutation (Sec. 2.1, "vertex numbers must be randomly permuted"):
- * pi[v] = rank of v in ascending (SM64(seed_perm, v), v). */
+/* Vertex permutation (Sec. 2.1: the generated vertex ids are relabelled at
+ * random): pi[v] = rank of v in ascending (SM64(seed_perm, v), v). */
 int gbo_vertex_perm(int scale, uint64_t seed_perm, int64_t *pi)
 {
     if (scale < 1 || scale > 30) return GBO_ERR_INVALID;

@@ -2,8 +2,9 @@
 //
 // One persistent cooperative kernel runs the whole search; levels are
 // separated by a software grid barrier (bounded waits), which is the level
-// synchronisation of Sec. 2.3.2 ("process an entire level in one step in
-// parallel", and the failure case without it).  Per level the kernel runs one
+// synchronisation of Sec. 2.3.2 (all vertices of a level are handled together
+// and the next level starts only once the whole level is done; the section
+// also shows the wrong levels a search gets without it).  Per level the kernel runs one
 // of two steps, chosen identically by every block from global counters:
 //
 //  top-down (Algorithm "Parallel BFS", Sec. 2.3.2): for every frontier vertex

@@ -2,10 +2,10 @@
 //
 //   1. symmetrise: tuple (u,v) becomes keys (u << S | v) and (v << S | u),
 //      S = scale, so one key holds an ordered pair in 2*S contiguous bits;
-//   2. radix sort of the keys (ceil(2S/8) passes) -- the "sorted array" the
-//      paper's CSR needs (Sec. 2.2, Sec. 4.2);
+//   2. radix sort of the keys (ceil(2S/8) passes): the CSR of Sec. 2.2 is
+//      built from the edges in sorted order (Sec. 4.2: by a parallel sort);
 //   3. a key is kept if it is not a self-loop (u == v) and differs from its
-//      predecessor (duplicates, Sec. 2.1 "may be ignored"); a count pass and a
+//      predecessor (a duplicate; Sec. 2.1 lets later kernels drop both); a count pass and a
 //      scan of the per-tile counts give each kept key its column slot;
 //   4. the write pass stores the columns and, at every change of row between
 //      neighbouring keys, the offsets of all rows in between: an empty row

@@ -1,7 +1,7 @@
 // LSD radix sort of uint64 keys (optionally carrying uint32 values) for the
 // Kronecker generator (vertex permutation, edge shuffle) and for kernel 1
-// (Sec. 2.2: "CSR format requires the sorted array"; Sec. 4.2 names a
-// parallel sort as the way to build the CSR).
+// (Sec. 2.2 builds the CSR from the edges in sorted order; Sec. 4.2 names a
+// parallel sort as the way to build it).
 //
 // Design (one-sweep, after Adinets & Merrill 2022): one read of the keys
 // counts the digits of every pass; then each 8-bit pass is a single kernel in
