@@ -343,7 +343,9 @@ def run_ours(args, dist):
         b.record(stream)
         b.synchronize()
         return a.elapsed_time(b), out
-    gen_ms, fused_ms = [], []
+    gen_ms, fused_ms, counting_ms = [], [], []
+    counting_same = True
+    off_g, col_g = g.csr()
     for _ in range(2):
         t, e2 = once(lambda: gb.kron_generate(**spec.kron_args()))
         gen_ms.append(t)
@@ -351,6 +353,14 @@ def run_ours(args, dist):
         t, g3 = once(lambda: gb.graph_generate_csr(**spec.kron_args()))
         fused_ms.append(t)
         g3.free()
+        # kernel 1 by counting sort on the same tuples: timed, and its CSR compared
+        t, g4 = once(lambda: gb.graph_build_csr_counting(edges, scale))
+        counting_ms.append(t)
+        off_c, col_c = g4.csr()
+        counting_same = counting_same and bool(torch.equal(off_c, off_g) and torch.equal(col_c, col_g))
+        del off_c, col_c
+        g4.free()
+    del off_g, col_g
     torch.cuda.empty_cache()
 
     # the batched search's rows (from the last timed step) validated too
@@ -410,7 +420,9 @@ def run_ours(args, dist):
                             "gbs": k1_bytes / (statistics.median(k1_ms) * 1e-3) / 1e9,
                             "alg_bytes": k1_bytes,
                             "generator_ms": min(gen_ms),
-                            "fused_generate_build_ms": min(fused_ms)},
+                            "fused_generate_build_ms": min(fused_ms),
+                            "counting_sort_ms": min(counting_ms),
+                            "counting_sort_same_csr": counting_same},
                 "validation": {"on": "device (bfs_validate, Graph500 rules 1-7)",
                                "trees": 2 * len(roots) * dist.world, "invalid_max_per_rank": n_invalid,
                                "first_failures": (invalid + batch_invalid)[:4]},

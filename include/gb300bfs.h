@@ -113,6 +113,19 @@ gb_status kron_generate(int scale, int edgefactor, double a, double b, double c,
 gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph **out,
                           gb_stream s);
 
+/* Kernel 1 by counting sort instead of a radix sort of the edges (Sec. 2.2
+ * builds the CSR from the edges in sorted order; here the rows are counted,
+ * the endpoints scattered into them, and each row sorted on its own): the
+ * same graph as graph_build_csr, bit for bit, for the same arguments.  Row
+ * counts, a scan to row starts, the scatter, per-row sorts by length (a warp
+ * up to 32 entries, a block up to 4096, one radix sort of (row, column) keys
+ * over the longer rows), the distinct counts scanned into the offsets, and
+ * the columns compacted.  Requires m < 2^31; GB_ERR_RANGE otherwise or for an
+ * endpoint outside [0, 2^scale).  Synchronises `s`; temporaries about
+ * 8 * m + 24 * n bytes plus 16 bytes per entry of the rows longer than 4096. */
+gb_status graph_build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_graph **out,
+                                   gb_stream s);
+
 /* Sec. 2.1 and Sec. 2.2 fused: the graph graph_build_csr builds from the
  * tuples of kron_generate(scale, edgefactor, a, b, c, seed_gen, seed_perm,
  * any seed_shuf), bit for bit, without the edge list: each generated tuple,

@@ -7,4 +7,4 @@ package only loads it (``binding``) and holds the seeded input recipes
 from .binding import (GbError, Graph, Server, bfs, bfs_batch, bfs_noalloc, bfs_get_options, bfs_last_stats,  # noqa: F401
                       bfs_validate,
                       bfs_multi_graph, bfs_set_options, gb_device_status, gb_kernel_launches, graph_build_csr,
-                      graph_from_csr, graph_generate_csr, kron_generate, lib)
+                      graph_build_csr_counting, graph_from_csr, graph_generate_csr, kron_generate, lib)

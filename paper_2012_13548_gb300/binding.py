@@ -75,6 +75,8 @@ def lib():
                                              ctypes.c_uint64, ctypes.c_uint64, _vp, _vp]),
             "graph_build_csr": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.POINTER(_vp), _vp]),
             "graph_from_csr": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.POINTER(_vp), _vp]),
+            "graph_build_csr_counting": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.POINTER(_vp),
+                                                        _vp]),
             "graph_generate_csr": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                   ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                                   ctypes.c_uint64, ctypes.POINTER(_vp), _vp]),
@@ -111,7 +113,8 @@ def lib():
 def exported_symbols():
     """Names of the C-ABI functions this binding wraps."""
     return ["gb_last_error", "gb_abi_version", "gb_kernel_launches", "gb_device_status", "kron_generate",
-            "graph_build_csr", "graph_from_csr", "graph_generate_csr", "graph_free", "graph_info", "graph_csr_view",
+            "graph_build_csr", "graph_build_csr_counting", "graph_from_csr", "graph_generate_csr",
+            "graph_free", "graph_info", "graph_csr_view",
             "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
             "bfs_last_stats", "bfs_noalloc", "bfs_validate", "server_create", "server_submit", "server_poll", "server_release",
             "server_run_trace", "server_destroy"]
@@ -214,6 +217,17 @@ def graph_build_csr(edges, scale, stream=None):
     h = _vp()
     _check(lib().graph_build_csr(_dev(edges, torch.int64, "edges"), edges.shape[1], scale,
                                  ctypes.byref(h), _stream(stream)))
+    return Graph(h.value)
+
+
+def graph_build_csr_counting(edges, scale, stream=None):
+    """Kernel 1 by counting sort (rows scattered, then each sorted): the same
+    Graph as graph_build_csr(edges, scale), for comparison."""
+    if edges.dim() != 2 or edges.shape[0] != 2:
+        raise ValueError("edges must have shape (2, m)")
+    h = _vp()
+    _check(lib().graph_build_csr_counting(_dev(edges, torch.int64, "edges"), edges.shape[1], scale,
+                                          ctypes.byref(h), _stream(stream)))
     return Graph(h.value)
 
 

@@ -224,6 +224,30 @@ gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *
     });
 }
 
+gb_status graph_build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_graph **out,
+                                   gb_stream s)
+{
+    return guarded([&]() {
+        if (!out || scale < 1 || scale > 30 || m < 0 || (m > 0 && !edges)) {
+            set_error("graph_build_csr_counting: need out != NULL, 1 <= scale <= 30, m >= 0");
+            return GB_ERR_INVALID;
+        }
+        *out = nullptr;
+        gb_graph *g = new gb_graph();
+        gb_status rc = build_csr_counting(edges, m, scale, g, as_stream(s));
+        if (rc != GB_OK) {
+            if (g->off) cudaFree(g->off);
+            if (g->col) cudaFree(g->col);
+            if (g->nz) cudaFree(g->nz);
+            if (g->hub) cudaFree(g->hub);
+            delete g;
+            return rc;
+        }
+        *out = g;
+        return GB_OK;
+    });
+}
+
 gb_status graph_generate_csr(int scale, int edgefactor, double a, double b, double c,
                              uint64_t seed_gen, uint64_t seed_perm, gb_graph **out, gb_stream s)
 {

@@ -412,4 +412,435 @@ gb_status kron_csr(int scale, int edgefactor, double a, double b, double c, uint
     return csr_from_keys(k0, k1, nk, scale, g, s);
 }
 
+// ---------------------------------------------------------------------------
+// Kernel 1, counting-sort variant (a comparison path for the radix build):
+//   1. entries per row, self-loops skipped and duplicates counted (atomics);
+//   2. an exclusive scan gives each row its start s0 in a scratch column array;
+//   3. every tuple's two endpoints are scattered into their rows;
+//   4. every row is sorted in place and its distinct entries counted: rows of
+//      at most 32 entries by one warp (a bitonic network over shuffles), rows of
+//      at most CS_BLOCK_MAX by one block (a bitonic network in shared memory),
+//      longer rows by one device radix sort of (row rank, column) keys;
+//   5. a scan of the distinct counts gives the offsets, and one warp per row
+//      copies the row's distinct entries to the columns.
+// The result is the same CSR as the radix build, bit for bit.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int CS_THREADS = 256;
+constexpr int CS_CHUNK = CS_THREADS * 16;   // elements per block of the scans
+constexpr int CS_BLOCK_MAX = 4096;          // longest row sorted in shared memory
+constexpr int SITE_CS = 14;
+
+__global__ void cs_count_kernel(const int64_t *__restrict__ edges, int64_t m, int64_t n,
+                                unsigned *__restrict__ deg0, DevStatus *st)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int64_t u = edges[e], v = edges[m + e];
+        if (u < 0 || u >= n || v < 0 || v >= n) {
+            record_error(st, GB_ERR_RANGE, SITE_K1_RANGE, (long long)e);
+            continue;
+        }
+        if (u == v) continue;
+        atomicAdd(&deg0[u], 1u);
+        atomicAdd(&deg0[v], 1u);
+    }
+}
+
+// Exclusive scan of cnt[0..n) into out[0..n] (out[n] = total), three steps:
+// chunk sums, a scan of the chunk sums, the chunks rescanned from their bases.
+__global__ void __launch_bounds__(CS_THREADS) cs_chunk_sum_kernel(const unsigned *__restrict__ cnt,
+                                                                  int64_t n, unsigned *__restrict__ sums)
+{
+    __shared__ unsigned long long s_w[CS_THREADS / 32];
+    const int64_t c0 = (int64_t)blockIdx.x * CS_CHUNK;
+    unsigned long long t = 0;
+    for (int j = 0; j < CS_CHUNK / CS_THREADS; ++j) {
+        const int64_t i = c0 + (int64_t)j * CS_THREADS + threadIdx.x;
+        if (i < n) t += cnt[i];
+    }
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < CS_THREADS / 32; ++w) b += s_w[w];
+        sums[blockIdx.x] = (unsigned)b;  // at most 2m < 2^32 entries in all
+    }
+}
+
+__global__ void __launch_bounds__(CS_THREADS) cs_chunk_write_kernel(
+    const unsigned *__restrict__ cnt, int64_t n, const unsigned long long *__restrict__ base,
+    int64_t nchunks, int64_t *__restrict__ out)
+{
+    __shared__ unsigned long long s_w[CS_THREADS / 32];
+    constexpr int PER = CS_CHUNK / CS_THREADS;  // 16 consecutive elements per thread
+    const int64_t i0 = (int64_t)blockIdx.x * CS_CHUNK + (int64_t)threadIdx.x * PER;
+    unsigned long long t = 0;
+    for (int j = 0; j < PER; ++j)
+        if (i0 + j < n) t += cnt[i0 + j];
+    const unsigned long long incl = warp_inclusive_scan(t);
+    if ((threadIdx.x & 31) == 31) s_w[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    unsigned long long run = base[blockIdx.x] + incl - t;
+    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) run += s_w[w];
+    for (int j = 0; j < PER; ++j) {
+        if (i0 + j < n) {
+            out[i0 + j] = (int64_t)run;
+            run += cnt[i0 + j];
+        }
+    }
+    if (blockIdx.x == nchunks - 1 && threadIdx.x == 0) out[n] = (int64_t)base[nchunks];
+}
+
+__global__ void cs_scatter_kernel(const int64_t *__restrict__ edges, int64_t m, int64_t n,
+                                  const int64_t *__restrict__ s0, unsigned *__restrict__ fill,
+                                  int32_t *__restrict__ tmp, DevStatus *st)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int64_t u = edges[e], v = edges[m + e];
+        if (u < 0 || u >= n || v < 0 || v >= n || u == v) continue;
+        const int64_t p = s0[u] + atomicAdd(&fill[u], 1u);
+        const int64_t q = s0[v] + atomicAdd(&fill[v], 1u);
+        if (p < s0[u + 1]) tmp[p] = (int32_t)v;
+        else record_error(st, GB_ERR_RANGE, SITE_CS, p);
+        if (q < s0[v + 1]) tmp[q] = (int32_t)u;
+        else record_error(st, GB_ERR_RANGE, SITE_CS, q);
+    }
+}
+
+// Rows by length: <= 1 (already sorted: its distinct count is its length),
+// <= 32, <= CS_BLOCK_MAX, longer; the last three appended to their lists.
+__global__ void cs_classify_kernel(const int64_t *__restrict__ s0, int64_t n,
+                                   unsigned *__restrict__ dcnt, int32_t *__restrict__ lists,
+                                   unsigned long long *__restrict__ counts)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x; x0 < n; x0 += stride) {
+        const int64_t x = x0 + threadIdx.x;
+        const int64_t len = x < n ? s0[x + 1] - s0[x] : 0;
+        int cls = -1;
+        if (x < n) {
+            if (len <= 1) dcnt[x] = (unsigned)len;
+            else cls = len <= 32 ? 0 : (len <= CS_BLOCK_MAX ? 1 : 2);
+        }
+        for (int c = 0; c < 3; ++c) {
+            const unsigned bm = __ballot_sync(kFull, cls == c);
+            if (!bm) continue;
+            unsigned long long b = 0;
+            if ((threadIdx.x & 31) == 0) b = atomicAdd(&counts[c], (unsigned long long)__popc(bm));
+            b = __shfl_sync(kFull, b, 0);
+            if (cls == c) lists[(int64_t)c * n + (int64_t)b + __popc(bm & lanemask_lt())] = (int32_t)x;
+        }
+    }
+}
+
+// Rows of 2..32 entries: one warp per row, a bitonic network over shuffles.
+__global__ void cs_sort_warp_kernel(const int32_t *__restrict__ rows, int64_t nrows,
+                                    const int64_t *__restrict__ s0, int32_t *__restrict__ tmp,
+                                    unsigned *__restrict__ dcnt)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = gwarp; r < nrows; r += nwarps) {
+        const int32_t x = rows[r];
+        const int64_t s = s0[x];
+        const int len = (int)(s0[x + 1] - s);
+        int32_t val = (int)lane < len ? tmp[s + lane] : 0x7fffffff;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int32_t other = __shfl_xor_sync(kFull, val, j);
+                const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+                val = (lower == up) ? min(val, other) : max(val, other);
+            }
+        }
+        const int32_t prev = __shfl_up_sync(kFull, val, 1);
+        const unsigned firsts = __ballot_sync(kFull, (int)lane < len && (lane == 0 || prev != val));
+        if ((int)lane < len) tmp[s + lane] = val;
+        if (lane == 0) dcnt[x] = __popc(firsts);
+    }
+}
+
+// Rows of 33..CS_BLOCK_MAX entries: one block per row, a bitonic network in
+// shared memory over the next power of two (padded with the largest int).
+__global__ void __launch_bounds__(CS_THREADS) cs_sort_block_kernel(
+    const int32_t *__restrict__ rows, int64_t nrows, const int64_t *__restrict__ s0,
+    int32_t *__restrict__ tmp, unsigned *__restrict__ dcnt)
+{
+    __shared__ int32_t buf[CS_BLOCK_MAX];
+    __shared__ unsigned s_w[CS_THREADS / 32];
+    for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int32_t x = rows[r];
+        const int64_t s = s0[x];
+        const int len = (int)(s0[x + 1] - s);
+        int p2 = 64;
+        while (p2 < len) p2 <<= 1;
+        for (int i = threadIdx.x; i < p2; i += CS_THREADS) buf[i] = i < len ? tmp[s + i] : 0x7fffffff;
+        __syncthreads();
+        for (int k = 2; k <= p2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < p2; i += CS_THREADS) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const int32_t a = buf[i], b = buf[ixj];
+                        if ((a > b) == ((i & k) == 0)) {
+                            buf[i] = b;
+                            buf[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        unsigned c = 0;
+        for (int i = threadIdx.x; i < len; i += CS_THREADS) {
+            tmp[s + i] = buf[i];
+            c += (i == 0 || buf[i] != buf[i - 1]);
+        }
+        c = warp_sum(c);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned t = 0;
+            for (int w = 0; w < CS_THREADS / 32; ++w) t += s_w[w];
+            dcnt[x] = t;
+        }
+        __syncthreads();  // buf and s_w are reused by the next row
+    }
+}
+
+// Long rows: the lengths of the listed rows (for their scan).
+__global__ void cs_long_len_kernel(const int32_t *__restrict__ rows, int64_t nrows,
+                                   const int64_t *__restrict__ s0, unsigned *__restrict__ len)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += stride) {
+        const int32_t x = rows[r];
+        len[r] = (unsigned)(s0[x + 1] - s0[x]);
+    }
+}
+
+// Long rows, before and after their sort: keys (rank << scale | column) are
+// gathered at the row's place g0[rank], and written back in sorted order with
+// the distinct count.  One block per row.
+__global__ void __launch_bounds__(CS_THREADS) cs_long_gather_kernel(
+    const int32_t *__restrict__ rows, int64_t nrows, const int64_t *__restrict__ s0,
+    const int64_t *__restrict__ g0, const int32_t *__restrict__ tmp, int scale,
+    uint64_t *__restrict__ keys)
+{
+    for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int32_t x = rows[r];
+        const int64_t s = s0[x], len = s0[x + 1] - s, g = g0[r];
+        for (int64_t i = threadIdx.x; i < len; i += CS_THREADS)
+            keys[g + i] = ((uint64_t)r << scale) | (uint64_t)(uint32_t)tmp[s + i];
+    }
+}
+
+__global__ void __launch_bounds__(CS_THREADS) cs_long_scatter_kernel(
+    const int32_t *__restrict__ rows, int64_t nrows, const int64_t *__restrict__ s0,
+    const int64_t *__restrict__ g0, const uint64_t *__restrict__ keys, int scale,
+    int32_t *__restrict__ tmp, unsigned *__restrict__ dcnt)
+{
+    __shared__ unsigned s_w[CS_THREADS / 32];
+    const uint64_t vmask = (uint64_t(1) << scale) - 1;
+    for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int32_t x = rows[r];
+        const int64_t s = s0[x], len = s0[x + 1] - s, g = g0[r];
+        unsigned c = 0;
+        for (int64_t i = threadIdx.x; i < len; i += CS_THREADS) {
+            const uint64_t k = keys[g + i];
+            tmp[s + i] = (int32_t)(k & vmask);
+            c += (i == 0 || keys[g + i - 1] != k);
+        }
+        c = warp_sum(c);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned t = 0;
+            for (int w = 0; w < CS_THREADS / 32; ++w) t += s_w[w];
+            dcnt[x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// Each row's distinct entries (its sorted scratch run without repeats) to the
+// columns at off[x]; one warp per row.
+__global__ void cs_compact_kernel(const int64_t *__restrict__ s0, const int64_t *__restrict__ off,
+                                  int64_t n, const int32_t *__restrict__ tmp,
+                                  int32_t *__restrict__ col, int64_t nnz, DevStatus *st)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = gwarp; x < n; x += nwarps) {
+        const int64_t s = s0[x], len = s0[x + 1] - s;
+        int64_t pos = off[x];
+        int32_t last = -1;  // the row's previous entry (columns are >= 0)
+        for (int64_t i0 = 0; i0 < len; i0 += 32) {
+            const int64_t i = i0 + lane;
+            const int32_t v = i < len ? tmp[s + i] : -1;
+            int32_t pv = __shfl_up_sync(kFull, v, 1);
+            if (lane == 0) pv = last;
+            const bool first = i < len && v != pv;
+            const unsigned fm = __ballot_sync(kFull, first);
+            if (first) {
+                const int64_t p = pos + __popc(fm & lanemask_lt());
+                if (p < nnz) col[p] = v;
+                else record_error(st, GB_ERR_RANGE, SITE_CS, p);
+            }
+            pos += __popc(fm);
+            last = __shfl_sync(kFull, v, 31);
+        }
+    }
+}
+
+// out[0..n] = exclusive scan of cnt[0..n); synchronises nothing.
+gb_status cs_scan(const unsigned *cnt, int64_t n, int64_t *out, cudaStream_t s)
+{
+    const int64_t nchunks = std::max<int64_t>(1, (n + CS_CHUNK - 1) / CS_CHUNK);
+    unsigned *sums = nullptr;
+    unsigned long long *base = nullptr;
+    GB_CUDA(alloc_async(&sums, (size_t)nchunks, s));
+    GB_CUDA(alloc_async(&base, (size_t)nchunks + 1, s));
+    cs_chunk_sum_kernel<<<(unsigned)nchunks, CS_THREADS, 0, s>>>(cnt, n, sums);
+    note_launch();
+    k1_scan_tiles_kernel<<<1, 1024, 0, s>>>(sums, nchunks, base);
+    note_launch();
+    cs_chunk_write_kernel<<<(unsigned)nchunks, CS_THREADS, 0, s>>>(cnt, n, base, nchunks, out);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
+    GB_CUDA(cudaFreeAsync(sums, s));
+    GB_CUDA(cudaFreeAsync(base, s));
+    return GB_OK;
+}
+
+}  // namespace
+
+gb_status build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_graph *g,
+                             cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    const int64_t n = int64_t(1) << scale;
+    g->n = n;
+    g->scale = scale;
+    g->device = ctx->device;
+    if (m >= (int64_t(1) << 31)) {  // 32-bit row counts hold at most 2m < 2^32 entries
+        set_error("graph_build_csr_counting: needs m < 2^31 tuples");
+        return GB_ERR_RANGE;
+    }
+    GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
+    if (m == 0) return empty_csr(g, s);
+    const int grid = ctx->num_sms * 8;
+    unsigned *cnt = nullptr, *dcnt = nullptr;
+    int64_t *s0 = nullptr;
+    GB_CUDA(alloc_async(&cnt, (size_t)n, s));
+    GB_CUDA(alloc_async(&dcnt, (size_t)n, s));
+    GB_CUDA(alloc_async(&s0, (size_t)n + 1, s));
+    // 1-2: entries per row, then the row starts
+    GB_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(unsigned), s));
+    cs_count_kernel<<<grid, 256, 0, s>>>(edges, m, n, cnt, ctx->status);
+    note_launch();
+    gb_status rc = cs_scan(cnt, n, s0, s);
+    if (rc != GB_OK) return rc;
+    int64_t nnz0 = 0;
+    DevStatus hst;
+    GB_CUDA(cudaMemcpyAsync(&nnz0, s0 + n, sizeof(nnz0), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&hst, ctx->status, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (hst.code != 0) {
+        GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
+        cudaFreeAsync(cnt, s);
+        cudaFreeAsync(dcnt, s);
+        cudaFreeAsync(s0, s);
+        cudaStreamSynchronize(s);
+        set_error(hst.code == GB_ERR_RANGE ? "graph_build_csr_counting: an edge endpoint is outside [0, 2^scale)"
+                                           : "graph_build_csr_counting: device error during the build");
+        return (gb_status)hst.code;
+    }
+    // 3: scatter into the rows (cnt reused as the fill counters)
+    int32_t *tmp = nullptr;
+    GB_CUDA(alloc_async(&tmp, (size_t)std::max<int64_t>(nnz0, 1), s));
+    GB_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(unsigned), s));
+    cs_scatter_kernel<<<grid, 256, 0, s>>>(edges, m, n, s0, cnt, tmp, ctx->status);
+    note_launch();
+    // 4: rows sorted by length class
+    int32_t *lists = nullptr;
+    unsigned long long *counts = nullptr;
+    GB_CUDA(alloc_async(&lists, 3 * (size_t)n, s));
+    GB_CUDA(alloc_async(&counts, 3, s));
+    GB_CUDA(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s));
+    cs_classify_kernel<<<grid, 256, 0, s>>>(s0, n, dcnt, lists, counts);
+    note_launch();
+    unsigned long long hc[3];
+    GB_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (hc[0]) {
+        cs_sort_warp_kernel<<<grid, 256, 0, s>>>(lists, (int64_t)hc[0], s0, tmp, dcnt);
+        note_launch();
+    }
+    if (hc[1]) {
+        cs_sort_block_kernel<<<(unsigned)std::min<unsigned long long>(hc[1], (unsigned long long)ctx->num_sms * 8),
+                               CS_THREADS, 0, s>>>(lists + n, (int64_t)hc[1], s0, tmp, dcnt);
+        note_launch();
+    }
+    if (hc[2]) {
+        const int64_t nl = (int64_t)hc[2];
+        const int32_t *lrows = lists + 2 * n;
+        unsigned *llen = nullptr;
+        int64_t *g0 = nullptr;
+        GB_CUDA(alloc_async(&llen, (size_t)nl, s));
+        GB_CUDA(alloc_async(&g0, (size_t)nl + 1, s));
+        cs_long_len_kernel<<<grid, 256, 0, s>>>(lrows, nl, s0, llen);
+        note_launch();
+        rc = cs_scan(llen, nl, g0, s);
+        if (rc != GB_OK) return rc;
+        int64_t tl = 0;
+        GB_CUDA(cudaMemcpyAsync(&tl, g0 + nl, sizeof(tl), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        int rbits = 1;
+        while ((int64_t(1) << rbits) < nl) ++rbits;
+        uint64_t *k0 = nullptr, *k1 = nullptr, *ks = nullptr;
+        GB_CUDA(alloc_async(&k0, (size_t)tl, s));
+        GB_CUDA(alloc_async(&k1, (size_t)tl, s));
+        const unsigned lb = (unsigned)std::min<int64_t>(nl, (int64_t)ctx->num_sms * 8);
+        cs_long_gather_kernel<<<lb, CS_THREADS, 0, s>>>(lrows, nl, s0, g0, tmp, scale, k0);
+        note_launch();
+        rc = radix_sort(k0, k1, nullptr, nullptr, tl, 0, scale + rbits, &ks, nullptr, s);
+        if (rc != GB_OK) return rc;
+        cs_long_scatter_kernel<<<lb, CS_THREADS, 0, s>>>(lrows, nl, s0, g0, ks, scale, tmp, dcnt);
+        note_launch();
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaFreeAsync(k0, s));
+        GB_CUDA(cudaFreeAsync(k1, s));
+        GB_CUDA(cudaFreeAsync(llen, s));
+        GB_CUDA(cudaFreeAsync(g0, s));
+    }
+    // 5: offsets from the distinct counts, then the columns
+    GB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(int64_t)));
+    rc = cs_scan(dcnt, n, g->off, s);
+    if (rc != GB_OK) return rc;
+    int64_t nnz = 0;
+    GB_CUDA(cudaMemcpyAsync(&nnz, g->off + n, sizeof(nnz), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    g->nnz = nnz;
+    GB_CUDA(cudaMalloc(&g->col, std::max<int64_t>(nnz, 4) * sizeof(int32_t)));
+    cs_compact_kernel<<<grid, 256, 0, s>>>(s0, g->off, n, tmp, g->col, nnz, ctx->status);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
+    GB_CUDA(cudaFreeAsync(cnt, s));
+    GB_CUDA(cudaFreeAsync(dcnt, s));
+    GB_CUDA(cudaFreeAsync(s0, s));
+    GB_CUDA(cudaFreeAsync(tmp, s));
+    GB_CUDA(cudaFreeAsync(lists, s));
+    GB_CUDA(cudaFreeAsync(counts, s));
+    return build_graph_aux(g, s);
+}
+
 }  // namespace gb

@@ -89,6 +89,8 @@ namespace gb {
 
 // Kernel 1 pieces (csr.cu).
 gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s);
+// Kernel 1 by counting sort (rows scattered, then sorted one by one), m < 2^31 (csr.cu).
+gb_status build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s);
 // Generator and kernel 1 fused: the CSR of the Kronecker graph with no edge list (csr.cu).
 gb_status kron_csr(int scale, int edgefactor, double a, double b, double c, uint64_t seed_gen,
                    uint64_t seed_perm, gb_graph *g, cudaStream_t s);

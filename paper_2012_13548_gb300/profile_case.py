@@ -3,6 +3,7 @@
   python -m paper_2012_13548_gb300.profile_case --kernel bfs --scale 22 --roots 3
   python -m paper_2012_13548_gb300.profile_case --kernel msbfs --scale 20 --roots 64
   python -m paper_2012_13548_gb300.profile_case --kernel k1 --scale 22
+  python -m paper_2012_13548_gb300.profile_case --kernel k1counting --scale 26
 
 It generates the Kronecker graph of the given SCALE on the device, builds the
 CSR and then runs the chosen kernel a few times, holding nothing else on the
@@ -18,7 +19,7 @@ from . import workloads as W
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--kernel", choices=["bfs", "msbfs", "k1"], default="bfs")
+    p.add_argument("--kernel", choices=["bfs", "msbfs", "k1", "k1counting"], default="bfs")
     p.add_argument("--scale", type=int, default=22)
     p.add_argument("--roots", type=int, default=3)
     p.add_argument("--canonical", type=int, default=0)
@@ -64,9 +65,10 @@ def main():
             gb.bfs_batch(g, roots, P, L)
             print(gb.bfs_last_stats())
     else:
-        del g
+        g.free()
+        build = gb.graph_build_csr if a.kernel == "k1" else gb.graph_build_csr_counting
         for _ in range(2):
-            g2 = gb.graph_build_csr(edges, a.scale)
+            g2 = build(edges, a.scale)
             g2.free()
     gb.gb_device_status()
     torch.cuda.synchronize()

@@ -145,6 +145,70 @@ def test_csr_rejects_out_of_range_endpoints():
         gb.graph_build_csr(e, 3)
 
 
+@pytest.mark.parametrize("scale", [1, 2, 5, 8, 12, 16, 20])
+def test_counting_sort_build_equals_the_oracle_csr(scale):
+    # kernel 1 by counting sort: the same CSR as the oracle's, bit for bit
+    e, _ = gpu_graph(scale)
+    G = gb.graph_build_csr_counting(e, scale)
+    _, off_ref, col_ref = oracle_graph(scale)
+    off, col = G.csr()
+    assert np.array_equal(np_(off), off_ref)
+    assert np.array_equal(np_(col), col_ref)
+    r = roots_for(scale, 1)[0]
+    _, level = gb.bfs(G, r)
+    assert np.array_equal(np_(level), oracle_bfs(scale, r)[1])
+    G.free()
+
+
+def test_counting_sort_build_row_classes_fixtures_and_errors():
+    for g in load_hand_graphs():
+        if "off" not in g:
+            continue
+        scale = max(1, (g["n"] - 1).bit_length())
+        G = gb.graph_build_csr_counting(torch.as_tensor(g["edges"]).cuda(), scale)
+        off, col = G.csr()
+        assert np.array_equal(np_(off)[: g["n"] + 1], g["off"]), g["name"]
+        assert np.array_equal(np_(col), g["col"]), g["name"]
+        G.free()
+    rng = np.random.default_rng(17)
+    # rows of every sort class: a hub of 8000 neighbours with repeats (the
+    # radix-sorted long rows), rows of 33..4096 (block sorts), short rows
+    scale = 13
+    n = 1 << scale
+    hub = np.stack([np.zeros(12000, dtype=np.int64), rng.integers(1, n, 12000)])
+    mid = np.stack([np.repeat(np.arange(1, 41), 200), rng.integers(0, n, 40 * 200)])
+    rnd = rng.integers(0, n, size=(2, 3 * n))
+    loops = np.stack([np.arange(50), np.arange(50)])
+    e = np.concatenate([hub, mid, rnd, loops, hub[:, :500]], axis=1).astype(np.int64)
+    e = e[:, rng.permutation(e.shape[1])].copy()
+    off_ref, col_ref = oracle.csr_build(e, scale)
+    assert np.diff(off_ref).max() > 4096
+    G = gb.graph_build_csr_counting(torch.as_tensor(e).cuda(), scale)
+    off, col = G.csr()
+    assert np.array_equal(np_(off), off_ref) and np.array_equal(np_(col), col_ref)
+    G.free()
+    for scale, m in [(1, 20000), (3, 4097)]:  # two rows of ~10^4 entries; rows of ~10^3
+        e = rng.integers(0, 1 << scale, size=(2, m)).astype(np.int64)
+        off_ref, col_ref = oracle.csr_build(e, scale)
+        G = gb.graph_build_csr_counting(torch.as_tensor(e).cuda(), scale)
+        off, col = G.csr()
+        assert np.array_equal(np_(off), off_ref) and np.array_equal(np_(col), col_ref), (scale, m)
+        G.free()
+    for scale in [1, 3, 8, 11]:
+        n = 1 << scale
+        for m in [0, 1, 7, 3 * n]:
+            e = rng.integers(0, n, size=(2, m)).astype(np.int64)
+            off_ref, col_ref = oracle.csr_build(e, scale)
+            G = gb.graph_build_csr_counting(torch.as_tensor(e).cuda(), scale)
+            off, col = G.csr()
+            assert np.array_equal(np_(off), off_ref), (scale, m)
+            assert np.array_equal(np_(col), col_ref), (scale, m)
+            G.free()
+    for bad in ([[0, 1, 2], [1, 2, 9]], [[0, -1], [1, 2]]):
+        with pytest.raises(gb.GbError, match="RANGE"):
+            gb.graph_build_csr_counting(torch.tensor(bad, dtype=torch.int64, device="cuda"), 3)
+
+
 # ---------------------------------------------------------------------------
 # Kernel 2 (Sec. 2.3): single-source BFS
 # ---------------------------------------------------------------------------
