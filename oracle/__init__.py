@@ -10,6 +10,8 @@ Every function follows the paper "Graph500 from OCaml-Multicore Perspective"
   csr_build                                             Sec. 2.2 (kernel 1, CSR)
   bfs                                                   Sec. 2.3.1 (kernel 2)
   validate, teps_edges                                  Sec. 2 outline step 5, Sec. 4.3
+  kron_weights, csr_build_weighted                      Sec. 2.1 weight row, Sec. 2.2
+  sssp, sssp_tree, sssp_validate                        Sec. 2.4 (kernel 3, Dijkstra)
 """
 import ctypes
 import numpy as np
@@ -20,6 +22,7 @@ _lib = None
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
+_f64p = ctypes.POINTER(ctypes.c_double)
 
 
 def lib():
@@ -53,6 +56,19 @@ def lib():
         L.gbo_teps_edges.argtypes = [_i64p, ctypes.c_int64, _i32p]
         L.gbo_component_edges.restype = ctypes.c_int64
         L.gbo_component_edges.argtypes = [_i64p, ctypes.c_int64, _i32p]
+        L.gbo_kron_weights.restype = ctypes.c_int
+        L.gbo_kron_weights.argtypes = [ctypes.c_int64, ctypes.c_uint64, _f64p]
+        L.gbo_csr_build_weighted.restype = ctypes.c_int
+        L.gbo_csr_build_weighted.argtypes = [_i64p, _f64p, ctypes.c_int64, ctypes.c_int, _i64p,
+                                             _i32p, _f64p, _i64p]
+        L.gbo_sssp.restype = ctypes.c_int64
+        L.gbo_sssp.argtypes = [_i64p, _i32p, _f64p, ctypes.c_int64, ctypes.c_int64, _f64p, _i32p]
+        L.gbo_sssp_tree.restype = ctypes.c_int
+        L.gbo_sssp_tree.argtypes = [_i64p, _i32p, _f64p, ctypes.c_int64, ctypes.c_int64, _f64p,
+                                    _i32p]
+        L.gbo_sssp_validate.restype = ctypes.c_int
+        L.gbo_sssp_validate.argtypes = [_i64p, _i32p, _f64p, ctypes.c_int64, ctypes.c_int64,
+                                        _i32p, _f64p]
         _lib = L
     return _lib
 
@@ -156,3 +172,71 @@ def component_edges(off, level):
     off = np.ascontiguousarray(off, dtype=np.int64)
     level = np.ascontiguousarray(level, dtype=np.int32)
     return int(lib().gbo_component_edges(_p(off, _i64p), off.size - 1, _p(level, _i32p)))
+
+
+def kron_weights(m, seed_w):
+    """The weight row: float64 [m], each a multiple of 2^-24 in (0, 1]."""
+    w = np.empty(max(m, 1), dtype=np.float64)
+    _check(lib().gbo_kron_weights(m, seed_w & (2**64 - 1), _p(w, _f64p)), "kron_weights")
+    return w[:m].copy()
+
+
+def csr_build_weighted(edges, w, scale):
+    """(off, col, wgt float64 [nnz]): csr_build's graph, each entry with the least
+    weight among the tuples joining its pair."""
+    edges = np.ascontiguousarray(edges, dtype=np.int64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    m = edges.shape[1]
+    if w.shape != (m,):
+        raise ValueError("one weight per tuple")
+    n = 1 << scale
+    off = np.empty(n + 1, dtype=np.int64)
+    col = np.empty(max(2 * m, 1), dtype=np.int32)
+    wgt = np.empty(max(2 * m, 1), dtype=np.float64)
+    nnz = ctypes.c_int64(0)
+    _check(lib().gbo_csr_build_weighted(_p(edges, _i64p), _p(w if m else np.zeros(1), _f64p), m,
+                                        scale, _p(off, _i64p), _p(col, _i32p), _p(wgt, _f64p),
+                                        ctypes.byref(nnz)), "csr_build_weighted")
+    return off, col[: nnz.value].copy(), wgt[: nnz.value].copy()
+
+
+def _csr_args(off, col, wgt):
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    wgt = np.ascontiguousarray(wgt, dtype=np.float64)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+        wgt = np.zeros(1, dtype=np.float64)
+    return off, col, wgt
+
+
+def sssp(off, col, wgt, root):
+    """(dist float64 [n], prev int32 [n]) of Algorithm "Sequential SSSP"."""
+    off, col, wgt = _csr_args(off, col, wgt)
+    n = off.size - 1
+    dist = np.empty(n, dtype=np.float64)
+    prev = np.empty(n, dtype=np.int32)
+    _check(lib().gbo_sssp(_p(off, _i64p), _p(col, _i32p), _p(wgt, _f64p), n, root,
+                          _p(dist, _f64p), _p(prev, _i32p)), "sssp")
+    return dist, prev
+
+
+def sssp_tree(off, col, wgt, root, dist):
+    """The canonical tree of `dist`: the smallest-id tight neighbour per vertex."""
+    off, col, wgt = _csr_args(off, col, wgt)
+    n = off.size - 1
+    dist = np.ascontiguousarray(dist, dtype=np.float64)
+    parent = np.empty(n, dtype=np.int32)
+    _check(lib().gbo_sssp_tree(_p(off, _i64p), _p(col, _i32p), _p(wgt, _f64p), n, root,
+                               _p(dist, _f64p), _p(parent, _i32p)), "sssp_tree")
+    return parent
+
+
+def sssp_validate(off, col, wgt, root, parent, dist):
+    """0 if (parent, dist) pass the SSSP rules, else the failed rule's number."""
+    off, col, wgt = _csr_args(off, col, wgt)
+    n = off.size - 1
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    dist = np.ascontiguousarray(dist, dtype=np.float64)
+    return int(lib().gbo_sssp_validate(_p(off, _i64p), _p(col, _i32p), _p(wgt, _f64p), n, root,
+                                       _p(parent, _i32p), _p(dist, _f64p)))

@@ -31,8 +31,23 @@
  *   - "for all index in E" on the per-vertex arrays is read as "in V";
  *   - the parent array is built from the level array: parent(v) is the
  *     smallest-id neighbour one level up (the canonical BFS tree);
- *   - the weight row of the 3 x #E matrix is not generated (BFS ignores it).
+ *   - the weight row of the 3 x #E matrix (kernel 3 only; BFS ignores it)
+ *     is drawn per output tuple j as (1 + (SM64(seed_w, j) >> 40)) * 2^-24:
+ *     uniform on the 2^24 multiples of 2^-24 in (0, 1].  Strictly positive
+ *     weights keep every tight-parent tree acyclic, and every path length is
+ *     then a multiple of 2^-24 below 2^29, which fp64 holds exactly: the
+ *     distances below are exact, with no rounding to agree on;
+ *   - kernel 1 keeps, for a pair joined by several tuples, the smallest of
+ *     their weights (a shortest path only ever uses the lightest copy);
+ *   - Algorithm "Sequential SSSP" takes the vertex of Q with the least
+ *     distance; among equal distances the oracle takes the smallest id, and
+ *     it stops once that least distance is infinite (the vertices left are
+ *     unreachable and no relaxation can change them);
+ *   - besides that algorithm's prev array, the canonical SSSP tree is
+ *     defined like the BFS one: parent(v) is the smallest-id neighbour u with
+ *     dist(u) + w(u,v) = dist(v).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -320,4 +335,200 @@ int64_t gbo_component_edges(const int64_t *off, int64_t n, const int32_t *level)
     for (int64_t v = 0; v < n; ++v)
         if (level[v] >= 0) s += off[v + 1] - off[v];
     return s / 2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.1: the weight row of the 3 x #E tuple matrix (see the readings at   */
+/* the top): w[j] = (1 + (SM64(seed_w, j) >> 40)) / 2^24 for output tuple j.  */
+/* ------------------------------------------------------------------------ */
+int gbo_kron_weights(int64_t m, uint64_t seed_w, double *w)
+{
+    if (m < 0) return GBO_ERR_INVALID;
+    for (int64_t j = 0; j < m; ++j)
+        w[j] = (double)(1u + (gbo_sm64(seed_w, (uint64_t)j) >> 40)) / 16777216.0;
+    return GBO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kernel 1 with the weight row (Sec. 2.2 CSR; the graph is weighted, Sec. 2): */
+/* off and col as gbo_csr_build; wgt[k] is the smallest weight among the      */
+/* tuples joining the pair of entry k, in either direction.                  */
+/* ------------------------------------------------------------------------ */
+typedef struct { int64_t u, v; double w; } gbo_wpair;
+
+static int gbo_cmp_wpair(const void *pa, const void *pb)
+{
+    const gbo_wpair *x = (const gbo_wpair *)pa, *y = (const gbo_wpair *)pb;
+    if (x->u != y->u) return x->u < y->u ? -1 : 1;
+    if (x->v != y->v) return x->v < y->v ? -1 : 1;
+    if (x->w != y->w) return x->w < y->w ? -1 : 1;
+    return 0;
+}
+
+int gbo_csr_build_weighted(const int64_t *edges, const double *w, int64_t m, int scale,
+                           int64_t *off, int32_t *col, double *wgt, int64_t *nnz)
+{
+    if (scale < 1 || scale > 30 || m < 0) return GBO_ERR_INVALID;
+    int64_t n = (int64_t)1 << scale;
+    gbo_wpair *p = (gbo_wpair *)malloc((size_t)(2 * m + 1) * sizeof(gbo_wpair));
+    if (!p) return GBO_ERR_NOMEM;
+    int64_t cnt = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t a = edges[e], b = edges[m + e];
+        if (a < 0 || a >= n || b < 0 || b >= n) { free(p); return GBO_ERR_RANGE; }
+        if (!(w[e] > 0.0 && w[e] <= 1.0)) { free(p); return GBO_ERR_RANGE; }
+        if (a == b) continue;
+        p[cnt].u = a; p[cnt].v = b; p[cnt].w = w[e]; ++cnt;
+        p[cnt].u = b; p[cnt].v = a; p[cnt].w = w[e]; ++cnt;
+    }
+    /* sorted by (u, v, w): the first entry of each (u, v) run has its least weight */
+    qsort(p, (size_t)cnt, sizeof(gbo_wpair), gbo_cmp_wpair);
+    for (int64_t i = 0; i <= n; ++i) off[i] = 0;
+    int64_t k = 0;
+    for (int64_t i = 0; i < cnt; ++i) {
+        if (i > 0 && p[i].u == p[i - 1].u && p[i].v == p[i - 1].v) continue;
+        col[k] = (int32_t)p[i].v;
+        wgt[k] = p[i].w;
+        ++k;
+        off[p[i].u + 1] += 1;
+    }
+    for (int64_t i = 0; i < n; ++i) off[i + 1] += off[i];
+    *nnz = k;
+    free(p);
+    return GBO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kernel 3 (Sec. 2.4, Algorithm "Sequential SSSP", Dijkstra): dist[v] = the  */
+/* least total weight of a path from root (INFINITY if none), prev[v] = the  */
+/* vertex whose relaxation last lowered dist[v] (-1 for the root and for      */
+/* unreached vertices, as the algorithm initialises it).  Q is kept in a      */
+/* binary heap of (dist, id) entries; an entry whose vertex has left Q or     */
+/* whose distance is out of date is skipped when it reaches the top, so the   */
+/* vertex taken is the one of least (dist, id) in Q.                          */
+/* Returns the number of vertices taken from Q (the reached ones).           */
+/* ------------------------------------------------------------------------ */
+typedef struct { double d; int64_t v; } gbo_hent;
+
+static int gbo_hless(const gbo_hent *x, const gbo_hent *y)
+{
+    return x->d < y->d || (x->d == y->d && x->v < y->v);
+}
+
+int64_t gbo_sssp(const int64_t *off, const int32_t *col, const double *wgt, int64_t n,
+                 int64_t root, double *dist, int32_t *prev)
+{
+    if (n < 1) return GBO_ERR_INVALID;
+    if (root < 0 || root >= n) return GBO_ERR_RANGE;
+    int64_t cap = off[n] + 2, hn = 0, taken = 0;
+    gbo_hent *h = (gbo_hent *)malloc((size_t)cap * sizeof(gbo_hent));
+    unsigned char *inq = (unsigned char *)malloc((size_t)n);
+    if (!h || !inq) { free(h); free(inq); return GBO_ERR_NOMEM; }
+    for (int64_t v = 0; v < n; ++v) { dist[v] = INFINITY; prev[v] = -1; inq[v] = 1; }
+    dist[root] = 0.0;
+    h[hn].d = 0.0; h[hn].v = root; ++hn;
+    while (hn > 0) {
+        gbo_hent top = h[0];
+        /* pop: move the last entry to the top and sift it down */
+        h[0] = h[--hn];
+        for (int64_t i = 0;;) {
+            int64_t l = 2 * i + 1, r = l + 1, b = i;
+            if (l < hn && gbo_hless(&h[l], &h[b])) b = l;
+            if (r < hn && gbo_hless(&h[r], &h[b])) b = r;
+            if (b == i) break;
+            gbo_hent t = h[i]; h[i] = h[b]; h[b] = t;
+            i = b;
+        }
+        int64_t u = top.v;
+        if (!inq[u] || top.d != dist[u]) continue;  /* left Q already, or out of date */
+        inq[u] = 0;
+        ++taken;
+        for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+            int64_t v = col[e];
+            if (!inq[v]) continue;                    /* v in Q and v in Adj[u] */
+            double alt = dist[u] + wgt[e];
+            if (alt < dist[v]) {
+                dist[v] = alt;
+                prev[v] = (int32_t)u;
+                if (hn == cap) {                      /* cannot happen: one push per lowering */
+                    free(h); free(inq);
+                    return GBO_ERR_NOMEM;
+                }
+                /* push (alt, v) and sift it up */
+                int64_t i = hn++;
+                h[i].d = alt; h[i].v = v;
+                while (i > 0) {
+                    int64_t pa = (i - 1) / 2;
+                    if (!gbo_hless(&h[i], &h[pa])) break;
+                    gbo_hent t = h[i]; h[i] = h[pa]; h[pa] = t;
+                    i = pa;
+                }
+            }
+        }
+    }
+    free(h);
+    free(inq);
+    return taken;
+}
+
+/* The canonical SSSP tree of a distance array: parent(root) = root,
+ * parent(v) = the smallest-id neighbour u with dist(u) + w(u,v) = dist(v),
+ * -1 for unreached v. */
+int gbo_sssp_tree(const int64_t *off, const int32_t *col, const double *wgt, int64_t n,
+                  int64_t root, const double *dist, int32_t *parent)
+{
+    if (n < 1) return GBO_ERR_INVALID;
+    if (root < 0 || root >= n) return GBO_ERR_RANGE;
+    for (int64_t v = 0; v < n; ++v) {
+        parent[v] = -1;
+        if (v == root) { parent[v] = (int32_t)root; continue; }
+        if (isinf(dist[v])) continue;
+        for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+            int64_t u = col[e];
+            if (dist[u] + wgt[e] == dist[v] && (parent[v] < 0 || u < parent[v]))
+                parent[v] = (int32_t)u;
+        }
+    }
+    return GBO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kernel 3 result validation (Graph500's SSSP rules, the benchmark the       */
+/* paper follows).  0 = valid, otherwise the first rule that failed:          */
+/*   1  parent(root) != root or dist(root) != 0                               */
+/*   2  parent(v) = -1 and dist(v) finite, or the reverse                     */
+/*   3  reached v != root whose parent is not a neighbour                      */
+/*   4  reached v != root with dist(v) != dist(parent) + w(parent, v)         */
+/*   5  a graph edge with exactly one reached endpoint                        */
+/*   6  a graph edge (u, v) with dist(v) > dist(u) + w(u, v)                   */
+/*   7  a parent out of range, or a distance negative or NaN                  */
+/* With positive weights rule 4 makes distances fall strictly along parent   */
+/* links, so the tree is acyclic and ends at the root; with rule 6 every      */
+/* distance is at most any path's length, so they are the shortest ones.     */
+/* ------------------------------------------------------------------------ */
+int gbo_sssp_validate(const int64_t *off, const int32_t *col, const double *wgt, int64_t n,
+                      int64_t root, const int32_t *parent, const double *dist)
+{
+    if (root < 0 || root >= n) return 7;
+    for (int64_t v = 0; v < n; ++v)
+        if (parent[v] < -1 || parent[v] >= n || isnan(dist[v]) || dist[v] < 0.0) return 7;
+    if (parent[root] != root || dist[root] != 0.0) return 1;
+    for (int64_t v = 0; v < n; ++v)
+        if ((parent[v] == -1) != (isinf(dist[v]) != 0)) return 2;
+    for (int64_t v = 0; v < n; ++v) {
+        if (v == root || parent[v] < 0) continue;
+        int64_t p = parent[v], found = -1;
+        for (int64_t e = off[v]; e < off[v + 1]; ++e)
+            if (col[e] == p) { found = e; break; }
+        if (found < 0) return 3;
+        if (dist[p] + wgt[found] != dist[v]) return 4;
+    }
+    for (int64_t u = 0; u < n; ++u) {
+        for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+            int64_t v = col[e];
+            if (isinf(dist[u]) != isinf(dist[v])) return 5;
+            if (!isinf(dist[u]) && dist[v] > dist[u] + wgt[e]) return 6;
+        }
+    }
+    return 0;
 }

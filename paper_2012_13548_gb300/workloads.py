@@ -24,6 +24,7 @@ EDGEFACTOR = 16
 A, B, C = 0.57, 0.19, 0.19          # D = 1 - A - B - C = 0.05
 
 SEED_GEN, SEED_PERM, SEED_SHUF, SEED_ROOT, SEED_ARRIVAL = 1, 2, 3, 4, 5
+SEED_WEIGHT = 6
 
 _MASK64 = (1 << 64) - 1
 
@@ -49,6 +50,13 @@ class GraphSpec:
         if self.index >= 0:
             salt ^= (self.index + 1) << 40
         return tuple((s ^ salt) & _MASK64 for s in (SEED_GEN, SEED_PERM, SEED_SHUF, SEED_ROOT))
+
+    def seed_weight(self):
+        """Seed of the weight row (kernel 3), salted like seeds()."""
+        salt = (self.scale << 32)
+        if self.index >= 0:
+            salt ^= (self.index + 1) << 40
+        return (SEED_WEIGHT ^ salt) & _MASK64
 
     def kron_args(self):
         """Arguments of kron_generate after (scale, edgefactor, a, b, c)."""

@@ -357,3 +357,206 @@ def test_teps_counts_component_tuples():
     # the deduplicated count is half the CSR entries of reached rows
     assert oracle.component_edges(off, lev) * 2 == int(np.diff(off)[lev >= 0].sum())
     assert 0 < oracle.component_edges(off, lev) <= m_r
+
+
+# --------------------------------------------------------------------------
+# Kernel 3 (Sec. 2.4): the weight row, the weighted CSR, Dijkstra
+# --------------------------------------------------------------------------
+
+def test_weight_row_grid_range_and_uniformity():
+    m = 200_000
+    w = oracle.kron_weights(m, 12345)
+    k = w * 2.0**24
+    assert np.all(k == np.round(k)) and k.min() >= 1 and k.max() <= 2**24
+    assert abs(w.mean() - 0.5) < 0.005
+    counts = np.histogram(w, bins=16, range=(0.0, 1.0))[0]
+    assert np.all(np.abs(counts - m / 16) < 0.05 * m / 16)
+    assert not np.array_equal(w[:1000], oracle.kron_weights(1000, 12346))
+    # the first weight of seed 0 from the published first SplitMix64 output
+    # 0xE220A8397B1DCDAF: its top 24 bits, plus one, in units of 2^-24
+    assert oracle.kron_weights(1, 0)[0] == (1 + 0xE220A8) / 2.0**24
+
+
+def test_weighted_csr_keeps_the_least_weight_of_each_pair():
+    rng = np.random.default_rng(5)
+    for scale in [1, 2, 4, 6]:
+        n = 1 << scale
+        for m in [0, 1, 9, 5 * n]:
+            e = rng.integers(0, n, size=(2, m)).astype(np.int64)
+            w = rng.integers(1, 9, size=m) / 8.0
+            off, col, wgt = oracle.csr_build_weighted(e, w, scale)
+            off0, col0 = oracle.csr_build(e, scale)
+            assert np.array_equal(off, off0) and np.array_equal(col, col0)
+            best = {}
+            for (a, b), x in zip(e.T.tolist(), w.tolist()):
+                if a != b:
+                    for key in ((a, b), (b, a)):
+                        best[key] = min(best.get(key, 2.0), x)
+            got = {(u, int(col[j])): float(wgt[j])
+                   for u in range(n) for j in range(off[u], off[u + 1])}
+            assert got == best
+
+
+def test_weighted_csr_rejects_bad_weights_and_endpoints():
+    e = np.array([[0, 1], [1, 2]], dtype=np.int64)
+    for bad in ([0.5, 0.0], [0.5, 1.5], [0.5, float("nan")], [-0.25, 0.5]):
+        with pytest.raises(RuntimeError):
+            oracle.csr_build_weighted(e, np.array(bad), 2)
+    with pytest.raises(RuntimeError):
+        oracle.csr_build_weighted(np.array([[0], [4]]), np.array([0.5]), 2)
+
+
+def test_sssp_hand_worked_diamond_with_a_tie():
+    # 0-1 (1/2), 0-2 (1/4), 1-3 (1/4), 2-3 (1/2), 3-4 (1/8); 5 isolated.
+    # Algorithm "Sequential SSSP": take 0 (dist 1 = 1/2, dist 2 = 1/4), take 2
+    # (dist 3 = 3/4 by 2), take 1 (1/2 + 1/4 is not < 3/4: prev 3 stays 2),
+    # take 3 (dist 4 = 7/8).  Both 1 and 2 are tight for 3: the canonical
+    # tree takes 1.
+    e = np.array([[0, 0, 1, 2, 3], [1, 2, 3, 3, 4]], dtype=np.int64)
+    w = np.array([0.5, 0.25, 0.25, 0.5, 0.125])
+    off, col, wgt = oracle.csr_build_weighted(e, w, 3)
+    dist, prev = oracle.sssp(off, col, wgt, 0)
+    inf = float("inf")
+    assert dist.tolist() == [0.0, 0.5, 0.25, 0.75, 0.875, inf, inf, inf]
+    assert prev.tolist() == [-1, 0, 0, 2, 3, -1, -1, -1]
+    tree = oracle.sssp_tree(off, col, wgt, 0, dist)
+    assert tree.tolist() == [0, 0, 0, 1, 3, -1, -1, -1]
+    assert oracle.sssp_validate(off, col, wgt, 0, tree, dist) == 0
+
+
+def test_sssp_path_closed_form():
+    rng = np.random.default_rng(8)
+    k = 200
+    w = rng.integers(1, 2**24 + 1, size=k - 1) / 2.0**24
+    e = np.stack([np.arange(k - 1), np.arange(1, k)]).astype(np.int64)
+    off, col, wgt = oracle.csr_build_weighted(e, w, 8)
+    dist, prev = oracle.sssp(off, col, wgt, 0)
+    expect = np.concatenate([[0.0], np.cumsum(w)])
+    assert np.array_equal(dist[:k], expect)          # exact: multiples of 2^-24
+    assert np.all(np.isinf(dist[k:]))
+    assert prev[1:k].tolist() == list(range(k - 1))
+    # from the far end the distances are the suffix sums
+    d2, _ = oracle.sssp(off, col, wgt, k - 1)
+    assert np.array_equal(d2[:k], expect[-1] - expect)
+
+
+def test_sssp_unit_weights_are_bfs_levels():
+    spec = W.GraphSpec(scale=9)
+    e = oracle.kron_generate(**spec.kron_args())
+    w = np.ones(e.shape[1])
+    off, col, wgt = oracle.csr_build_weighted(e, w, 9)
+    for root in [int(np.argmax(np.diff(off))), 3, 100]:
+        parent_b, level = oracle.bfs(off, col, root)
+        dist, _ = oracle.sssp(off, col, wgt, root)
+        reached = level >= 0
+        assert np.array_equal(dist[reached], level[reached].astype(np.float64))
+        assert np.all(np.isinf(dist[~reached]))
+        assert np.array_equal(oracle.sssp_tree(off, col, wgt, root, dist), parent_b)
+
+
+def _brute_force_distances(n, edges, w, root):
+    adj = {}
+    for (a, b), x in zip(edges.T.tolist(), w.tolist()):
+        if a != b:
+            adj.setdefault(a, []).append((b, x))
+            adj.setdefault(b, []).append((a, x))
+    best = [math.inf] * n
+    best[root] = 0.0
+
+    def walk(u, d, seen):
+        for v, x in adj.get(u, []):
+            if v not in seen:
+                best[v] = min(best[v], d + x)
+                walk(v, d + x, seen | {v})
+
+    walk(root, 0.0, {root})
+    return np.array(best)
+
+
+def test_sssp_matches_all_simple_paths_on_tiny_graphs():
+    rng = np.random.default_rng(21)
+    for _ in range(60):
+        n = int(rng.integers(2, 8))
+        m = int(rng.integers(0, 14))
+        e = rng.integers(0, n, size=(2, m)).astype(np.int64)
+        w = rng.integers(1, 2**24 + 1, size=m) / 2.0**24
+        off, col, wgt = oracle.csr_build_weighted(e, w, 3)
+        root = int(rng.integers(0, n))
+        dist, prev = oracle.sssp(off, col, wgt, root)
+        assert np.array_equal(dist[:n], _brute_force_distances(n, e, w, root))
+        assert np.all(np.isinf(dist[n:]))
+        p = prev.copy()
+        p[root] = root
+        assert oracle.sssp_validate(off, col, wgt, root, p, dist) == 0
+        assert oracle.sssp_validate(off, col, wgt, root,
+                                    oracle.sssp_tree(off, col, wgt, root, dist), dist) == 0
+
+
+def test_sssp_matches_scipy_dijkstra():
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    sparse = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(34)
+    for n, m in [(300, 900), (500, 600), (256, 4000)]:
+        e = rng.integers(0, n, size=(2, m)).astype(np.int64)
+        w = rng.integers(1, 2**24 + 1, size=m) / 2.0**24
+        dense = np.full((n, n), np.inf)
+        keep = e[0] != e[1]
+        np.minimum.at(dense, (e[0][keep], e[1][keep]), w[keep])
+        np.minimum.at(dense, (e[1][keep], e[0][keep]), w[keep])
+        dense[np.isinf(dense)] = 0.0                    # no edge
+        ref = csgraph.dijkstra(sparse.csr_matrix(dense), directed=True, indices=[0, 7])
+        scale = max(1, (n - 1).bit_length())
+        off, col, wgt = oracle.csr_build_weighted(e, w, scale)
+        for i, root in enumerate([0, 7]):
+            dist, _ = oracle.sssp(off, col, wgt, root)
+            assert np.array_equal(dist[:n], ref[i])
+
+
+def test_sssp_validator_rejects_planted_mistakes():
+    spec = W.GraphSpec(scale=9)
+    e = oracle.kron_generate(**spec.kron_args())
+    w = oracle.kron_weights(e.shape[1], 77)
+    off, col, wgt = oracle.csr_build_weighted(e, w, 9)
+    root = int(np.argmax(np.diff(off)))
+    dist, _ = oracle.sssp(off, col, wgt, root)
+    tree = oracle.sssp_tree(off, col, wgt, root, dist)
+    assert oracle.sssp_validate(off, col, wgt, root, tree, dist) == 0
+    reached = np.flatnonzero(np.isfinite(dist))
+    isolated = np.flatnonzero(np.diff(off) == 0)
+    children = np.bincount(tree[tree >= 0], minlength=tree.size)
+    # a leaf of the tree with a neighbour that is not tight for it
+    v = next(int(x) for x in reached if x != root and children[x] == 0 and any(
+        dist[col[j]] + wgt[j] > dist[x] for j in range(off[x], off[x + 1])))
+
+    def check(rule, p=None, d=None):
+        assert oracle.sssp_validate(off, col, wgt, root, tree if p is None else p,
+                                    dist if d is None else d) == rule
+
+    d = dist.copy(); d[root] = 2.0**-24; check(1, d=d)
+    p = tree.copy(); p[root] = tree[v]; check(1, p=p)
+    p = tree.copy(); p[v] = -1; check(2, p=p)
+    non_nb = next(u for u in reached if u != v and u not in col[off[v]:off[v + 1]])
+    p = tree.copy(); p[v] = non_nb; check(3, p=p)
+    d = dist.copy(); d[v] += 2.0**-24; check(4, d=d)
+    # v hung from a longer path: its tree edge is consistent, an edge is not
+    j = next(j for j in range(off[v], off[v + 1]) if dist[col[j]] + wgt[j] > dist[v])
+    p = tree.copy(); p[v] = col[j]
+    d = dist.copy(); d[v] = dist[col[j]] + wgt[j]
+    check(6, p=p, d=d)
+    # an isolated vertex claimed as reached from a reached one
+    x = int(isolated[0])
+    p = tree.copy(); p[x] = root
+    d = dist.copy(); d[x] = 1.0
+    check(3, p=p, d=d)
+    d = dist.copy(); d[v] = -1.0; check(7, d=d)
+    p = tree.copy(); p[v] = tree.size; check(7, p=p)
+
+
+def test_sssp_rejects_bad_root():
+    off = np.array([0, 1, 2], dtype=np.int64)
+    col = np.array([1, 0], dtype=np.int32)
+    wgt = np.array([0.5, 0.5])
+    with pytest.raises(RuntimeError):
+        oracle.sssp(off, col, wgt, 2)
+    with pytest.raises(RuntimeError):
+        oracle.sssp(off, col, wgt, -1)
