@@ -1,11 +1,12 @@
 /*
- * gb300bfs.h -- C ABI of the GB300 Graph500 library (kernel 1 + kernel 2).
+ * gb300bfs.h -- C ABI of the GB300 Graph500 library (kernels 1, 2 and 3).
  *
  * The library implements the data-parallel part of the Graph500 pipeline that
  * arXiv 2012.13548 ("Graph500 from OCaml-Multicore Perspective") builds on a
  * CPU: Sec. 2.1 (Kronecker edge list), Sec. 2.2 (kernel 1: graph construction
  * as CSR) and Sec. 2.3 (kernel 2: level-synchronous BFS producing a parent and
- * a level array), plus a batched multi-source BFS and a serving loop.
+ * a level array), plus a batched multi-source BFS, a serving loop and Sec. 2.4
+ * (kernel 3: single-source shortest paths with parent and distance arrays).
  *
  * Conventions shared by every entry point:
  *   - Every function returns a gb_status; no C++ exception crosses the ABI.
@@ -316,6 +317,103 @@ typedef struct gb_validation {
 gb_status bfs_validate(const gb_graph *g, int64_t root, const int32_t *parent,
                        const int32_t *level, const int64_t *edges, int64_t m,
                        gb_validation *out, gb_stream s);
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.4: kernel 3, single-source shortest paths on the weighted graph.   */
+/* ------------------------------------------------------------------------ */
+
+/* The weight row of the 3 x #E tuple matrix (Sec. 2.1): w[j] (device float
+ * [m], caller-allocated) = (1 + the top 24 bits of SplitMix64(seed_weight, j))
+ * * 2^-24, a multiple of 2^-24 in (0, 1], exact in float.  Weight j belongs
+ * to tuple j of the edge list it is used with. */
+gb_status kron_weights(int64_t m, uint64_t seed_weight, float *w, gb_stream s);
+
+/* Kernel 1 with weights: the graph graph_build_csr builds from `edges`, and
+ * for every CSR entry the least weight among the tuples joining its pair (in
+ * either direction; a shortest path uses the lightest copy of an edge).
+ * w: device float [m], each in (0, 1]; stored as integer units of 2^-24
+ * (rounded to the nearest unit, at least one), so that every path length is
+ * an exact sum.  GB_ERR_RANGE for an endpoint outside [0, 2^scale) or a
+ * weight outside (0, 1] (NaN included).  Synchronises `s`; the graph also
+ * holds 4 * nnz bytes of weights. */
+gb_status graph_build_csr_weighted(const int64_t *edges, const float *w, int64_t m, int scale,
+                                   gb_graph **out, gb_stream s);
+
+/* Borrowed device pointer to the weights of a weighted graph (uint32 [nnz],
+ * units of 2^-24, parallel to the columns); GB_ERR_INVALID if g has none. */
+gb_status graph_weights_view(const gb_graph *g, const uint32_t **wgt);
+
+/* Single-source shortest paths from `root` (Sec. 2.4, Algorithm "Sequential
+ * SSSP" computes the same distances; Sec. 4.1 names delta-stepping, which
+ * this runs in its near/far form on the device).  g must be built by
+ * graph_build_csr_weighted.  delta: bucket width in weight units of 1.0
+ * (e.g. 0.0625), <= 0 for the default.  Outputs, caller-allocated device
+ * arrays: dist float64 [n] (exact: the least path weight, a multiple of
+ * 2^-24; +infinity if unreachable) and parent int32 [n] (parent(root) = root;
+ * for a reached v the smallest-id neighbour u with dist(u) + w(u,v) =
+ * dist(v); -1 if unreachable).  The distances are those of Dijkstra's
+ * algorithm exactly; the parent array is the unique canonical tree of them.
+ * Allocates about 32 * n bytes of stream-ordered scratch.  GB_ERR_RANGE for
+ * a root outside [0, n); GB_ERR_INVALID for an unweighted graph. */
+gb_status sssp(const gb_graph *g, int64_t root, double delta, double *dist, int32_t *parent,
+               gb_stream s);
+
+/* Statistics of this thread's last sssp call (synchronises its stream).
+ *   rounds      expansion rounds (near queues) run
+ *   buckets     buckets settled
+ *   processed   near-queue entries expanded (a vertex may be expanded
+ *               again when its distance drops within its bucket)
+ *   scanned     edges of the expanded rows
+ *   won         relaxations that lowered a distance
+ *   reached     vertices with a finite distance
+ *   delta       bucket width used, in weight units of 1.0 */
+typedef struct gb_sssp_stats {
+    int64_t rounds;
+    int64_t buckets;
+    int64_t processed;
+    int64_t scanned;
+    int64_t won;
+    int64_t reached;
+    double delta;
+} gb_sssp_stats;
+
+gb_status sssp_last_stats(gb_sssp_stats *out);
+
+/* Verdict of sssp_validate (the SSSP result rules of the Graph500 benchmark).
+ *   code  0 if (parent, dist) is a shortest-path tree of g from root, else
+ *         the first failing rule, in the order a serial check meets them
+ *         (rule 7 over the vertices, rule 1, rule 2 over the vertices, rules
+ *         3-4 over the vertices, rules 5-6 over the CSR entries):
+ *           1  parent(root) != root or dist(root) != 0
+ *           2  parent(v) = -1 while dist(v) is finite, or the reverse
+ *           3  a reached v != root whose parent is not a neighbour
+ *           4  a reached v != root with dist(v) != dist(parent) + w(parent, v)
+ *           5  a graph edge with exactly one reached endpoint
+ *           6  a graph edge (u, v) with dist(v) > dist(u) + w(u, v)
+ *           7  root outside [0, n), a parent outside [-1, n), or a distance
+ *              that is negative or NaN
+ *   where            the vertex (1-4, 7) or CSR entry (5, 6) of the failure
+ *   reached          vertices with a finite distance
+ *   component_edges  undirected simple edges among them
+ *   teps_edges       input tuples whose start vertex is reached (-1 if no
+ *                    tuples were given)
+ *   max_dist         the largest finite distance */
+typedef struct gb_sssp_validation {
+    int32_t code;
+    int32_t pad;
+    int64_t where;
+    int64_t reached;
+    int64_t component_edges;
+    int64_t teps_edges;
+    double max_dist;
+} gb_sssp_validation;
+
+/* Check (parent, dist) (device arrays as written by sssp) against the
+ * weighted graph g on the device; count the TEPS numerator over edges
+ * (device int64 [2][m]; NULL with m = 0 to skip).  Synchronises s; returns
+ * GB_OK whenever the check ran, whatever its verdict. */
+gb_status sssp_validate(const gb_graph *g, int64_t root, const int32_t *parent, const double *dist,
+                        const int64_t *edges, int64_t m, gb_sssp_validation *out, gb_stream s);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: resident graphs, BFS queries admitted as they arrive.            */

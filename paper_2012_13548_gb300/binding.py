@@ -51,6 +51,18 @@ class gb_validation(ctypes.Structure):
                 ("teps_edges", ctypes.c_int64)]
 
 
+class gb_sssp_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in
+                ("rounds", "buckets", "processed", "scanned", "won", "reached")] + \
+        [("delta", ctypes.c_double)]
+
+
+class gb_sssp_validation(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int32), ("pad", ctypes.c_int32), ("where", ctypes.c_int64),
+                ("reached", ctypes.c_int64), ("component_edges", ctypes.c_int64),
+                ("teps_edges", ctypes.c_int64), ("max_dist", ctypes.c_double)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -94,6 +106,14 @@ def lib():
             "bfs_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp]),
             "bfs_validate": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp, _i64,
                                             ctypes.POINTER(gb_validation), _vp]),
+            "kron_weights": (ctypes.c_int, [_i64, ctypes.c_uint64, _vp, _vp]),
+            "graph_build_csr_weighted": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int,
+                                                        ctypes.POINTER(_vp), _vp]),
+            "graph_weights_view": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+            "sssp": (ctypes.c_int, [_vp, _i64, ctypes.c_double, _vp, _vp, _vp]),
+            "sssp_last_stats": (ctypes.c_int, [ctypes.POINTER(gb_sssp_stats)]),
+            "sssp_validate": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp, _i64,
+                                             ctypes.POINTER(gb_sssp_validation), _vp]),
             "server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t,
                                              ctypes.POINTER(_vp)]),
             "server_submit": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.POINTER(_i64)]),
@@ -116,8 +136,9 @@ def exported_symbols():
             "graph_build_csr", "graph_build_csr_counting", "graph_from_csr", "graph_generate_csr",
             "graph_free", "graph_info", "graph_csr_view",
             "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
-            "bfs_last_stats", "bfs_noalloc", "bfs_validate", "server_create", "server_submit", "server_poll", "server_release",
-            "server_run_trace", "server_destroy"]
+            "bfs_last_stats", "bfs_noalloc", "bfs_validate", "kron_weights", "graph_build_csr_weighted",
+            "graph_weights_view", "sssp", "sssp_last_stats", "sssp_validate", "server_create",
+            "server_submit", "server_poll", "server_release", "server_run_trace", "server_destroy"]
 
 
 def _check(rc):
@@ -172,6 +193,15 @@ class Graph:
         o = torch.as_tensor(_DevArray(off.value, (self.n + 1,), "<i8", self), device="cuda:%d" % dev)
         c = torch.as_tensor(_DevArray(col.value, (self.nnz,), "<i4", self), device="cuda:%d" % dev)
         return o, c
+
+    def weights(self):
+        """Borrowed uint32 [nnz] weights of a weighted graph, in units of 2^-24
+        (torch has no uint32 arithmetic on every version: returned as int32
+        bits, all values below 2^31)."""
+        w = _vp()
+        _check(lib().graph_weights_view(self.handle, ctypes.byref(w)))
+        dev = torch.cuda.current_device()
+        return torch.as_tensor(_DevArray(w.value, (self.nnz,), "<i4", self), device="cuda:%d" % dev)
 
     def free(self):
         if self._h:
@@ -439,3 +469,72 @@ class Server:
         except Exception:
             pass
 
+
+
+def kron_weights(m, seed_weight, w=None, stream=None):
+    """The weight row of the tuple matrix (Sec. 2.1): float32 [m] CUDA tensor,
+    multiples of 2^-24 in (0, 1]."""
+    if w is None:
+        w = torch.empty(max(int(m), 1), dtype=torch.float32, device="cuda")[: int(m)]
+    if w.numel() != m:
+        raise ValueError("w must have m = %d entries" % m)
+    _check(lib().kron_weights(int(m), int(seed_weight) & (2**64 - 1),
+                              _dev(w, torch.float32, "w") if m else ctypes.c_void_p(None),
+                              _stream(stream)))
+    return w
+
+
+def graph_build_csr_weighted(edges, w, scale, stream=None):
+    """Kernel 1 with weights: graph_build_csr's graph, each entry with the least
+    weight (float32 [m], each in (0, 1]) among the tuples joining its pair."""
+    if edges.dim() != 2 or edges.shape[0] != 2:
+        raise ValueError("edges must have shape (2, m)")
+    m = int(edges.shape[1])
+    if w.numel() != m:
+        raise ValueError("w must have one weight per tuple")
+    h = _vp()
+    _check(lib().graph_build_csr_weighted(
+        _dev(edges, torch.int64, "edges") if m else ctypes.c_void_p(None),
+        _dev(w, torch.float32, "w") if m else ctypes.c_void_p(None), m, int(scale),
+        ctypes.byref(h), _stream(stream)))
+    return Graph(h.value)
+
+
+def sssp(graph, root, delta=0.0, dist=None, parent=None, stream=None):
+    """Kernel 3 (Sec. 2.4): (dist float64 [n], parent int32 [n]) CUDA tensors of
+    the shortest paths from `root`; delta = bucket width (<= 0: the default)."""
+    if dist is None:
+        dist = torch.empty(graph.n, dtype=torch.float64, device="cuda")
+    if parent is None:
+        parent = torch.empty(graph.n, dtype=torch.int32, device="cuda")
+    if dist.numel() != graph.n or parent.numel() != graph.n:
+        raise ValueError("outputs must have n = %d entries" % graph.n)
+    _check(lib().sssp(graph.handle, int(root), float(delta), _dev(dist, torch.float64, "dist"),
+                      _dev(parent, torch.int32, "parent"), _stream(stream)))
+    return dist, parent
+
+
+def sssp_last_stats():
+    """Counters of this thread's last sssp call (synchronises its stream)."""
+    s = gb_sssp_stats()
+    _check(lib().sssp_last_stats(ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in gb_sssp_stats._fields_}
+
+
+def sssp_validate(graph, root, parent, dist, edges=None, stream=None):
+    """SSSP result validation on the device (synchronises the stream): a dict with
+    code (0 = valid, else the first failing rule 1..7), where, reached,
+    component_edges, teps_edges (-1 without edges) and max_dist."""
+    if parent.numel() != graph.n or dist.numel() != graph.n:
+        raise ValueError("parent/dist must have n = %d entries" % graph.n)
+    if edges is not None:
+        if edges.dim() != 2 or edges.shape[0] != 2:
+            raise ValueError("edges must be a [2, m] tensor")
+        ep, m = _dev(edges, torch.int64, "edges"), int(edges.shape[1])
+    else:
+        ep, m = ctypes.c_void_p(None), 0
+    out = gb_sssp_validation()
+    _check(lib().sssp_validate(graph.handle, int(root), _dev(parent, torch.int32, "parent"),
+                               _dev(dist, torch.float64, "dist"), ep, m, ctypes.byref(out),
+                               _stream(stream)))
+    return {f: getattr(out, f) for f, _ in gb_sssp_validation._fields_ if f != "pad"}

@@ -1,11 +1,12 @@
 // C ABI of the library (include/gb300bfs.h): argument checks, error
 // reporting, the per-device context and the graph objects.  Every compute
-// step runs in the CUDA kernels of gen.cu, sort.cu, csr.cu, bfs.cu and
-// msbfs.cu.
+// step runs in the CUDA kernels of gen.cu, sort.cu, csr.cu, bfs.cu, msbfs.cu,
+// validate.cu and sssp.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -42,6 +43,34 @@ struct StatsSlot {
     bool valid = false;
 };
 thread_local StatsSlot t_stats;
+
+// last sssp call of this thread
+struct SsspSlot {
+    int device = -1;
+    SsspDevStats *dev = nullptr;
+    cudaStream_t stream = nullptr;
+    bool valid = false;
+};
+thread_local SsspSlot t_sssp;
+
+SsspDevStats *sssp_stats_buffer()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (t_sssp.dev && t_sssp.device == dev) return t_sssp.dev;
+    if (t_sssp.dev) {
+        int old = 0;
+        cudaGetDevice(&old);
+        cudaSetDevice(t_sssp.device);
+        cudaFree(t_sssp.dev);
+        cudaSetDevice(old);
+        t_sssp.dev = nullptr;
+    }
+    if (cudaMalloc((void **)&t_sssp.dev, sizeof(SsspDevStats)) != cudaSuccess) return nullptr;
+    t_sssp.device = dev;
+    t_sssp.valid = false;
+    return t_sssp.dev;
+}
 
 gb_status check_graph(const gb_graph *g)
 {
@@ -146,6 +175,9 @@ namespace {
 
 cudaStream_t as_stream(gb_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Default bucket width of kernel 3 (weight units of 1.0).
+constexpr double kDefaultDelta = 0.0625;
+
 template <typename F>
 gb_status guarded(F &&f)
 {
@@ -248,6 +280,120 @@ gb_status graph_build_csr_counting(const int64_t *edges, int64_t m, int scale, g
     });
 }
 
+gb_status kron_weights(int64_t m, uint64_t seed_weight, float *w, gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        if (m < 0 || (m > 0 && !w)) {
+            set_error("kron_weights: need m >= 0 and w != NULL");
+            return GB_ERR_INVALID;
+        }
+        return kron_weights_impl(m, seed_weight, w, as_stream(s));
+    });
+}
+
+gb_status graph_build_csr_weighted(const int64_t *edges, const float *w, int64_t m, int scale,
+                                   gb_graph **out, gb_stream s)
+{
+    return guarded([&]() {
+        if (!out || scale < 1 || scale > 30 || m < 0 || (m > 0 && (!edges || !w))) {
+            set_error("graph_build_csr_weighted: need out != NULL, 1 <= scale <= 30, m >= 0, "
+                      "edges and w != NULL if m > 0");
+            return GB_ERR_INVALID;
+        }
+        *out = nullptr;
+        gb_graph *g = new gb_graph();
+        gb_status rc = build_csr_weighted(edges, w, m, scale, g, as_stream(s));
+        if (rc != GB_OK) {
+            cudaStreamSynchronize(as_stream(s));
+            if (g->off) cudaFree(g->off);
+            if (g->col) cudaFree(g->col);
+            if (g->nz) cudaFree(g->nz);
+            if (g->hub) cudaFree(g->hub);
+            if (g->wgt) cudaFree(g->wgt);
+            delete g;
+            return rc;
+        }
+        *out = g;
+        return GB_OK;
+    });
+}
+
+gb_status graph_weights_view(const gb_graph *g, const uint32_t **wgt)
+{
+    gb_status rc = check_graph(g);
+    if (rc != GB_OK) return rc;
+    if (!g->wgt) {
+        set_error("graph_weights_view: the graph has no weights");
+        return GB_ERR_INVALID;
+    }
+    if (wgt) *wgt = g->wgt;
+    return GB_OK;
+}
+
+gb_status sssp(const gb_graph *g, int64_t root, double delta, double *dist, int32_t *parent,
+               gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        gb_status rc = check_graph(g);
+        if (rc != GB_OK) return rc;
+        if (!dist || !parent || std::isnan(delta)) {
+            set_error("sssp: NULL output or NaN delta");
+            return GB_ERR_INVALID;
+        }
+        if (root < 0 || root >= g->n) {
+            set_error("sssp: root outside [0, n)");
+            return GB_ERR_RANGE;
+        }
+        SsspDevStats *st = sssp_stats_buffer();
+        if (!st) return cuda_fail(cudaErrorMemoryAllocation, "sssp stats buffer");
+        rc = sssp_impl(g, root, delta > 0 ? delta : kDefaultDelta, dist, parent, st, as_stream(s));
+        if (rc == GB_OK) {
+            t_sssp.stream = as_stream(s);
+            t_sssp.valid = true;
+        }
+        return rc;
+    });
+}
+
+gb_status sssp_last_stats(gb_sssp_stats *out)
+{
+    return guarded([&]() -> gb_status {
+        if (!out) {
+            set_error("sssp_last_stats: NULL");
+            return GB_ERR_INVALID;
+        }
+        if (!t_sssp.valid || !t_sssp.dev) {
+            set_error("sssp_last_stats: no sssp call on this thread yet");
+            return GB_ERR_INVALID;
+        }
+        SsspDevStats h;
+        GB_CUDA(cudaStreamSynchronize(t_sssp.stream));
+        GB_CUDA(cudaMemcpy(&h, t_sssp.dev, sizeof(h), cudaMemcpyDeviceToHost));
+        out->rounds = (int64_t)h.rounds;
+        out->buckets = (int64_t)h.buckets;
+        out->processed = (int64_t)h.processed;
+        out->scanned = (int64_t)h.scanned;
+        out->won = (int64_t)h.won;
+        out->reached = (int64_t)h.reached;
+        out->delta = (double)h.delta / 16777216.0;
+        return GB_OK;
+    });
+}
+
+gb_status sssp_validate(const gb_graph *g, int64_t root, const int32_t *parent, const double *dist,
+                        const int64_t *edges, int64_t m, gb_sssp_validation *out, gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        if (!g || !parent || !dist || !out || m < 0 || (m > 0 && !edges)) {
+            set_error("sssp_validate: need g, parent, dist, out != NULL, m >= 0, edges != NULL if m > 0");
+            return GB_ERR_INVALID;
+        }
+        gb_status rc = check_graph(g);
+        if (rc != GB_OK) return rc;
+        return sssp_validate_impl(g, root, parent, dist, m > 0 ? edges : nullptr, m, out, as_stream(s));
+    });
+}
+
 gb_status graph_generate_csr(int scale, int edgefactor, double a, double b, double c,
                              uint64_t seed_gen, uint64_t seed_perm, gb_graph **out, gb_stream s)
 {
@@ -347,6 +493,7 @@ gb_status graph_free(gb_graph *g)
         if (g->col) cudaFree(g->col);
         if (g->nz) cudaFree(g->nz);
         if (g->hub) cudaFree(g->hub);
+        if (g->wgt) cudaFree(g->wgt);
         g->off = nullptr;
         g->col = nullptr;
         g->nz = nullptr;

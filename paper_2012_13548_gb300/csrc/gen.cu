@@ -35,6 +35,18 @@ __global__ void gen_hash_iota_kernel(int64_t count, uint64_t seed, uint64_t *__r
     }
 }
 
+// Sec. 2.1 weight row: tuple j weighs (1 + the top 24 bits of
+// SplitMix64(seed_w, j)) * 2^-24, a multiple of 2^-24 in (0, 1]; the integer
+// is at most 2^24 and the scale a power of two, so the float is exact.
+__global__ void gen_weights_kernel(int64_t m, uint64_t seed_w, float *__restrict__ w)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const uint32_t k = 1u + (uint32_t)(splitmix64(seed_w, (uint64_t)j) >> 40);
+        w[j] = (float)k * 5.9604644775390625e-8f;  // 2^-24
+    }
+}
+
 // pi[v] = rank of v: the sorted id list read as rank -> vertex, inverted.
 __global__ void gen_perm_scatter_kernel(const uint32_t *__restrict__ sorted_ids, int64_t n,
                                         int32_t *__restrict__ pi, DevStatus *st)
@@ -236,6 +248,17 @@ gb_status kron_keys_impl(int scale, int edgefactor, double a, double b, double c
     GB_CUDA(cudaFreeAsync(v0, s));
     GB_CUDA(cudaFreeAsync(v1, s));
     GB_CUDA(cudaFreeAsync(pi, s));
+    return GB_OK;
+}
+
+gb_status kron_weights_impl(int64_t m, uint64_t seed_w, float *w, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    if (m == 0) return GB_OK;
+    gen_weights_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(m, seed_w, w);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
     return GB_OK;
 }
 

@@ -82,6 +82,7 @@ struct gb_graph {
     int32_t *col = nullptr;  // device [nnz]
     uint32_t *nz = nullptr;  // device [ceil(n/32)]: bit v set iff degree(v) >= 1
     int32_t *hub = nullptr;  // device [n]: a neighbour of v of largest degree, or -1
+    uint32_t *wgt = nullptr; // device [nnz] weights in units of 2^-24 (weighted graphs only)
     int device = -1;
 };
 
@@ -97,7 +98,28 @@ gb_status kron_csr(int scale, int edgefactor, double a, double b, double c, uint
 // The degree >= 1 bitmap and the hub array of a graph whose CSR is in place (csr.cu).
 gb_status build_graph_aux(gb_graph *g, cudaStream_t s);
 
+// Kernel 1 with the weight row: build_csr, then each entry's least weight (sssp.cu).
+gb_status build_csr_weighted(const int64_t *edges, const float *w, int64_t m, int scale, gb_graph *g,
+                             cudaStream_t s);
+
+// Kernel 3 (sssp.cu): device statistics of the last search, and the search.
+struct SsspDevStats {
+    unsigned long long rounds;     // expansion rounds (near queues processed)
+    unsigned long long buckets;    // buckets settled
+    unsigned long long processed;  // near-queue entries expanded
+    unsigned long long scanned;    // edges of the expanded rows
+    unsigned long long won;        // relaxations that lowered a distance
+    unsigned long long reached;    // vertices with a finite distance
+    unsigned long long delta;      // bucket width in units of 2^-24
+};
+gb_status sssp_impl(const gb_graph *g, int64_t root, double delta, double *dist, int32_t *parent,
+                    SsspDevStats *stats, cudaStream_t s);
+gb_status sssp_validate_impl(const gb_graph *g, int64_t root, const int32_t *parent, const double *dist,
+                             const int64_t *edges, int64_t m, gb_sssp_validation *out, cudaStream_t s);
+
 // Kronecker generator (gen.cu).
+// The weight row of m tuples (gen.cu).
+gb_status kron_weights_impl(int64_t m, uint64_t seed_w, float *w, cudaStream_t s);
 // The 2m symmetrised kernel-1 keys of the Kronecker tuples, written to keys (gen.cu).
 gb_status kron_keys_impl(int scale, int edgefactor, double a, double b, double c,
                          uint64_t seed_gen, uint64_t seed_perm, uint64_t *keys, cudaStream_t s);

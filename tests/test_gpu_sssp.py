@@ -1,0 +1,202 @@
+"""GPU parity of kernel 3 (Sec. 2.4) and of the weighted kernel 1.
+
+The weight row and the weighted CSR must equal the oracle's bit for bit.  The
+distances must equal those of the oracle's Dijkstra exactly (every weight is a
+multiple of 2^-24, so both sides compute exact sums), and the parents the
+oracle's canonical tree of those distances.  The device validator must return
+the oracle validator's verdict on valid and corrupted outputs alike.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2012_13548_gb300 as gb  # noqa: E402
+from paper_2012_13548_gb300 import workloads as W  # noqa: E402
+from tests.conftest import oracle_graph, roots_for  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+UNIT = 2.0 ** -24
+
+
+def np_(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_weighted(scale):
+    """(edges, w, off, col, wgt) of the oracle for the workload graph of `scale`."""
+    e, _, _ = oracle_graph(scale)
+    w = oracle.kron_weights(e.shape[1], W.GraphSpec(scale=scale).seed_weight())
+    off, col, wgt = oracle.csr_build_weighted(e, w, scale)
+    return e, w, off, col, wgt
+
+
+def gpu_weighted(scale):
+    spec = W.GraphSpec(scale=scale)
+    e = gb.kron_generate(**spec.kron_args())
+    w = gb.kron_weights(e.shape[1], spec.seed_weight())
+    return e, w, gb.graph_build_csr_weighted(e, w, scale)
+
+
+def check_search(G, off, col, wgt, root, delta=0.0, edges=None):
+    dist, parent = gb.sssp(G, root, delta)
+    d_ref, _ = oracle.sssp(off, col, wgt, root)
+    p_ref = oracle.sssp_tree(off, col, wgt, root, d_ref)
+    d, p = np_(dist), np_(parent)
+    n = len(off) - 1
+    assert np.array_equal(d[:n], d_ref[:n]), (root, delta)
+    assert np.array_equal(p[:n], p_ref[:n]), (root, delta)
+    v = gb.sssp_validate(G, root, parent, dist, edges)
+    assert v["code"] == 0, v
+    assert v["reached"] == int(np.isfinite(d_ref).sum())
+    st = gb.sssp_last_stats()
+    assert st["reached"] == v["reached"]
+    return v
+
+
+def test_weight_row_bit_exact():
+    for m, seed in [(1, 0), (1000, 5), (1 << 20, W.GraphSpec(scale=16).seed_weight())]:
+        w = gb.kron_weights(m, seed)
+        assert np.array_equal(np_(w).astype(np.float64), oracle.kron_weights(m, seed))
+
+
+@pytest.mark.parametrize("scale", [1, 4, 8, 12, 16])
+def test_weighted_csr_equals_the_oracle(scale):
+    e, w, G = gpu_weighted(scale)
+    _, _, off_ref, col_ref, wgt_ref = oracle_weighted(scale)
+    off, col = G.csr()
+    assert np.array_equal(np_(off), off_ref)
+    assert np.array_equal(np_(col), col_ref)
+    assert np.array_equal(np_(G.weights()).astype(np.float64) * UNIT, wgt_ref)
+    G.free()
+
+
+@pytest.mark.parametrize("scale", [1, 2, 5, 8, 12, 16])
+def test_sssp_kronecker_equals_dijkstra(scale):
+    e, w, G = gpu_weighted(scale)
+    _, _, off, col, wgt = oracle_weighted(scale)
+    roots = roots_for(scale, 3)
+    for i, r in enumerate(roots):
+        v = check_search(G, off, col, wgt, r, edges=e)
+        d_ref, _ = oracle.sssp(off, col, wgt, r)
+        lev = np.where(np.isfinite(d_ref), 0, -1).astype(np.int32)
+        assert v["teps_edges"] == oracle.teps_edges(oracle_graph(scale)[0], lev)
+    for delta in [0.004, 0.25, 8.0]:          # many buckets, a few, one
+        check_search(G, off, col, wgt, roots[0], delta)
+    G.free()
+
+
+def build_from_host(e, w, scale):
+    return gb.graph_build_csr_weighted(torch.as_tensor(e).cuda(),
+                                       torch.as_tensor(w.astype(np.float32)).cuda(), scale)
+
+
+def test_sssp_structured_graphs():
+    rng = np.random.default_rng(9)
+    cases = []
+    # a path of 3000 vertices: one bucket after another
+    k = 3000
+    e = np.stack([np.arange(k - 1), np.arange(1, k)])
+    cases.append((12, e, rng.integers(1, 2**24 + 1, size=k - 1) * UNIT, [0, k - 1, 1234]))
+    # a star with 5000 leaves (a row split into chunks) plus a cycle through the leaves
+    leaves = np.arange(1, 5001)
+    e = np.concatenate([np.stack([np.zeros(5000, dtype=np.int64), leaves]),
+                        np.stack([leaves, np.roll(leaves, 1)])], axis=1)
+    cases.append((13, e, rng.integers(1, 2**24 + 1, size=e.shape[1]) * UNIT, [0, 7, 4999]))
+    # unit weights: the distances are BFS levels and ties are everywhere
+    spec = W.GraphSpec(scale=11)
+    ek = oracle.kron_generate(**spec.kron_args())
+    cases.append((11, ek, np.ones(ek.shape[1]), roots_for(11, 2)))
+    # few distinct weights, many ties between paths, duplicates with other weights
+    e = rng.integers(0, 1 << 10, size=(2, 12000))
+    e = np.concatenate([e, e[:, :3000]], axis=1)
+    cases.append((10, e, rng.integers(1, 5, size=e.shape[1]) / 4.0, [0, 5, 999]))
+    for scale, e, w, roots in cases:
+        e = e.astype(np.int64)
+        G = build_from_host(e, w, scale)
+        off, col, wgt = oracle.csr_build_weighted(e, w, scale)
+        for r in roots:
+            for delta in [0.0, 0.03, 1.0]:
+                check_search(G, off, col, wgt, int(r), delta)
+        G.free()
+
+
+def test_sssp_random_small_graphs_all_roots():
+    rng = np.random.default_rng(13)
+    for trial in range(12):
+        scale = int(rng.integers(1, 6))
+        n = 1 << scale
+        m = int(rng.integers(0, 4 * n))
+        e = rng.integers(0, n, size=(2, m)).astype(np.int64)
+        w = rng.integers(1, 2**24 + 1, size=m) * UNIT
+        G = build_from_host(e, w, scale)
+        off, col, wgt = oracle.csr_build_weighted(e, w, scale)
+        for r in range(n):
+            check_search(G, off, col, wgt, r)
+        G.free()
+
+
+def test_sssp_isolated_root_and_errors():
+    e = np.array([[0, 1], [1, 2]], dtype=np.int64)
+    G = build_from_host(e, np.array([0.5, 0.25]), 3)
+    dist, parent = gb.sssp(G, 5)
+    d, p = np_(dist), np_(parent)
+    assert d[5] == 0.0 and p[5] == 5
+    assert np.all(np.isinf(np.delete(d, 5))) and np.all(np.delete(p, 5) == -1)
+    with pytest.raises(gb.GbError, match="RANGE"):
+        gb.sssp(G, 8)
+    with pytest.raises(gb.GbError, match="RANGE"):
+        gb.sssp(G, -1)
+    G.free()
+    plain = gb.graph_build_csr(torch.as_tensor(e).cuda(), 3)
+    with pytest.raises(gb.GbError, match="INVALID"):
+        gb.sssp(plain, 0)
+    with pytest.raises(gb.GbError, match="INVALID"):
+        plain.weights()
+    plain.free()
+    for bad in ([0.5, 0.0], [0.5, 1.5], [float("nan"), 0.5], [-0.5, 0.5]):
+        with pytest.raises(gb.GbError, match="RANGE"):
+            build_from_host(e, np.array(bad), 3)
+    with pytest.raises(gb.GbError, match="RANGE"):
+        build_from_host(np.array([[0], [9]]), np.array([0.5]), 3)
+    gb.gb_device_status()
+
+
+def test_sssp_validator_matches_the_oracle_on_planted_mistakes():
+    scale = 9
+    e, w, off, col, wgt = oracle_weighted(scale)
+    G = build_from_host(e, w, scale)
+    root = roots_for(scale, 1)[0]
+    d_ref, _ = oracle.sssp(off, col, wgt, root)
+    tree = oracle.sssp_tree(off, col, wgt, root, d_ref)
+    reached = np.flatnonzero(np.isfinite(d_ref))
+    v = int(reached[reached != root][5])
+    isolated = int(np.flatnonzero(np.diff(off) == 0)[0])
+    cases = [(tree, d_ref)]
+    d = d_ref.copy(); d[root] = UNIT; cases.append((tree, d))
+    p = tree.copy(); p[v] = -1; cases.append((p, d_ref))
+    p = tree.copy(); p[v] = next(u for u in reached if u not in col[off[v]:off[v + 1]] and u != v)
+    cases.append((p, d_ref))
+    d = d_ref.copy(); d[v] += UNIT; cases.append((tree, d))
+    p = tree.copy(); p[isolated] = root
+    d = d_ref.copy(); d[isolated] = 1.0; cases.append((p, d))
+    d = d_ref.copy(); d[v] = -1.0; cases.append((tree, d))
+    d = d_ref.copy(); d[v] = np.nan; cases.append((tree, d))
+    p = tree.copy(); p[v] = len(tree) + 3; cases.append((p, d_ref))
+    d = d_ref.copy(); d[reached[reached != root]] *= 1.5; cases.append((tree, d))
+    for p, d in cases:
+        want = oracle.sssp_validate(off, col, wgt, root, p, d)
+        got = gb.sssp_validate(G, root, torch.as_tensor(p.astype(np.int32)).cuda(),
+                               torch.as_tensor(d).cuda())
+        assert got["code"] == want, (got, want)
+    assert gb.sssp_validate(G, len(tree), torch.as_tensor(tree).cuda(),
+                            torch.as_tensor(d_ref).cuda())["code"] == 7
+    G.free()
