@@ -166,7 +166,8 @@ gb_status graph_csr_view(const gb_graph *g, const int64_t **off, const int32_t *
  *                      claimed v first (any valid Graph500 tree);
  *                      1: parent(v) is the smallest-id neighbour one level
  *                      up (a unique tree, Sec. 2.3.1: the tree follows from
- *                      the level array).
+ *                      the level array).  It selects the same for sssp
+ *                      (smallest-id neighbour on a shortest path).
  *   alpha, beta        direction switch: top-down -> bottom-up when the
  *                      frontier's edges exceed (unexplored edges)/alpha;
  *                      bottom-up -> top-down when the frontier shrinks below
@@ -335,7 +336,9 @@ gb_status kron_weights(int64_t m, uint64_t seed_weight, float *w, gb_stream s);
  * (rounded to the nearest unit, at least one), so that every path length is
  * an exact sum.  GB_ERR_RANGE for an endpoint outside [0, 2^scale) or a
  * weight outside (0, 1] (NaN included).  Synchronises `s`; the graph also
- * holds 4 * nnz bytes of weights. */
+ * holds 12 * nnz bytes for the weights: one weight per CSR entry and every
+ * row again as (column, weight) pairs by ascending weight, which the search
+ * reads (built by one radix sort; temporaries about 24 * nnz bytes). */
 gb_status graph_build_csr_weighted(const int64_t *edges, const float *w, int64_t m, int scale,
                                    gb_graph **out, gb_stream s);
 
@@ -350,10 +353,11 @@ gb_status graph_weights_view(const gb_graph *g, const uint32_t **wgt);
  * (e.g. 0.0625), <= 0 for the default.  Outputs, caller-allocated device
  * arrays: dist float64 [n] (exact: the least path weight, a multiple of
  * 2^-24; +infinity if unreachable) and parent int32 [n] (parent(root) = root;
- * for a reached v the smallest-id neighbour u with dist(u) + w(u,v) =
- * dist(v); -1 if unreachable).  The distances are those of Dijkstra's
- * algorithm exactly; the parent array is the unique canonical tree of them.
- * Allocates about 32 * n bytes of stream-ordered scratch.  GB_ERR_RANGE for
+ * for a reached v a neighbour u with dist(u) + w(u,v) = dist(v), the
+ * smallest-id one when the canonical_parents option is set; -1 if
+ * unreachable).  The distances are those of Dijkstra's algorithm exactly; in
+ * canonical mode the parent array is the unique canonical tree of them.
+ * Allocates about 40 * n bytes of stream-ordered scratch.  GB_ERR_RANGE for
  * a root outside [0, n); GB_ERR_INVALID for an unweighted graph. */
 gb_status sssp(const gb_graph *g, int64_t root, double delta, double *dist, int32_t *parent,
                gb_stream s);
@@ -366,7 +370,9 @@ gb_status sssp(const gb_graph *g, int64_t root, double delta, double *dist, int3
  *   scanned     edges of the expanded rows
  *   won         relaxations that lowered a distance
  *   reached     vertices with a finite distance
- *   delta       bucket width used, in weight units of 1.0 */
+ *   delta       bucket width used, in weight units of 1.0
+ *   phase_ns    device time of the expansion rounds, the settle steps (heavy
+ *               edges), the far-list minima and the far-list splits */
 typedef struct gb_sssp_stats {
     int64_t rounds;
     int64_t buckets;
@@ -375,6 +381,7 @@ typedef struct gb_sssp_stats {
     int64_t won;
     int64_t reached;
     double delta;
+    int64_t phase_ns[4];
 } gb_sssp_stats;
 
 gb_status sssp_last_stats(gb_sssp_stats *out);

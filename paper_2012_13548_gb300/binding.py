@@ -54,7 +54,7 @@ class gb_validation(ctypes.Structure):
 class gb_sssp_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in
                 ("rounds", "buckets", "processed", "scanned", "won", "reached")] + \
-        [("delta", ctypes.c_double)]
+        [("delta", ctypes.c_double), ("phase_ns", ctypes.c_int64 * 4)]
 
 
 class gb_sssp_validation(ctypes.Structure):
@@ -518,7 +518,9 @@ def sssp_last_stats():
     """Counters of this thread's last sssp call (synchronises its stream)."""
     s = gb_sssp_stats()
     _check(lib().sssp_last_stats(ctypes.byref(s)))
-    return {f: getattr(s, f) for f, _ in gb_sssp_stats._fields_}
+    out = {f: getattr(s, f) for f, _ in gb_sssp_stats._fields_[:7]}
+    out["phase_ns"] = list(s.phase_ns)
+    return out
 
 
 def sssp_validate(graph, root, parent, dist, edges=None, stream=None):

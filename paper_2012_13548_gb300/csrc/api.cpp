@@ -310,6 +310,7 @@ gb_status graph_build_csr_weighted(const int64_t *edges, const float *w, int64_t
             if (g->nz) cudaFree(g->nz);
             if (g->hub) cudaFree(g->hub);
             if (g->wgt) cudaFree(g->wgt);
+            if (g->wadj) cudaFree(g->wadj);
             delete g;
             return rc;
         }
@@ -376,6 +377,7 @@ gb_status sssp_last_stats(gb_sssp_stats *out)
         out->won = (int64_t)h.won;
         out->reached = (int64_t)h.reached;
         out->delta = (double)h.delta / 16777216.0;
+        for (int k = 0; k < 4; ++k) out->phase_ns[k] = (int64_t)h.phase_ns[k];
         return GB_OK;
     });
 }
@@ -494,6 +496,7 @@ gb_status graph_free(gb_graph *g)
         if (g->nz) cudaFree(g->nz);
         if (g->hub) cudaFree(g->hub);
         if (g->wgt) cudaFree(g->wgt);
+        if (g->wadj) cudaFree(g->wadj);
         g->off = nullptr;
         g->col = nullptr;
         g->nz = nullptr;

@@ -83,6 +83,7 @@ struct gb_graph {
     uint32_t *nz = nullptr;  // device [ceil(n/32)]: bit v set iff degree(v) >= 1
     int32_t *hub = nullptr;  // device [n]: a neighbour of v of largest degree, or -1
     uint32_t *wgt = nullptr; // device [nnz] weights in units of 2^-24 (weighted graphs only)
+    uint2 *wadj = nullptr;   // device [nnz] (column, weight) of each row by ascending weight
     int device = -1;
 };
 
@@ -111,6 +112,7 @@ struct SsspDevStats {
     unsigned long long won;        // relaxations that lowered a distance
     unsigned long long reached;    // vertices with a finite distance
     unsigned long long delta;      // bucket width in units of 2^-24
+    unsigned long long phase_ns[4];  // device time: expansion rounds, settle steps, far minima, far splits
 };
 gb_status sssp_impl(const gb_graph *g, int64_t root, double delta, double *dist, int32_t *parent,
                     SsspDevStats *stats, cudaStream_t s);

@@ -19,15 +19,31 @@
 //     T = (d / delta + 1) * delta (empty buckets are skipped), and the far
 //     list is split: entries below T (settled meanwhile) are dropped, entries
 //     inside the new bucket form the near queue, the rest the next far list;
+//   * light and heavy edges (Meyer and Sanders' split, taken per vertex): the
+//     search reads a second copy of every row sorted by weight.  Expanding u
+//     relaxes only the prefix of its row with w < T - dist(u), the edges that
+//     can still land in the current bucket; u is listed once per bucket, and
+//     when the bucket is settled the rest of each listed row (the heavy
+//     edges, which can only produce distances >= T) is relaxed once, with
+//     the final dist(u).  A vertex expanded again after its distance dropped
+//     re-reads only its light prefix;
 //   * rows longer than SP_BIG are cut into SP_CHUNK-edge chunks that all warps
-//     share; shorter rows are expanded 32 per warp as one stream of edges;
-//   * after the last bucket the kernel writes the distances as doubles and
-//     the canonical tree: parent(v) is the smallest-id neighbour u with
-//     dist(u) + w(u,v) = dist(v), the first such entry of v's sorted row.
+//     share (a chunk tests each edge against the split itself); shorter rows
+//     find their split by bisection and are expanded 32 per warp as one
+//     stream of edges;
+//   * a relaxation that lowers dist(v) also writes u as v's parent (a plain
+//     store: racing winners may leave a parent that is no longer tight);
+//   * after the last bucket the kernel writes the distances as doubles and the
+//     tree: by default each recorded parent is checked (one bisection of v's
+//     row) and kept if tight, dist(u) + w(u,v) = dist(v); otherwise, and for
+//     every vertex in canonical mode, parent(v) is the smallest-id tight
+//     neighbour, the first tight entry of v's column-sorted row.
 //
 // Kernel 1's weights: graph_build_csr_weighted builds the CSR as kernel 1 does
 // and then gives each entry the least weight among the tuples joining its pair
-// (each tuple finds its two entries by bisection of the sorted rows).
+// (each tuple finds its two entries by bisection of the sorted rows); the
+// weight-sorted rows come from one radix sort of (row << 25 | weight) keys
+// carrying the columns (stable, so equal weights keep ascending columns).
 #include "common.cuh"
 #include "internal.h"
 
@@ -98,6 +114,31 @@ __global__ void wt_attach_kernel(const int64_t *__restrict__ edges, const float 
     }
 }
 
+// Keys (row << 25 | weight) and column values of every entry, one warp per row.
+__global__ void wsort_keys_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                  const uint32_t *__restrict__ wgt, int64_t n,
+                                  uint64_t *__restrict__ keys, uint32_t *__restrict__ vals)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = gwarp; u < n; u += nwarps) {
+        const int64_t s0 = off[u], e0 = off[u + 1];
+        for (int64_t j = s0 + lane; j < e0; j += 32) {
+            keys[j] = ((uint64_t)u << 25) | (uint64_t)wgt[j];
+            vals[j] = (uint32_t)col[j];
+        }
+    }
+}
+
+__global__ void wsort_pack_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                                  int64_t nnz, uint2 *__restrict__ wadj)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += stride)
+        wadj[j] = make_uint2(vals[j], (uint32_t)(keys[j] & 0x1ffffffull));
+}
+
 // ---------------------------------------------------------------------------
 // The search
 // ---------------------------------------------------------------------------
@@ -117,6 +158,7 @@ struct SpHeader {
     unsigned long long minfar;     // least far distance >= T (bucket advance)
     unsigned long long farcnt[2];  // far list sizes, by epoch parity
     SpQueueCtl q[4];               // near queue counters, by queue id mod 4
+    SpQueueCtl settle;             // vertices expanded in the current bucket
     unsigned long long acc[4];     // processed, scanned, won, reached
 };
 
@@ -124,14 +166,17 @@ struct SpArgs {
     const int64_t *off;
     const int32_t *col;
     const uint32_t *wgt;
+    const uint2 *wadj;         // rows by ascending weight: (column, weight)
     int64_t n;
     int32_t root;
     unsigned long long *dist;  // [n] units of 2^-24, SP_INF if unreached
     uint32_t *nstamp;          // [n] id of the last near queue v entered
     uint32_t *fstamp;          // [n] epoch of the last far list v entered
+    uint32_t *sstamp;          // [n] epoch of the bucket that expanded v
     int32_t *nq;               // 2 near queues of n
     int32_t *fq;               // 2 far lists of n
-    SpBig *bq;                 // 2 big-row lists of bigcap
+    int32_t *sq;               // the settle list of n
+    SpBig *bq;                 // 2 big-row lists of bigcap, then the settle list's
     int64_t bigcap;
     SpHeader *hdr;
     DevStatus *st;
@@ -139,6 +184,7 @@ struct SpArgs {
     unsigned long long delta;
     double *dist_out;
     int32_t *parent;
+    int canonical;  // 1: the smallest-id tight parent of every vertex
     uint64_t timeout_ns;
     uint64_t run_limit_ns;  // the search gives up (GB_ERR_TIMEOUT) after this long
     long long max_rounds;
@@ -182,6 +228,58 @@ __device__ __forceinline__ void push_near(const SpArgs &a, unsigned qid, bool wa
     }
 }
 
+// Warp-collective: the lanes with `want` append v to the settle list of the
+// current bucket (a row longer than SP_BIG also with its chunks).
+__device__ __forceinline__ void push_settle(const SpArgs &a, bool want, int32_t v, int64_t d)
+{
+    const unsigned m = __ballot_sync(kFull, want);
+    if (!m) return;
+    const unsigned lane = lane_id();
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(&a.hdr->settle.cnt, (unsigned long long)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (!want) return;
+    const int64_t pos = (int64_t)base + __popc(m & lanemask_lt());
+    if (pos < a.n) a.sq[pos] = v;
+    else record_error(a.st, GB_ERR_RANGE, SITE_SP_NEAR, pos);
+    if (d > SP_BIG) {
+        const unsigned nch = (unsigned)((d + SP_CHUNK - 1) / SP_CHUNK);
+        const unsigned long long old = atomicAdd(&a.hdr->settle.big, (1ull << 32) | nch);
+        const int64_t bi = (int64_t)(old >> 32);
+        if (bi < a.bigcap) {
+            const unsigned long long r = (unsigned long long)(uint32_t)v | ((old & 0xffffffffull) << 32);
+            reinterpret_cast<unsigned long long *>(a.bq)[2 * a.bigcap + bi] = r;
+        } else {
+            record_error(a.st, GB_ERR_RANGE, SITE_SP_BIGQ, bi);
+        }
+    }
+}
+
+// First index j in [lo, hi) of a weight-sorted row with weight >= lim (hi if none).
+__device__ __forceinline__ int64_t weight_split(const uint2 *__restrict__ wadj, int64_t lo, int64_t hi,
+                                                unsigned long long lim)
+{
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((unsigned long long)wadj[mid].y < lim) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The entry of a big-row list that holds chunk c (the largest cbase <= c).
+__device__ __forceinline__ SpBig find_chunk(const SpBig *B, int64_t nb, int64_t c)
+{
+    int64_t lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)load_spbig(B, mid).cbase <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return load_spbig(B, lo);
+}
+
 // Warp-collective: the lanes with `want` append v to the far list of `epoch`.
 __device__ __forceinline__ void push_far(const SpArgs &a, unsigned epoch, bool want, int32_t v)
 {
@@ -200,15 +298,16 @@ __device__ __forceinline__ void push_far(const SpArgs &a, unsigned epoch, bool w
 
 // Warp-collective relaxation of one edge per lane: dist(v) lowered to nd if
 // smaller; a lowered v is queued near (nd < T) or listed far.
-__device__ __forceinline__ void relax(const SpArgs &a, bool valid, int32_t v, unsigned long long nd,
-                                      unsigned long long T, unsigned qnext, unsigned epoch,
-                                      unsigned long long &won)
+__device__ __forceinline__ void relax(const SpArgs &a, bool valid, int32_t u, int32_t v,
+                                      unsigned long long nd, unsigned long long T, unsigned qnext,
+                                      unsigned epoch, unsigned long long &won)
 {
     bool to_near = false, to_far = false;
     if (valid && nd < __ldcg(&a.dist[v])) {
         const unsigned long long old = atomicMin(&a.dist[v], nd);
         if (nd < old) {
             ++won;
+            a.parent[v] = u;
             if (nd < T) to_near = atomicExch(&a.nstamp[v], qnext) != qnext;
             else to_far = atomicExch(&a.fstamp[v], epoch) != epoch;
         }
@@ -233,8 +332,10 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
     // ---- init: every distance infinite but the root's; the root queued
     for (int64_t v = gtid; v < n; v += gthreads) {
         a.dist[v] = v == a.root ? 0ull : SP_INF;
+        a.parent[v] = v == a.root ? a.root : -1;
         a.nstamp[v] = v == a.root ? 1u : 0u;
         a.fstamp[v] = 0u;
+        a.sstamp[v] = 0u;
     }
     if (gtid == 0) {
         a.nq[n + 0] = a.root;  // queue 1 sits in slot 1
@@ -251,6 +352,16 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
     unsigned qcur = 1, epoch = 1;
     unsigned long long T = a.delta;
     long long rounds = 0, buckets = 0;
+    // device time per phase, as thread 0 sees it from barrier to barrier
+    unsigned long long ph[4] = {0, 0, 0, 0};
+    uint64_t t_ph = globaltimer_ns();
+    auto phase_end = [&](int k) {
+        if (gtid == 0) {
+            const uint64_t now = globaltimer_ns();
+            ph[k] += now - t_ph;
+            t_ph = now;
+        }
+    };
     for (;; ++rounds) {
         if (rounds > a.max_rounds) {  // cannot happen: every queued vertex had its distance lowered
             if (gtid == 0) record_error(a.st, GB_ERR_TIMEOUT, SITE_SP_ROUNDS, rounds);
@@ -268,49 +379,48 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
         const int64_t ncur = (int64_t)__ldcg(&h->q[qcur & 3].cnt);
         const unsigned long long bigc = __ldcg(&h->q[qcur & 3].big);
         const int32_t *Q = a.nq + (int64_t)(qcur & 1) * n;
-        // ---- big rows: chunk c of the queue's numbering, one chunk per warp
+        // ---- light edges of big rows: chunk c of the queue's numbering, one per warp;
+        // an edge is light while w < T - dist(u), a prefix of the weight-sorted row
         const int64_t nb = (int64_t)(bigc >> 32) < a.bigcap ? (int64_t)(bigc >> 32) : a.bigcap;
         const int64_t nch = nb > 0 ? (int64_t)(bigc & 0xffffffffull) : 0;
         const SpBig *B = a.bq + (int64_t)(qcur & 1) * a.bigcap;
         for (int64_t c = gwarp; c < nch; c += nwarps) {
-            int64_t lo = 0, hi = nb - 1;  // the entry with the largest cbase <= c
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if ((int64_t)load_spbig(B, mid).cbase <= c) lo = mid;
-                else hi = mid - 1;
-            }
-            const SpBig be = load_spbig(B, lo);
+            const SpBig be = find_chunk(B, nb, c);
             const int64_t rs = a.off[be.u], re = a.off[be.u + 1];
             const int64_t s0 = rs + (c - (int64_t)be.cbase) * SP_CHUNK;
             const int64_t e0 = s0 + SP_CHUNK < re ? s0 + SP_CHUNK : re;
             const unsigned long long du = __ldcg(&a.dist[be.u]);
-            if (lane == 0) scanned += (unsigned long long)(e0 - s0);
+            const unsigned long long lim = T - du;
+            if ((unsigned long long)a.wadj[s0].y >= lim) continue;  // the chunk is all heavy
             for (int64_t j0 = s0; j0 < e0; j0 += 32) {
                 const int64_t j = j0 + lane;
-                const bool valid = j < e0;
-                int32_t v = 0;
-                unsigned long long nd = 0;
-                if (valid) {
-                    v = a.col[j];
-                    nd = du + a.wgt[j];
-                }
-                relax(a, valid, v, nd, T, qnext, epoch, won);
+                uint2 cw = make_uint2(0u, 0u);
+                if (j < e0) cw = a.wadj[j];
+                const bool valid = j < e0 && (unsigned long long)cw.y < lim;
+                scanned += valid;
+                relax(a, valid, be.u, (int32_t)cw.x, du + cw.y, T, qnext, epoch, won);
+                if (!__any_sync(kFull, valid)) break;  // past the split
             }
         }
-        // ---- shorter rows: 32 queue entries per warp, their edges as one stream
+        // ---- every queue entry: listed for its bucket's settle step once; the
+        // light prefix of a shorter row expanded, 32 rows per warp as one stream
         for (int64_t i0 = gwarp * 32; i0 < ncur; i0 += nwarps * 32) {
             const int64_t i = i0 + lane;
-            int64_t s0 = 0, d = 0;
+            int64_t s0 = 0, d = 0, deg = 0;
             unsigned long long du = 0;
+            bool first = false;
+            int32_t u = 0;
             if (i < ncur) {
-                const int32_t u = __ldcg(&Q[i]);
+                u = __ldcg(&Q[i]);
                 s0 = a.off[u];
-                d = a.off[u + 1] - s0;
-                if (d > SP_BIG) d = 0;  // expanded through the big list
+                deg = a.off[u + 1] - s0;
                 du = __ldcg(&a.dist[u]);
+                first = atomicExch(&a.sstamp[u], epoch) != epoch;
+                d = deg > SP_BIG ? 0 : weight_split(a.wadj, s0, s0 + deg, T - du) - s0;
                 ++processed;
                 scanned += (unsigned long long)d;
             }
+            push_settle(a, first, u, deg);
             const int64_t incl = warp_inclusive_scan(d);
             const int64_t total = __shfl_sync(kFull, incl, 31);
             const int64_t excl = incl - d;
@@ -325,27 +435,92 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
                 const int64_t so = __shfl_sync(kFull, s0, owner);
                 const int64_t eo = __shfl_sync(kFull, excl, owner);
                 const unsigned long long duo = __shfl_sync(kFull, du, owner);
+                const int32_t uo = __shfl_sync(kFull, u, owner);
                 const bool valid = k < total;
-                int32_t v = 0;
-                unsigned long long nd = 0;
-                if (valid) {
-                    const int64_t j = so + (k - eo);
-                    v = a.col[j];
-                    nd = duo + a.wgt[j];
-                }
-                relax(a, valid, v, nd, T, qnext, epoch, won);
+                uint2 cw = make_uint2(0u, 0u);
+                if (valid) cw = a.wadj[so + (k - eo)];
+                relax(a, valid, uo, (int32_t)cw.x, duo + cw.y, T, qnext, epoch, won);
             }
         }
         if (!grid_sync(&h->bar, bar, a.st, a.timeout_ns, SITE_SP_BAR)) return;
+        phase_end(0);
         if (__ldcg(&h->q[qnext & 3].cnt) > 0) {
             qcur = qnext;
             continue;
         }
-        // ---- the bucket below T is settled: the least far distance >= T
+        // ---- the bucket below T is settled: the heavy edges of its vertices,
+        // from their final distances (every candidate is >= T: far)
         const unsigned e = epoch;
+        if (gtid == 0) h->farcnt[(e + 1) & 1] = 0;  // its last reader was the previous split
+        {
+            const int64_t ns = (int64_t)__ldcg(&h->settle.cnt);
+            const unsigned long long sbig = __ldcg(&h->settle.big);
+            const int64_t snb = (int64_t)(sbig >> 32) < a.bigcap ? (int64_t)(sbig >> 32) : a.bigcap;
+            const int64_t snch = snb > 0 ? (int64_t)(sbig & 0xffffffffull) : 0;
+            const SpBig *SB = a.bq + 2 * a.bigcap;
+            for (int64_t c = gwarp; c < snch; c += nwarps) {
+                const SpBig be = find_chunk(SB, snb, c);
+                const int64_t rs = a.off[be.u], re = a.off[be.u + 1];
+                const int64_t s0 = rs + (c - (int64_t)be.cbase) * SP_CHUNK;
+                const int64_t e0 = s0 + SP_CHUNK < re ? s0 + SP_CHUNK : re;
+                const unsigned long long du = __ldcg(&a.dist[be.u]);
+                const unsigned long long lim = T - du;
+                if ((unsigned long long)a.wadj[e0 - 1].y < lim) continue;  // the chunk is all light
+                for (int64_t j0 = s0; j0 < e0; j0 += 32) {
+                    const int64_t j = j0 + lane;
+                    uint2 cw = make_uint2(0u, 0u);
+                    if (j < e0) cw = a.wadj[j];
+                    const bool valid = j < e0 && (unsigned long long)cw.y >= lim;
+                    scanned += valid;
+                    relax(a, valid, be.u, (int32_t)cw.x, du + cw.y, T, qnext, e, won);
+                }
+            }
+            for (int64_t i0 = gwarp * 32; i0 < ns; i0 += nwarps * 32) {
+                const int64_t i = i0 + lane;
+                int64_t s0 = 0, d = 0;
+                unsigned long long du = 0;
+                int32_t u = 0;
+                if (i < ns) {
+                    u = __ldcg(&a.sq[i]);
+                    const int64_t rs = a.off[u], deg = a.off[u + 1] - rs;
+                    du = __ldcg(&a.dist[u]);
+                    if (deg <= SP_BIG) {
+                        s0 = weight_split(a.wadj, rs, rs + deg, T - du);
+                        d = rs + deg - s0;
+                        scanned += (unsigned long long)d;
+                    }
+                }
+                const int64_t incl = warp_inclusive_scan(d);
+                const int64_t total = __shfl_sync(kFull, incl, 31);
+                const int64_t excl = incl - d;
+                for (int64_t b = 0; b < total; b += 32) {
+                    const int64_t k = b + lane;
+                    int owner = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int cand = owner + step;
+                        if (__shfl_sync(kFull, excl, cand) <= k) owner = cand;
+                    }
+                    const int64_t so = __shfl_sync(kFull, s0, owner);
+                    const int64_t eo = __shfl_sync(kFull, excl, owner);
+                    const unsigned long long duo = __shfl_sync(kFull, du, owner);
+                    const int32_t uo = __shfl_sync(kFull, u, owner);
+                    const bool valid = k < total;
+                    uint2 cw = make_uint2(0u, 0u);
+                    if (valid) cw = a.wadj[so + (k - eo)];
+                    relax(a, valid, uo, (int32_t)cw.x, duo + cw.y, T, qnext, e, won);
+                }
+            }
+        }
+        if (!grid_sync(&h->bar, bar, a.st, a.timeout_ns, SITE_SP_BAR)) return;
+        phase_end(1);
+        // ---- the least far distance >= T
+        if (gtid == 0) {  // every block read the settle list before the barrier above
+            h->settle.cnt = 0;
+            h->settle.big = 0;
+        }
         const int64_t nf = (int64_t)__ldcg(&h->farcnt[e & 1]);
         const int32_t *F = a.fq + (int64_t)(e & 1) * n;
-        if (gtid == 0) h->farcnt[(e + 1) & 1] = 0;  // its last reader was the previous split
         unsigned long long mn = SP_INF;
         for (int64_t i = gtid; i < nf; i += gthreads) {
             const unsigned long long d = __ldcg(&a.dist[__ldcg(&F[i])]);
@@ -357,6 +532,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
         }
         if (lane == 0 && mn != SP_INF) atomicMin(&h->minfar, mn);
         if (!grid_sync(&h->bar, bar, a.st, a.timeout_ns, SITE_SP_BAR)) return;
+        phase_end(2);
         const unsigned long long mf = __ldcg(&h->minfar);
         if (mf == SP_INF) break;  // nothing left to settle
         const unsigned long long Tn = (mf / a.delta + 1) * a.delta;
@@ -368,14 +544,21 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
             if (i < nf) {
                 v = __ldcg(&F[i]);
                 const unsigned long long d = __ldcg(&a.dist[v]);
-                if (d >= T && d < Tn) to_near = atomicExch(&a.nstamp[v], qnext) != qnext;
-                else if (d >= Tn) to_far = atomicExch(&a.fstamp[v], e + 1) != e + 1;
+                // the list holds each vertex once and nothing else pushes now: plain stamps
+                if (d >= T && d < Tn) {
+                    to_near = true;
+                    a.nstamp[v] = qnext;
+                } else if (d >= Tn) {
+                    to_far = true;
+                    a.fstamp[v] = e + 1;
+                }
             }
             push_near(a, qnext, to_near, v);
             push_far(a, e + 1, to_far, v);
         }
         if (!grid_sync(&h->bar, bar, a.st, a.timeout_ns, SITE_SP_BAR)) return;
-        if (gtid == 0) h->minfar = SP_INF;  // every block read it before the barrier
+        phase_end(3);
+        if (gtid == 0) h->minfar = SP_INF;  // every block read it before the barrier above
         ++buckets;
         T = Tn;
         epoch = e + 1;
@@ -398,6 +581,17 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
                 rs = a.off[v];
                 d = a.off[v + 1] - rs;
                 scan = true;
+                if (!a.canonical) {  // keep the recorded parent if it is tight
+                    const int32_t q = __ldcg(&a.parent[v]);
+                    if (q >= 0 && (int64_t)q < n) {
+                        const int64_t j = find_in_row(a.col, rs, rs + d, q);
+                        const unsigned long long dq = __ldcg(&a.dist[q]);
+                        if (j >= 0 && dq != SP_INF && dq + a.wgt[j] == dv) {
+                            p = q;
+                            scan = false;
+                        }
+                    }
+                }
             }
         }
         // short rows: the lane scans its own row in order
@@ -458,6 +652,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
         a.stats->won = __ldcg(&h->acc[2]);
         a.stats->reached = __ldcg(&h->acc[3]);
         a.stats->delta = a.delta;
+        for (int k = 0; k < 4; ++k) a.stats->phase_ns[k] = ph[k];
     }
 }
 
@@ -650,6 +845,30 @@ gb_status build_csr_weighted(const int64_t *edges, const float *w, int64_t m, in
                                          : "graph_build_csr_weighted: device error while attaching weights");
         return (gb_status)hst.code;
     }
+    // the rows by ascending weight: one sort of (row << 25 | weight) keys with the columns
+    const int64_t nnz = g->nnz;
+    GB_CUDA(cudaMalloc(&g->wadj, std::max<int64_t>(nnz, 4) * sizeof(uint2)));
+    if (nnz > 0) {
+        uint64_t *k0 = nullptr, *k1 = nullptr, *ks = nullptr;
+        uint32_t *v0 = nullptr, *v1 = nullptr, *vs = nullptr;
+        GB_CUDA(alloc_async(&k0, (size_t)nnz, s));
+        GB_CUDA(alloc_async(&k1, (size_t)nnz, s));
+        GB_CUDA(alloc_async(&v0, (size_t)nnz, s));
+        GB_CUDA(alloc_async(&v1, (size_t)nnz, s));
+        wsort_keys_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(g->off, g->col, g->wgt, g->n, k0, v0);
+        note_launch();
+        GB_CUDA(cudaGetLastError());
+        gb_status rc2 = radix_sort(k0, k1, v0, v1, nnz, 0, 25 + scale, &ks, &vs, s);
+        if (rc2 != GB_OK) return rc2;
+        wsort_pack_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(ks, vs, nnz, g->wadj);
+        note_launch();
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaFreeAsync(k0, s));
+        GB_CUDA(cudaFreeAsync(k1, s));
+        GB_CUDA(cudaFreeAsync(v0, s));
+        GB_CUDA(cudaFreeAsync(v1, s));
+    }
+    GB_CUDA(cudaStreamSynchronize(s));
     return GB_OK;
 }
 
@@ -658,22 +877,25 @@ gb_status sssp_impl(const gb_graph *g, int64_t root, double delta, double *dist,
 {
     Context *ctx = context();
     if (!ctx) return GB_ERR_CUDA;
-    if (!g->wgt) {
+    if (!g->wgt || !g->wadj) {
         set_error("sssp: the graph has no weights (build it with graph_build_csr_weighted)");
         return GB_ERR_INVALID;
     }
     const int64_t n = g->n;
     const int64_t bigcap = g->nnz / SP_BIG + 2;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    // header | dist | near stamps | far stamps | near queues | far lists | big lists;
-    // each pair of slots is one region, slot k at base + k * size
+    // header | dist | near, far and settle stamps | near queues | far lists |
+    // settle list | big lists (2 near slots, then the settle list's); slot k of
+    // a region at base + k * size
     const size_t o_dist = al(sizeof(SpHeader));
     const size_t o_ns = o_dist + al(8 * (size_t)n);
     const size_t o_fs = o_ns + al(4 * (size_t)n);
-    const size_t o_nq = o_fs + al(4 * (size_t)n);
+    const size_t o_ss = o_fs + al(4 * (size_t)n);
+    const size_t o_nq = o_ss + al(4 * (size_t)n);
     const size_t o_fq = o_nq + al(8 * (size_t)n);
-    const size_t o_bq = o_fq + al(8 * (size_t)n);
-    const size_t total = o_bq + al(16 * (size_t)bigcap);
+    const size_t o_sq = o_fq + al(8 * (size_t)n);
+    const size_t o_bq = o_sq + al(4 * (size_t)n);
+    const size_t total = o_bq + al(24 * (size_t)bigcap);
     unsigned char *ws = nullptr;
     GB_CUDA(cudaMallocAsync((void **)&ws, total, s));
     GB_CUDA(cudaMemsetAsync(ws, 0, sizeof(SpHeader), s));
@@ -681,13 +903,16 @@ gb_status sssp_impl(const gb_graph *g, int64_t root, double delta, double *dist,
     a.off = g->off;
     a.col = g->col;
     a.wgt = g->wgt;
+    a.wadj = g->wadj;
     a.n = n;
     a.root = (int32_t)root;
     a.dist = reinterpret_cast<unsigned long long *>(ws + o_dist);
     a.nstamp = reinterpret_cast<uint32_t *>(ws + o_ns);
     a.fstamp = reinterpret_cast<uint32_t *>(ws + o_fs);
+    a.sstamp = reinterpret_cast<uint32_t *>(ws + o_ss);
     a.nq = reinterpret_cast<int32_t *>(ws + o_nq);
     a.fq = reinterpret_cast<int32_t *>(ws + o_fq);
+    a.sq = reinterpret_cast<int32_t *>(ws + o_sq);
     a.bq = reinterpret_cast<SpBig *>(ws + o_bq);
     a.bigcap = bigcap;
     a.hdr = reinterpret_cast<SpHeader *>(ws);
@@ -697,6 +922,7 @@ gb_status sssp_impl(const gb_graph *g, int64_t root, double delta, double *dist,
     a.delta = (unsigned long long)std::max(1.0, std::min(du, 4.0e18));
     a.dist_out = dist;
     a.parent = parent;
+    a.canonical = options().canonical_parents;
     a.timeout_ns = timeout_ns();
     a.run_limit_ns = 8 * a.timeout_ns;
     a.max_rounds = (long long)1 << 31;  // round ids are 32-bit stamps
