@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 from paper_2012_13548_gb300 import workloads as W  # noqa: E402
 
 METRIC = "BFS GTEPS (harm. mean, 64 roots) plain vs batched; % HBM peak; p50/p99 ms"
+SSSP_METRIC = "SSSP GTEPS (kernel 3, harm. mean over 64 roots)"
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -44,7 +45,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="s20", choices=["s20", "s26", "s22ms", "serve6", "batch32"])
+    p.add_argument("--workload", default="s20",
+                   choices=["s20", "s26", "s22ms", "serve6", "batch32", "sssp22"])
     p.add_argument("--untuned", action="store_true", help="library defaults instead of tune_table.json")
     p.add_argument("--duration", type=float, default=3.0, help="serve6: seconds of arrivals")
     p.add_argument("--rate", type=float, default=None, help="serve6: arrivals per second")
@@ -187,10 +189,42 @@ def oracle_sample(scale, nroots, seconds):
     return harmonic_mean(rates), done, spent, (off, col, e)
 
 
+def oracle_weighted_graph(scale):
+    """The oracle's weighted graph of the workload of `scale`: (edges, off, col, wgt)."""
+    import oracle
+    spec = W.GraphSpec(scale=scale)
+    e = oracle.kron_generate(**spec.kron_args())
+    w = oracle.kron_weights(e.shape[1], spec.seed_weight())
+    off, col, wgt = oracle.csr_build_weighted(e, w, scale)
+    return e, off, col, wgt
+
+
+def oracle_sssp_sample(scale, nroots, seconds, graph=None):
+    """Time the serial oracle Dijkstra over the workload's roots until `seconds`
+    of search; returns (harmonic-mean GTEPS, roots timed, seconds spent)."""
+    import oracle
+    e, off, col, wgt = graph if graph is not None else oracle_weighted_graph(scale)
+    roots = W.select_roots(off, nroots, W.GraphSpec(scale=scale).seeds()[3])
+    rates, spent, done = [], 0.0, 0
+    for r in roots:
+        t0 = time.perf_counter()
+        d, _ = oracle.sssp(off, col, wgt, int(r))
+        dt = time.perf_counter() - t0
+        lev = np.where(np.isfinite(d), 0, -1).astype(np.int32)
+        rates.append(oracle.teps_edges(e, lev) / dt / 1e9)
+        spent += dt
+        done += 1
+        if spent >= seconds:
+            break
+    return harmonic_mean(rates), done, spent
+
+
 def run_reference(args, dist):
     if dist.rank != 0:
         return
     wl = W.WORKLOADS[args.workload]
+    if args.workload == "sssp22":
+        return run_reference_sssp(args, wl)
     scale = wl["scale"]
     import oracle
     spec = W.GraphSpec(scale=scale)
@@ -225,6 +259,55 @@ def run_reference(args, dist):
                              "sample": sample},
             "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def run_reference_sssp(args, wl):
+    """The oracle's Dijkstra as the reference arm of the kernel-3 workload: each
+    step searches from the next few roots of the same graph."""
+    import oracle
+    scale = wl["scale"]
+    e, off, col, wgt = oracle_weighted_graph(scale)
+    roots = W.select_roots(off, args.roots, W.GraphSpec(scale=scale).seeds()[3])
+    per_step = 2
+    rates, step_times = [], []
+    i = 0
+    for s in range(args.warmup + args.steps):
+        t_step = 0.0
+        for _ in range(per_step):
+            r = int(roots[i % len(roots)])
+            i += 1
+            t0 = time.perf_counter()
+            d, _ = oracle.sssp(off, col, wgt, r)
+            dt = time.perf_counter() - t0
+            t_step += dt
+            if s >= args.warmup:
+                lev = np.where(np.isfinite(d), 0, -1).astype(np.int32)
+                rates.append(oracle.teps_edges(e, lev) / dt / 1e9)
+        if s >= args.warmup:
+            step_times.append(t_step)
+    v = harmonic_mean(rates)
+    sample = ("serial C oracle Dijkstra (binary heap) on the SCALE %d weighted graph (oracle-built), "
+              "%d roots per step, %d timed steps" % (scale, per_step, args.steps))
+    print(json.dumps({
+        "impl": "reference", "metric": SSSP_METRIC, "value": v, "unit": "GTEPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(step_times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": sssp_config(args, wl),
+        "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def sssp_config(args, wl):
+    scale = wl["scale"]
+    return {"workload": "graph500-kernel3-sssp-kronecker-scale%d-ef16-%droots" % (scale, args.roots),
+            "scale": scale, "edgefactor": W.EDGEFACTOR,
+            "initiator": [W.A, W.B, W.C, round(1 - W.A - W.B - W.C, 2)],
+            "weights": "multiples of 2^-24 in (0, 1], SplitMix64 weight row",
+            "roots": args.roots, "delta": wl["delta"],
+            "parents": "canonical" if args.canonical else "any-valid",
+            "l2": "flushed before every timed call (256 MB write)",
+            "step": "%d single-source shortest-path searches" % args.roots}
 
 
 def workload_config(args, scale):
@@ -459,14 +542,14 @@ def read_traffic(scale):
     return int(kv["bytes_per_launch"])
 
 
-def kernel_source_hash():
-    """Hash of the single-source kernel's code (bfs.cu, common.cuh) with comments
-    and whitespace removed: a traffic summary stays valid across comment edits
-    and is dropped by any change to the code itself."""
+def kernel_source_hash(main="bfs.cu"):
+    """Hash of a kernel's code (its file, bfs.cu by default, and common.cuh) with
+    comments and whitespace removed: a traffic summary stays valid across
+    comment edits and is dropped by any change to the code itself."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("bfs.cu", "common.cuh"):
+    for f in (main, "common.cuh"):
         src = open(os.path.join(ROOT, "paper_2012_13548_gb300", "csrc", f)).read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
@@ -515,6 +598,199 @@ def run_e2e(args, gb, torch, edges, scale, roots, m_r, dist):
     return {"value": harmonic_mean(all_rates) * dist.world, "unit": "GTEPS",
             "h2d_bytes_per_step": int(h_edges.numel() * 8),
             "d2h_bytes_per_step": int(k * 2 * n * 4)}
+
+
+# ---------------------------------------------------------------------------
+# Kernel 3 workload: single-source shortest paths from 64 roots
+# ---------------------------------------------------------------------------
+
+def sssp_bytes(st, n):
+    """Algorithmic bytes of one search: 16 per edge relaxed (its 8-byte
+    (column, weight) pair and the 8-byte distance of its endpoint), 24 per
+    expansion (two offsets and the vertex's own distance), 32 per vertex (the
+    distance and three stamps initialised, the distance and parent written)."""
+    return 16 * st["scanned"] + 24 * st["processed"] + 32 * n
+
+
+def run_sssp(args, dist):
+    import torch
+    import paper_2012_13548_gb300 as gb
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    stream = torch.cuda.current_stream()
+    wl = W.WORKLOADS["sssp22"]
+    scale, delta = wl["scale"], wl["delta"]
+    spec = W.GraphSpec(scale=scale)
+    gb.bfs_set_options(canonical_parents=args.canonical)
+    edges = gb.kron_generate(**spec.kron_args())             # inputs: generated, untimed
+    w = gb.kron_weights(edges.shape[1], spec.seed_weight())
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    a, b = ev(), ev()
+    a.record(stream)
+    g = gb.graph_build_csr_weighted(edges, w, scale)         # kernel 1 with weights
+    b.record(stream)
+    b.synchronize()
+    k1_ms = a.elapsed_time(b)
+    off, _ = g.csr()
+    all_roots = W.select_roots(off.cpu().numpy(), args.roots * dist.world, spec.seeds()[3])
+    roots = shard_roots(all_roots, dist.rank, dist.world, args.roots)
+    n = g.n
+    dist_t = torch.empty(n, dtype=torch.float64, device=dev)
+    par = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    # TEPS numerators, counters and the device validation of every root's tree
+    m_r, stats, invalid = [], [], []
+    for r in roots:
+        gb.sssp(g, int(r), delta, dist_t, par)
+        stats.append(gb.sssp_last_stats())
+        v = gb.sssp_validate(g, int(r), par, dist_t, edges)
+        m_r.append(v["teps_edges"])
+        if v["code"] != 0:
+            invalid.append((int(r), v["code"], v["where"]))
+    gb.gb_device_status()
+
+    def step(rec):
+        per = []
+        for r in roots:
+            flush.fill_(2)
+            x, y = ev(), ev()
+            x.record(stream)
+            gb.sssp(g, int(r), delta, dist_t, par)
+            y.record(stream)
+            per.append((x, y))
+        rec.append(per)
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    launches0 = gb.gb_kernel_launches()
+    t0, t1 = ev(), ev()
+    rec = []
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(rec)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    launches = gb.gb_kernel_launches() - launches0
+    clk = clocks.stop()
+    gb.gb_device_status()
+    # the last timed search's tree validated too
+    last = gb.sssp_validate(g, int(roots[-1]), par, dist_t)
+    if last["code"] != 0:
+        invalid.append((int(roots[-1]), last["code"], last["where"]))
+    ms = [[x.elapsed_time(y) for (x, y) in per] for per in rec]
+    rates = [m_r[i] / (t[i] * 1e-3) / 1e9 for t in ms for i in range(len(roots))]
+    hm = harmonic_mean(dist.gather(rates))
+    flat = dist.gather([x for t in ms for x in t])
+    peaks = load_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    alg = statistics.mean(sssp_bytes(st, n) for st in stats)
+    achieved = alg / (statistics.mean(flat) * 1e-3) / 1e9
+    e2e = None if args.no_e2e else run_sssp_e2e(args, gb, torch, edges, w, scale, delta, roots, m_r, dist)
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cs = 20   # the serial oracle builds larger weighted graphs too slowly
+        v, done, spent = oracle_sssp_sample(cs, len(all_roots), args.cpu_seconds)
+        cpu = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": "serial C oracle Dijkstra (binary heap) on the SCALE %d weighted graph of "
+                         "the same recipe, rebuilt by the oracle, first %d of its %d roots (%.1f s)"
+                         % (cs, done, len(all_roots), spent)}
+    if dist.rank == 0:
+        print(json.dumps({
+            "metric": SSSP_METRIC, "value": hm * dist.world, "unit": "GTEPS", "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dist.max(t0.elapsed_time(t1) / args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": sssp_config(args, wl),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": read_sssp_traffic(scale),
+                         "kernel": "sssp_kernel (persistent, one launch per root)",
+                         "peak_source": "measured" if peaks else "fallback"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "latency_ms": {"p50": float(np.percentile(flat, 50)), "p99": float(np.percentile(flat, 99))},
+            "kernel1_weighted_ms": k1_ms,
+            "validation": {"on": "device (sssp_validate, rules 1-7)", "trees": len(roots) + 1,
+                           "invalid": invalid[:4], "n_invalid": len(invalid)},
+            "search": {"mean_rounds": statistics.mean(st["rounds"] for st in stats),
+                       "mean_buckets": statistics.mean(st["buckets"] for st in stats),
+                       "mean_scanned": statistics.mean(st["scanned"] for st in stats),
+                       "mean_processed": statistics.mean(st["processed"] for st in stats),
+                       "mean_phase_ms": [statistics.mean(st["phase_ns"][k] for st in stats) / 1e6
+                                         for k in range(4)]},
+            "graph": {"n": n, "nnz": g.nnz, "m": int(edges.shape[1])}}))
+    g.free()
+
+
+def run_sssp_e2e(args, gb, torch, edges, w, scale, delta, roots, m_r, dist):
+    """Kernel 3 end to end: per step the tuples and weights go host->device
+    from pinned memory, kernel 1 builds the weighted graph, and every root's
+    distances and parents come back device->host.  A root's time is its search
+    plus its copy back plus 1/k of the upload and the build."""
+    stream = torch.cuda.current_stream()
+    h_edges = edges.cpu().pin_memory()
+    h_w = w.cpu().pin_memory()
+    n = 1 << scale
+    d_edges, d_w = torch.empty_like(edges), torch.empty_like(w)
+    dist_t = torch.empty(n, dtype=torch.float64, device=edges.device)
+    par = torch.empty(n, dtype=torch.int32, device=edges.device)
+    h_d = torch.empty(n, dtype=torch.float64).pin_memory()
+    h_p = torch.empty(n, dtype=torch.int32).pin_memory()
+    k = len(roots)
+    rates = []
+    steps = max(1, min(args.steps, 2))
+    for s in range(1 + steps):
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        d_edges.copy_(h_edges, non_blocking=True)
+        d_w.copy_(h_w, non_blocking=True)
+        g = gb.graph_build_csr_weighted(d_edges, d_w, scale)
+        a1.record(stream)
+        per = []
+        for r in roots:
+            b0, b1 = ev(), ev()
+            b0.record(stream)
+            gb.sssp(g, int(r), delta, dist_t, par)
+            h_d.copy_(dist_t, non_blocking=True)
+            h_p.copy_(par, non_blocking=True)
+            b1.record(stream)
+            per.append((b0, b1))
+        torch.cuda.synchronize()
+        if s >= 1:
+            share = a0.elapsed_time(a1) / k
+            rates += [m_r[i] / ((per[i][0].elapsed_time(per[i][1]) + share) * 1e-3) / 1e9
+                      for i in range(k)]
+        g.free()
+    return {"value": harmonic_mean(dist.gather(rates)) * dist.world, "unit": "GTEPS",
+            "h2d_bytes_per_step": int(h_edges.numel() * 8 + h_w.numel() * 4),
+            "d2h_bytes_per_step": int(k * n * 12)}
+
+
+def read_sssp_traffic(scale):
+    """DRAM bytes per sssp_kernel launch from the committed ncu summary, if it
+    was taken at this SCALE on the current source of the kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "sssp_kernel_s%d_traffic.txt" % scale)
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != kernel_source_hash("sssp.cu"):
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 # ---------------------------------------------------------------------------
@@ -716,6 +992,8 @@ def main():
             run_serve(args, dist)
         elif args.workload == "batch32":
             run_batch32(args, dist)
+        elif args.workload == "sssp22":
+            run_sssp(args, dist)
         else:
             run_ours(args, dist)
     finally:

@@ -4,6 +4,7 @@
   python -m paper_2012_13548_gb300.profile_case --kernel msbfs --scale 20 --roots 64
   python -m paper_2012_13548_gb300.profile_case --kernel k1 --scale 22
   python -m paper_2012_13548_gb300.profile_case --kernel k1counting --scale 26
+  python -m paper_2012_13548_gb300.profile_case --kernel sssp --scale 22 --roots 3
 
 It generates the Kronecker graph of the given SCALE on the device, builds the
 CSR and then runs the chosen kernel a few times, holding nothing else on the
@@ -19,13 +20,14 @@ from . import workloads as W
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--kernel", choices=["bfs", "msbfs", "k1", "k1counting"], default="bfs")
+    p.add_argument("--kernel", choices=["bfs", "msbfs", "k1", "k1counting", "sssp"], default="bfs")
     p.add_argument("--scale", type=int, default=22)
     p.add_argument("--roots", type=int, default=3)
     p.add_argument("--canonical", type=int, default=0)
     p.add_argument("--alpha", type=float, default=None)
     p.add_argument("--beta", type=float, default=None)
     p.add_argument("--blocks-per-sm", type=int, default=None)
+    p.add_argument("--delta", type=float, default=0.1, help="sssp: bucket width")
     p.add_argument("--tuned", action="store_true",
                    help="apply tune_table.json's options for this SCALE first (as bench.py does)")
     a = p.parse_args()
@@ -64,6 +66,16 @@ def main():
         for _ in range(2):
             gb.bfs_batch(g, roots, P, L)
             print(gb.bfs_last_stats())
+    elif a.kernel == "sssp":
+        g.free()
+        w = gb.kron_weights(edges.shape[1], spec.seed_weight())
+        gw = gb.graph_build_csr_weighted(edges, w, a.scale)
+        dist = torch.empty(gw.n, dtype=torch.float64, device="cuda")
+        parent = torch.empty(gw.n, dtype=torch.int32, device="cuda")
+        for r in roots:
+            gb.sssp(gw, r, a.delta, dist, parent)
+            print("root %d" % r, gb.sssp_last_stats())
+        gw.free()
     else:
         g.free()
         build = gb.graph_build_csr if a.kernel == "k1" else gb.graph_build_csr_counting

@@ -15,6 +15,8 @@ Workloads (Graph500 Kronecker graphs, Sec. 2.1 of the paper: #V = 2^scale,
   s22ms    SCALE 22, 64 roots in one multi-source launch
   batch32  32 graphs, SCALE uniform in 12..18, 8 roots each, one launch
   serve6   6 resident graphs SCALE 14..24, Poisson 5000 req/s
+  sssp22   kernel 3: SCALE 22 with the weight row, 64 roots, single-source
+           shortest paths (Sec. 2.4)
 """
 from dataclasses import dataclass
 
@@ -72,6 +74,7 @@ WORKLOADS = {
     "s22ms": dict(scale=22, roots=64),
     "batch32": dict(graphs=32, scale_lo=12, scale_hi=18, roots=8),
     "serve6": dict(scales=(14, 16, 18, 20, 22, 24), rate=5000.0),
+    "sssp22": dict(scale=22, roots=64, delta=0.1),
 }
 
 

@@ -49,3 +49,23 @@ def test_shard_roots_gives_disjoint_blocks():
 def test_harmonic_mean():
     assert bench.harmonic_mean([1.0, 1.0]) == pytest.approx(1.0)
     assert bench.harmonic_mean([1.0, 3.0]) == pytest.approx(1.5)
+
+
+def test_sssp_traffic_summary_follows_the_kernel_source(tmp_path, monkeypatch):
+    path = os.path.join(ROOT, "profiles", "sssp_kernel_s22_traffic.txt")
+    assert os.path.exists(path)
+    h = bench.kernel_source_hash("sssp.cu")
+    assert len(h) == 16 and h != bench.kernel_source_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "sssp_kernel_s22_traffic.txt").write_text(
+        "# comment\nscale = 22\ndram_bytes_per_launch = 777\nsource_hash = %s\n" % h)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda main="bfs.cu": h if main == "sssp.cu" else "x")
+    assert bench.read_sssp_traffic(22) == 777
+    assert bench.read_sssp_traffic(20) is None
+
+
+def test_sssp_algorithmic_bytes():
+    st = {"scanned": 10, "processed": 3}
+    assert bench.sssp_bytes(st, 4) == 16 * 10 + 24 * 3 + 32 * 4
