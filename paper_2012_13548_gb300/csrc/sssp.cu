@@ -256,6 +256,26 @@ __device__ __forceinline__ void push_settle(const SpArgs &a, bool want, int32_t 
     }
 }
 
+// The weight-sorted rows are a stream (each entry read about once by a light
+// prefix and once by a settle step): they are loaded with an L2 evict-first
+// policy and no L1 allocation, so that they do not push the distance array
+// and the stamps, which every relaxation reads at random, out of L2.
+__device__ __forceinline__ uint64_t stream_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint2 ld_stream(const uint2 *p, uint64_t pol)
+{
+    uint2 r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(r.x), "=r"(r.y)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+
 // First index j in [lo, hi) of a weight-sorted row with weight >= lim (hi if none).
 __device__ __forceinline__ int64_t weight_split(const uint2 *__restrict__ wadj, int64_t lo, int64_t hi,
                                                 unsigned long long lim)
@@ -328,6 +348,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
     unsigned bar = grid_barrier_base(&h->bar);
     unsigned long long processed = 0, scanned = 0, won = 0, reached = 0;
     const uint64_t t_start = globaltimer_ns();
+    const uint64_t pol = stream_policy();
 
     // ---- init: every distance infinite but the root's; the root queued
     for (int64_t v = gtid; v < n; v += gthreads) {
@@ -395,7 +416,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
             for (int64_t j0 = s0; j0 < e0; j0 += 32) {
                 const int64_t j = j0 + lane;
                 uint2 cw = make_uint2(0u, 0u);
-                if (j < e0) cw = a.wadj[j];
+                if (j < e0) cw = ld_stream(a.wadj + j, pol);
                 const bool valid = j < e0 && (unsigned long long)cw.y < lim;
                 scanned += valid;
                 relax(a, valid, be.u, (int32_t)cw.x, du + cw.y, T, qnext, epoch, won);
@@ -438,7 +459,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
                 const int32_t uo = __shfl_sync(kFull, u, owner);
                 const bool valid = k < total;
                 uint2 cw = make_uint2(0u, 0u);
-                if (valid) cw = a.wadj[so + (k - eo)];
+                if (valid) cw = ld_stream(a.wadj + so + (k - eo), pol);
                 relax(a, valid, uo, (int32_t)cw.x, duo + cw.y, T, qnext, epoch, won);
             }
         }
@@ -469,7 +490,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
                 for (int64_t j0 = s0; j0 < e0; j0 += 32) {
                     const int64_t j = j0 + lane;
                     uint2 cw = make_uint2(0u, 0u);
-                    if (j < e0) cw = a.wadj[j];
+                    if (j < e0) cw = ld_stream(a.wadj + j, pol);
                     const bool valid = j < e0 && (unsigned long long)cw.y >= lim;
                     scanned += valid;
                     relax(a, valid, be.u, (int32_t)cw.x, du + cw.y, T, qnext, e, won);
@@ -507,7 +528,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
                     const int32_t uo = __shfl_sync(kFull, u, owner);
                     const bool valid = k < total;
                     uint2 cw = make_uint2(0u, 0u);
-                    if (valid) cw = a.wadj[so + (k - eo)];
+                    if (valid) cw = ld_stream(a.wadj + so + (k - eo), pol);
                     relax(a, valid, uo, (int32_t)cw.x, duo + cw.y, T, qnext, e, won);
                 }
             }

@@ -1,8 +1,10 @@
 """Full-size checks that need no oracle run: at SCALE 24 (and SCALE 26 when
 GB_TEST_S26=1) the CSR must satisfy the Sec. 2.2 invariants and every BFS
 result must pass the Graph500 rules, which together force the levels to be
-the exact hop distances.  The properties are computed here with plain torch
-tensor operations, independently of the library."""
+the exact hop distances.  At SCALE 22 (the kernel-3 bench size) every
+shortest-path result must be tight along its tree and relaxed over every
+edge, which forces the exact distances.  The properties are computed here
+with plain torch tensor operations, independently of the library."""
 import os
 
 import pytest
@@ -80,3 +82,52 @@ def test_full_size_csr_and_bfs_properties(scale):
         tree_properties(off, col, rows, key, n, int(r), P[i], L[i])
     gb.gb_device_status()
     del e0
+
+
+def test_full_size_sssp_properties():
+    scale = 22
+    spec = W.GraphSpec(scale=scale)
+    edges = gb.kron_generate(**spec.kron_args())
+    w = gb.kron_weights(edges.shape[1], spec.seed_weight())
+    g = gb.graph_build_csr_weighted(edges, w, scale)
+    off, col = g.csr()
+    n = g.n
+    rows, key = csr_properties(off, col, n)
+    wt = g.weights().to(torch.float64) * 2.0 ** -24
+    # each entry's weight is the least weight of the tuples joining its pair
+    keep = edges[0] != edges[1]
+    tk = torch.cat([edges[0][keep] * n + edges[1][keep], edges[1][keep] * n + edges[0][keep]])
+    tw = torch.cat([w[keep], w[keep]]).to(torch.float64)
+    least = torch.full((key.numel(),), 2.0, dtype=torch.float64, device="cuda")
+    least.scatter_reduce_(0, torch.searchsorted(key, tk), tw, reduce="amin")
+    assert torch.equal(least, wt)
+    del tk, tw, least
+    roots = W.select_roots(off.cpu().numpy(), 3, spec.seeds()[3])
+    for canonical in (0, 1):
+        gb.bfs_set_options(canonical_parents=canonical)
+        for r in roots:
+            dist, par = gb.sssp(g, int(r), 0.1)
+            gb.gb_device_status()
+            r = int(r)
+            assert float(dist[r]) == 0.0 and int(par[r]) == r
+            reached = torch.isfinite(dist)
+            assert bool(((par == -1) == ~reached).all())
+            du, dv = dist[rows.long()], dist[col.long()]
+            assert bool((reached[rows.long()] == reached[col.long()]).all()), "edge leaves the reached set"
+            m = reached[rows.long()]
+            assert bool((dv[m] <= du[m] + wt[m]).all()), "an edge still relaxes"
+            v = torch.nonzero(reached).flatten()
+            v = v[v != r]
+            p = par[v].long()
+            pk = v * n + p
+            pos = torch.searchsorted(key, pk).clamp(max=key.numel() - 1)
+            assert bool((key[pos] == pk).all()), "parent is not a neighbour"
+            assert bool((dist[p] + wt[pos] == dist[v]).all()), "tree edge not tight"
+            if canonical:  # no smaller-id neighbour is tight
+                first = torch.full((n,), n, dtype=torch.int64, device="cuda")
+                cand = (dist[rows.long()] + wt == dist[col.long()]) & reached[col.long()]
+                first.scatter_reduce_(0, col.long()[cand], rows.long()[cand], reduce="amin")
+                assert torch.equal(first[v], p)
+                del first, cand
+    gb.bfs_set_options(canonical_parents=0)
+    g.free()

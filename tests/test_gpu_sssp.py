@@ -215,3 +215,13 @@ def test_sssp_validator_matches_the_oracle_on_planted_mistakes():
     assert gb.sssp_validate(G, len(tree), torch.as_tensor(tree).cuda(),
                             torch.as_tensor(d_ref).cuda())["code"] == 7
     G.free()
+
+
+def test_sssp_scale20_sampled_root_equals_dijkstra():
+    # the bench's launch configuration on a graph the oracle still finishes in seconds
+    e, w, G = gpu_weighted(20)
+    _, _, off, col, wgt = oracle_weighted(20)
+    r = roots_for(20, 1)[0]
+    for canonical in (0, 1):
+        check_search(G, off, col, wgt, r, 0.1, edges=e, canonical=canonical)
+    G.free()
