@@ -316,14 +316,15 @@ __device__ __forceinline__ void push_far(const SpArgs &a, unsigned epoch, bool w
     else record_error(a.st, GB_ERR_RANGE, SITE_SP_FAR, pos);
 }
 
-// Warp-collective relaxation of one edge per lane: dist(v) lowered to nd if
-// smaller; a lowered v is queued near (nd < T) or listed far.
-__device__ __forceinline__ void relax(const SpArgs &a, bool valid, int32_t u, int32_t v,
-                                      unsigned long long nd, unsigned long long T, unsigned qnext,
-                                      unsigned epoch, unsigned long long &won)
+// Warp-collective relaxation of one edge per lane whose distance test has
+// been made: dist(v) lowered to nd if still smaller; a lowered v is queued
+// near (nd < T) or listed far.
+__device__ __forceinline__ void relax_tail(const SpArgs &a, bool cand, int32_t u, int32_t v,
+                                           unsigned long long nd, unsigned long long T, unsigned qnext,
+                                           unsigned epoch, unsigned long long &won)
 {
     bool to_near = false, to_far = false;
-    if (valid && nd < __ldcg(&a.dist[v])) {
+    if (cand) {
         const unsigned long long old = atomicMin(&a.dist[v], nd);
         if (nd < old) {
             ++won;
@@ -334,6 +335,57 @@ __device__ __forceinline__ void relax(const SpArgs &a, bool valid, int32_t u, in
     }
     push_near(a, qnext, to_near, v);
     push_far(a, epoch, to_far, v);
+}
+
+// Two edges per lane: both endpoint distances are read before either atomic,
+// so that a warp keeps twice the random reads in flight.
+__device__ __forceinline__ void relax2(const SpArgs &a, bool ok0, int32_t u0, uint2 c0,
+                                       unsigned long long d0, bool ok1, int32_t u1, uint2 c1,
+                                       unsigned long long d1, unsigned long long T, unsigned qnext,
+                                       unsigned epoch, unsigned long long &won)
+{
+    const unsigned long long nd0 = d0 + c0.y, nd1 = d1 + c1.y;
+    const unsigned long long cur0 = ok0 ? __ldcg(&a.dist[c0.x]) : 0ull;
+    const unsigned long long cur1 = ok1 ? __ldcg(&a.dist[c1.x]) : 0ull;
+    relax_tail(a, ok0 && nd0 < cur0, u0, (int32_t)c0.x, nd0, T, qnext, epoch, won);
+    relax_tail(a, ok1 && nd1 < cur1, u1, (int32_t)c1.x, nd1, T, qnext, epoch, won);
+}
+
+// The row of stream slot k of a warp's 32-row edge stream (the lane whose
+// exclusive prefix is the largest <= k).
+__device__ __forceinline__ int stream_owner(int64_t excl, int64_t k)
+{
+    int owner = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int cand = owner + step;
+        if (__shfl_sync(kFull, excl, cand) <= k) owner = cand;
+    }
+    return owner;
+}
+
+// Warp-collective: relax the edges [so + (k - eo)] of a 32-row stream of
+// `total` slots (row starts s0, exclusive prefixes excl, distances du, ids u),
+// two slots per lane per step.
+__device__ __forceinline__ void relax_stream(const SpArgs &a, uint64_t pol, int64_t total, int64_t s0,
+                                             int64_t excl, unsigned long long du, int32_t u,
+                                             unsigned long long T, unsigned qnext, unsigned epoch,
+                                             unsigned long long &won)
+{
+    const unsigned lane = lane_id();
+    for (int64_t b = 0; b < total; b += 64) {
+        const int64_t k0 = b + lane, k1 = b + 32 + lane;
+        const int o0 = stream_owner(excl, k0), o1 = stream_owner(excl, k1);
+        const int64_t so0 = __shfl_sync(kFull, s0, o0), eo0 = __shfl_sync(kFull, excl, o0);
+        const int64_t so1 = __shfl_sync(kFull, s0, o1), eo1 = __shfl_sync(kFull, excl, o1);
+        const unsigned long long du0 = __shfl_sync(kFull, du, o0), du1 = __shfl_sync(kFull, du, o1);
+        const int32_t u0 = __shfl_sync(kFull, u, o0), u1 = __shfl_sync(kFull, u, o1);
+        const bool ok0 = k0 < total, ok1 = k1 < total;
+        uint2 c0 = make_uint2(0u, 0u), c1 = make_uint2(0u, 0u);
+        if (ok0) c0 = ld_stream(a.wadj + so0 + (k0 - eo0), pol);
+        if (ok1) c1 = ld_stream(a.wadj + so1 + (k1 - eo1), pol);
+        relax2(a, ok0, u0, c0, du0, ok1, u1, c1, du1, T, qnext, epoch, won);
+    }
 }
 
 __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
@@ -413,14 +465,16 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
             const unsigned long long du = __ldcg(&a.dist[be.u]);
             const unsigned long long lim = T - du;
             if ((unsigned long long)a.wadj[s0].y >= lim) continue;  // the chunk is all heavy
-            for (int64_t j0 = s0; j0 < e0; j0 += 32) {
+            for (int64_t j0 = s0; j0 < e0; j0 += 64) {
                 const int64_t j = j0 + lane;
-                uint2 cw = make_uint2(0u, 0u);
-                if (j < e0) cw = ld_stream(a.wadj + j, pol);
-                const bool valid = j < e0 && (unsigned long long)cw.y < lim;
-                scanned += valid;
-                relax(a, valid, be.u, (int32_t)cw.x, du + cw.y, T, qnext, epoch, won);
-                if (!__any_sync(kFull, valid)) break;  // past the split
+                uint2 c0 = make_uint2(0u, 0u), c1 = make_uint2(0u, 0u);
+                if (j < e0) c0 = ld_stream(a.wadj + j, pol);
+                if (j + 32 < e0) c1 = ld_stream(a.wadj + j + 32, pol);
+                const bool ok0 = j < e0 && (unsigned long long)c0.y < lim;
+                const bool ok1 = j + 32 < e0 && (unsigned long long)c1.y < lim;
+                scanned += ok0 + ok1;
+                relax2(a, ok0, be.u, c0, du, ok1, be.u, c1, du, T, qnext, epoch, won);
+                if (!__any_sync(kFull, ok1)) break;  // past the split
             }
         }
         // ---- every queue entry: listed for its bucket's settle step once; the
@@ -444,24 +498,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
             push_settle(a, first, u, deg);
             const int64_t incl = warp_inclusive_scan(d);
             const int64_t total = __shfl_sync(kFull, incl, 31);
-            const int64_t excl = incl - d;
-            for (int64_t b = 0; b < total; b += 32) {
-                const int64_t k = b + lane;
-                int owner = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int cand = owner + step;
-                    if (__shfl_sync(kFull, excl, cand) <= k) owner = cand;
-                }
-                const int64_t so = __shfl_sync(kFull, s0, owner);
-                const int64_t eo = __shfl_sync(kFull, excl, owner);
-                const unsigned long long duo = __shfl_sync(kFull, du, owner);
-                const int32_t uo = __shfl_sync(kFull, u, owner);
-                const bool valid = k < total;
-                uint2 cw = make_uint2(0u, 0u);
-                if (valid) cw = ld_stream(a.wadj + so + (k - eo), pol);
-                relax(a, valid, uo, (int32_t)cw.x, duo + cw.y, T, qnext, epoch, won);
-            }
+            relax_stream(a, pol, total, s0, incl - d, du, u, T, qnext, epoch, won);
         }
         if (!grid_sync(&h->bar, bar, a.st, a.timeout_ns, SITE_SP_BAR)) return;
         phase_end(0);
@@ -487,13 +524,15 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
                 const unsigned long long du = __ldcg(&a.dist[be.u]);
                 const unsigned long long lim = T - du;
                 if ((unsigned long long)a.wadj[e0 - 1].y < lim) continue;  // the chunk is all light
-                for (int64_t j0 = s0; j0 < e0; j0 += 32) {
+                for (int64_t j0 = s0; j0 < e0; j0 += 64) {
                     const int64_t j = j0 + lane;
-                    uint2 cw = make_uint2(0u, 0u);
-                    if (j < e0) cw = ld_stream(a.wadj + j, pol);
-                    const bool valid = j < e0 && (unsigned long long)cw.y >= lim;
-                    scanned += valid;
-                    relax(a, valid, be.u, (int32_t)cw.x, du + cw.y, T, qnext, e, won);
+                    uint2 c0 = make_uint2(0u, 0u), c1 = make_uint2(0u, 0u);
+                    if (j < e0) c0 = ld_stream(a.wadj + j, pol);
+                    if (j + 32 < e0) c1 = ld_stream(a.wadj + j + 32, pol);
+                    const bool ok0 = j < e0 && (unsigned long long)c0.y >= lim;
+                    const bool ok1 = j + 32 < e0 && (unsigned long long)c1.y >= lim;
+                    scanned += ok0 + ok1;
+                    relax2(a, ok0, be.u, c0, du, ok1, be.u, c1, du, T, qnext, e, won);
                 }
             }
             for (int64_t i0 = gwarp * 32; i0 < ns; i0 += nwarps * 32) {
@@ -513,24 +552,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MINB) sssp_kernel(SpArgs a)
                 }
                 const int64_t incl = warp_inclusive_scan(d);
                 const int64_t total = __shfl_sync(kFull, incl, 31);
-                const int64_t excl = incl - d;
-                for (int64_t b = 0; b < total; b += 32) {
-                    const int64_t k = b + lane;
-                    int owner = 0;
-#pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const int cand = owner + step;
-                        if (__shfl_sync(kFull, excl, cand) <= k) owner = cand;
-                    }
-                    const int64_t so = __shfl_sync(kFull, s0, owner);
-                    const int64_t eo = __shfl_sync(kFull, excl, owner);
-                    const unsigned long long duo = __shfl_sync(kFull, du, owner);
-                    const int32_t uo = __shfl_sync(kFull, u, owner);
-                    const bool valid = k < total;
-                    uint2 cw = make_uint2(0u, 0u);
-                    if (valid) cw = ld_stream(a.wadj + so + (k - eo), pol);
-                    relax(a, valid, uo, (int32_t)cw.x, duo + cw.y, T, qnext, e, won);
-                }
+                relax_stream(a, pol, total, s0, incl - d, du, u, T, qnext, e, won);
             }
         }
         if (!grid_sync(&h->bar, bar, a.st, a.timeout_ns, SITE_SP_BAR)) return;
