@@ -621,6 +621,9 @@ def run_sssp(args, dist):
     stream = torch.cuda.current_stream()
     wl = W.WORKLOADS["sssp22"]
     scale, delta = wl["scale"], wl["delta"]
+    if not args.untuned:
+        from paper_2012_13548_gb300 import autotune
+        delta = autotune.tuned_options("sssp", scale).get("delta", delta)
     spec = W.GraphSpec(scale=scale)
     gb.bfs_set_options(canonical_parents=args.canonical)
     edges = gb.kron_generate(**spec.kron_args())             # inputs: generated, untimed
@@ -709,7 +712,8 @@ def run_sssp(args, dist):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dist.max(t0.elapsed_time(t1) / args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": sssp_config(args, wl),
+            "config": dict(sssp_config(args, wl), delta=delta,
+                           options="tune_table.json" if not args.untuned else "workload default"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": read_sssp_traffic(scale),
                          "kernel": "sssp_kernel (persistent, one launch per root)",

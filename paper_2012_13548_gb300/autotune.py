@@ -16,9 +16,12 @@ kinds are tuned:
   batched     bfs_batch() with 64 roots: ms_alpha, ms_beta
   multigraph  bfs_multi_graph() over 32 graphs of SCALE 12..18, 8 roots each:
               ms_alpha, ms_beta
+  sssp        sssp() on the weighted graph (--sssp): the bucket width delta, an
+              argument of the call rather than a library option, scored by
+              the mean time over 16 roots
 
-The table maps "plain/<scale>", "batched/<scale>" and "multigraph" to option
-dicts; apply_tuned() loads the entry closest in SCALE.
+The table maps "plain/<scale>", "batched/<scale>", "sssp/<scale>" and
+"multigraph" to option dicts; apply_tuned() loads the entry closest in SCALE.
 """
 import argparse
 import json
@@ -37,6 +40,9 @@ PLAIN_SPACE = {
 MS_SPACE = {
     "ms_alpha": [1.0, 4.0, 16.0, 64.0, 256.0],
     "ms_beta": [2.0, 8.0, 32.0, 128.0],
+}
+SSSP_SPACE = {
+    "delta": [0.03, 0.05, 0.075, 0.1, 0.125, 0.15, 0.2, 0.3],
 }
 
 
@@ -125,6 +131,32 @@ def tune_scale(scale, roots=8, kinds=("plain", "batched")):
     return out
 
 
+def tune_sssp(scale, roots=16, start_delta=0.1):
+    """The bucket width of sssp() on the weighted graph of `scale`."""
+    import torch
+    from . import binding as gb
+    from . import workloads as W
+
+    spec = W.GraphSpec(scale=scale)
+    edges = gb.kron_generate(**spec.kron_args())
+    w = gb.kron_weights(edges.shape[1], spec.seed_weight())
+    g = gb.graph_build_csr_weighted(edges, w, scale)
+    del edges, w
+    off, _ = g.csr()
+    rs = [int(r) for r in W.select_roots(off.cpu().numpy(), roots, spec.seeds()[3])]
+    timed = _timer(torch)
+    dist = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
+
+    def ev(opts):
+        gb.sssp(g, rs[0], opts["delta"], dist, parent)   # warm-up
+        return statistics.mean(timed(lambda r=r: gb.sssp(g, r, opts["delta"], dist, parent))
+                                for r in rs)
+    best, t, _ = descend(ev, SSSP_SPACE, {"delta": start_delta}, passes=1)
+    g.free()
+    return {"sssp/%d" % scale: dict(best, mean_ms=round(t, 4))}
+
+
 def tune_multigraph(count=32, lo=12, hi=18, r=8):
     import torch
     from . import binding as gb
@@ -161,8 +193,8 @@ def load_table(path=DEFAULT_TABLE):
 
 
 def tuned_options(kind, scale=None, path=DEFAULT_TABLE):
-    """The tuned option dict for `kind` ("plain", "batched", "multigraph") at
-    the nearest tuned SCALE, or {} if the table has none."""
+    """The tuned option dict for `kind` ("plain", "batched", "multigraph",
+    "sssp") at the nearest tuned SCALE, or {} if the table has none."""
     table = load_table(path)
     if kind == "multigraph":
         ent = table.get("multigraph", {})
@@ -189,11 +221,12 @@ def main():
     p.add_argument("--scales", type=int, nargs="+", default=[20, 22])
     p.add_argument("--roots", type=int, default=8)
     p.add_argument("--multigraph", action="store_true")
+    p.add_argument("--sssp", action="store_true", help="tune sssp()'s bucket width instead of BFS")
     p.add_argument("--out", default=DEFAULT_TABLE)
     a = p.parse_args()
     table = load_table(a.out)
     for s in a.scales:
-        res = tune_scale(s, a.roots)
+        res = tune_sssp(s) if a.sssp else tune_scale(s, a.roots)
         print(json.dumps(res))
         table.update(res)
     if a.multigraph:

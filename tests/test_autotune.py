@@ -39,12 +39,26 @@ def test_table_lookup_strips_both_timing_fields(tmp_path):
 
 def test_committed_table_holds_only_library_options():
     # every entry of the shipped table must be accepted by bfs_set_options
+    # (sssp entries: the bucket width, a positive argument of sssp())
     names = {"canonical_parents", "alpha", "beta", "big_degree", "ms_alpha", "ms_beta",
              "timeout_ms", "blocks_per_sm"}
     table = AT.load_table()
     assert table, "tune_table.json is missing"
     for key, ent in table.items():
         opts = AT.tuned_options(key.split("/")[0], int(key.split("/")[1]) if "/" in key else None)
+        if key.startswith("sssp/"):
+            assert set(opts) == {"delta"} and opts["delta"] > 0, (key, opts)
+            continue
         assert set(opts) <= names, (key, opts)
         if "blocks_per_sm" in opts:
             assert opts["blocks_per_sm"] in (1, 2, 3)
+
+
+def test_sssp_entries_are_looked_up_by_scale(tmp_path):
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps({"sssp/20": {"delta": 0.125, "mean_ms": 2.5},
+                                "sssp/24": {"delta": 0.075, "mean_ms": 35.0},
+                                "plain/22": {"alpha": 14.0}}))
+    assert AT.tuned_options("sssp", 21, str(path)) == {"delta": 0.125}
+    assert AT.tuned_options("sssp", 23, str(path)) == {"delta": 0.075}
+    assert "delta" in AT.SSSP_SPACE and all(d > 0 for d in AT.SSSP_SPACE["delta"])
