@@ -225,3 +225,19 @@ def test_sssp_scale20_sampled_root_equals_dijkstra():
     for canonical in (0, 1):
         check_search(G, off, col, wgt, r, 0.1, edges=e, canonical=canonical)
     G.free()
+
+
+def test_sssp_bounded_waits_report_timeout_and_the_context_survives():
+    # A 100 ns limit makes the grid-barrier waits and the search's own time
+    # bound run out: every block leaves, the status word says GB_ERR_TIMEOUT,
+    # nothing faults or hangs; the next search is exact again.
+    e, w, G = gpu_weighted(14)
+    _, _, off, col, wgt = oracle_weighted(14)
+    r = roots_for(14, 1)[0]
+    gb.bfs_set_options(timeout_ms=1e-4)
+    gb.sssp(G, r)
+    with pytest.raises(gb.GbError, match="TIMEOUT"):
+        gb.gb_device_status()
+    gb.bfs_set_options(timeout_ms=5000.0)
+    check_search(G, off, col, wgt, r)
+    G.free()
