@@ -298,13 +298,23 @@ def run_reference_sssp(args, wl):
         "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def sssp_delta(args, wl):
+    """The bucket width of the kernel-3 workload: tune_table.json's for its
+    SCALE unless --untuned, else the workload's default."""
+    if args.untuned:
+        return wl["delta"]
+    from paper_2012_13548_gb300 import autotune
+    return autotune.tuned_options("sssp", wl["scale"]).get("delta", wl["delta"])
+
+
 def sssp_config(args, wl):
     scale = wl["scale"]
     return {"workload": "graph500-kernel3-sssp-kronecker-scale%d-ef16-%droots" % (scale, args.roots),
             "scale": scale, "edgefactor": W.EDGEFACTOR,
             "initiator": [W.A, W.B, W.C, round(1 - W.A - W.B - W.C, 2)],
             "weights": "multiples of 2^-24 in (0, 1], SplitMix64 weight row",
-            "roots": args.roots, "delta": wl["delta"],
+            "roots": args.roots, "delta": sssp_delta(args, wl),
+            "options": "tune_table.json" if not args.untuned else "workload default",
             "parents": "canonical" if args.canonical else "any-valid",
             "l2": "flushed before every timed call (256 MB write)",
             "step": "%d single-source shortest-path searches" % args.roots}
@@ -620,10 +630,7 @@ def run_sssp(args, dist):
     dev = torch.device("cuda", dist.local)
     stream = torch.cuda.current_stream()
     wl = W.WORKLOADS["sssp22"]
-    scale, delta = wl["scale"], wl["delta"]
-    if not args.untuned:
-        from paper_2012_13548_gb300 import autotune
-        delta = autotune.tuned_options("sssp", scale).get("delta", delta)
+    scale, delta = wl["scale"], sssp_delta(args, wl)
     spec = W.GraphSpec(scale=scale)
     gb.bfs_set_options(canonical_parents=args.canonical)
     edges = gb.kron_generate(**spec.kron_args())             # inputs: generated, untimed
@@ -712,8 +719,7 @@ def run_sssp(args, dist):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dist.max(t0.elapsed_time(t1) / args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": dict(sssp_config(args, wl), delta=delta,
-                           options="tune_table.json" if not args.untuned else "workload default"),
+            "config": sssp_config(args, wl),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": read_sssp_traffic(scale),
                          "kernel": "sssp_kernel (persistent, one launch per root)",

@@ -69,3 +69,15 @@ def test_sssp_traffic_summary_follows_the_kernel_source(tmp_path, monkeypatch):
 def test_sssp_algorithmic_bytes():
     st = {"scanned": 10, "processed": 3}
     assert bench.sssp_bytes(st, 4) == 16 * 10 + 24 * 3 + 32 * 4
+
+
+def test_sssp_config_is_the_same_for_both_arms():
+    import argparse
+    from paper_2012_13548_gb300 import autotune
+    from paper_2012_13548_gb300 import workloads as W
+    wl = W.WORKLOADS["sssp22"]
+    tuned = argparse.Namespace(untuned=False, roots=64, canonical=0)
+    plain = argparse.Namespace(untuned=True, roots=64, canonical=0)
+    assert bench.sssp_delta(tuned, wl) == autotune.tuned_options("sssp", 22).get("delta", wl["delta"])
+    assert bench.sssp_delta(plain, wl) == wl["delta"]
+    assert bench.sssp_config(tuned, wl)["delta"] == bench.sssp_delta(tuned, wl)
