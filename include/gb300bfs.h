@@ -349,8 +349,11 @@ gb_status graph_weights_view(const gb_graph *g, const uint32_t **wgt);
 /* Single-source shortest paths from `root` (Sec. 2.4, Algorithm "Sequential
  * SSSP" computes the same distances; Sec. 4.1 names delta-stepping, which
  * this runs in its near/far form on the device).  g must be built by
- * graph_build_csr_weighted.  delta: bucket width in weight units of 1.0
- * (e.g. 0.0625), <= 0 for the default.  Outputs, caller-allocated device
+ * graph_build_csr_weighted.  delta: bucket width in weight units of 1.0,
+ * rounded to a multiple of 2^-24 (at least one unit); <= 0 selects the
+ * default 0.0625.  Widths near 0.05-0.1 suit Kronecker graphs with this
+ * weight row (a narrower width means more buckets, a wider one more
+ * re-expansions within a bucket).  Outputs, caller-allocated device
  * arrays: dist float64 [n] (exact: the least path weight, a multiple of
  * 2^-24; +infinity if unreachable) and parent int32 [n] (parent(root) = root;
  * for a reached v a neighbour u with dist(u) + w(u,v) = dist(v), the
