@@ -68,6 +68,18 @@ int gb_abi_version(void);
  * a region.  Library bookkeeping: the paper has no counterpart. */
 uint64_t gb_kernel_launches(void);
 
+/* Keys per portion of the device radix sort behind kron_generate and kernel 1
+ * (library tuning; the paper has no counterpart).  A sort of more keys than
+ * one portion runs portion by portion, each portion's digit counts giving the
+ * next portion's output positions; a portion's counts must fit in 30 bits, so
+ * 1 <= keys <= 2^28 (the default, and what 0 restores).  Every portion size
+ * gives the same result; smaller portions only add kernel launches, and a test
+ * uses them to run the chained path, which the default reaches only above
+ * 2^28 keys, on small inputs.  Process-wide; applies to later calls.
+ * GB_ERR_INVALID outside that range. */
+gb_status gb_set_sort_portion(int64_t keys);
+int64_t gb_sort_portion(void);
+
 /* Synchronise `s`, then return and clear the device status word: GB_OK, or
  * the first GB_ERR_RANGE / GB_ERR_TIMEOUT a kernel recorded since the last
  * call. */

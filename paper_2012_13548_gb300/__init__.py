@@ -8,4 +8,4 @@ from .binding import (GbError, Graph, Server, bfs, bfs_batch, bfs_noalloc, bfs_g
                       bfs_last_stats, bfs_validate, bfs_multi_graph, bfs_set_options, gb_device_status,
                       gb_kernel_launches, graph_build_csr, graph_build_csr_counting,
                       graph_build_csr_weighted, graph_from_csr, graph_generate_csr, kron_generate,
-                      kron_weights, lib, sssp, sssp_last_stats, sssp_validate)
+                      kron_weights, lib, sort_portion, sssp, sssp_last_stats, sssp_validate)

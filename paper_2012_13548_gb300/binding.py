@@ -81,6 +81,8 @@ def lib():
             "gb_last_error": (ctypes.c_char_p, []),
             "gb_abi_version": (ctypes.c_int, []),
             "gb_kernel_launches": (ctypes.c_uint64, []),
+            "gb_set_sort_portion": (ctypes.c_int, [_i64]),
+            "gb_sort_portion": (_i64, []),
             "gb_device_status": (ctypes.c_int, [_vp]),
             "kron_generate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
@@ -132,7 +134,8 @@ def lib():
 
 def exported_symbols():
     """Names of the C-ABI functions this binding wraps."""
-    return ["gb_last_error", "gb_abi_version", "gb_kernel_launches", "gb_device_status", "kron_generate",
+    return ["gb_last_error", "gb_abi_version", "gb_kernel_launches", "gb_set_sort_portion",
+            "gb_sort_portion", "gb_device_status", "kron_generate",
             "graph_build_csr", "graph_build_csr_counting", "graph_from_csr", "graph_generate_csr",
             "graph_free", "graph_info", "graph_csr_view",
             "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
@@ -219,6 +222,14 @@ class Graph:
 def gb_kernel_launches():
     """Kernels this library has launched so far in this process."""
     return int(lib().gb_kernel_launches())
+
+
+def sort_portion(keys=None):
+    """Keys per portion of the library's radix sort: returns the current value,
+    after setting it to `keys` if given (0 restores the default 2^28)."""
+    if keys is not None:
+        _check(lib().gb_set_sort_portion(int(keys)))
+    return int(lib().gb_sort_portion())
 
 
 def gb_device_status(stream=None):

@@ -202,6 +202,10 @@ int gb_abi_version(void) { return 1; }
 
 uint64_t gb_kernel_launches(void) { return launches(); }
 
+gb_status gb_set_sort_portion(int64_t keys) { return set_sort_portion(keys); }
+
+int64_t gb_sort_portion(void) { return sort_portion(); }
+
 gb_status gb_device_status(gb_stream s)
 {
     return guarded([&]() -> gb_status {

@@ -68,6 +68,9 @@ inline cudaError_t alloc_async(T **p, size_t count, cudaStream_t s)
 gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                      int64_t n, int begin_bit, int end_bit, uint64_t **keys_out,
                      uint32_t **vals_out, cudaStream_t s);
+// Keys per portion of radix_sort (process-wide; 0 restores the default 2^28).
+gb_status set_sort_portion(int64_t keys);
+int64_t sort_portion();
 
 // ---------------------------------------------------------------------------
 // Graph object.

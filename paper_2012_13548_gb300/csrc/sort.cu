@@ -11,12 +11,14 @@
 // written contiguously.  Tiles take their index from an atomic counter, so a
 // tile only ever waits on tiles that are already running; every wait is
 // bounded and records GB_ERR_TIMEOUT instead of hanging.  Inputs larger than
-// 2^28 keys are sorted in portions chained through their digit bases, which
-// keeps the look-back values within 30 bits.
+// one portion (2^28 keys by default, smaller on request) are sorted portion by
+// portion, chained through their digit bases, which keeps the look-back values
+// within 30 bits.
 #include "common.cuh"
 #include "internal.h"
 
 #include <algorithm>
+#include <atomic>
 
 namespace gb {
 namespace {
@@ -27,7 +29,7 @@ constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // keys per tile
 #define RS_MINB(vals) ((vals) ? 3 * 256 / RS_THREADS : 4 * 256 / RS_THREADS)
 static_assert(RS_THREADS % 256 == 0, "threads 0..255 own one digit each");
-constexpr int64_t RS_PORTION = int64_t(1) << 28;
+constexpr int64_t RS_PORTION = int64_t(1) << 28;  // default and largest portion
 constexpr unsigned FLAG_AGG = 1u << 30;
 constexpr unsigned FLAG_INCL = 2u << 30;
 constexpr unsigned VAL_MASK = FLAG_AGG - 1u;
@@ -214,9 +216,27 @@ __global__ void __launch_bounds__(RS_THREADS, RS_MINB(VALS)) rs_onesweep_kernel(
     }
 }
 
-bool g_attr_set = false;
+// The shared-memory limits of the sort kernels are raised once per device
+// (cudaFuncSetAttribute applies to the device current at the call).
+constexpr int kAttrDevices = 64;
+std::atomic<bool> g_attr_set[kAttrDevices];
+
+// Keys per portion (gb_set_sort_portion); every portion size gives the same result.
+std::atomic<int64_t> g_portion{RS_PORTION};
 
 }  // namespace
+
+gb_status set_sort_portion(int64_t keys)
+{
+    if (keys < 0 || keys > RS_PORTION) {
+        set_error("gb_set_sort_portion: keys must be 0 (the default) or in [1, 2^28]");
+        return GB_ERR_INVALID;
+    }
+    g_portion.store(keys == 0 ? RS_PORTION : keys);
+    return GB_OK;
+}
+
+int64_t sort_portion() { return g_portion.load(); }
 
 gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                      int64_t n, int begin_bit, int end_bit, uint64_t **keys_out,
@@ -233,17 +253,19 @@ gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_
     if (!ctx) return GB_ERR_CUDA;
     const bool has_vals = vals != nullptr;
     const int passes = (end_bit - begin_bit + 7) / 8;
-    const int64_t portions = (n + RS_PORTION - 1) / RS_PORTION;
-    const int64_t tiles_max = (std::min(n, RS_PORTION) + RS_TILE - 1) / RS_TILE;
+    const int64_t portion = g_portion.load();
+    const int64_t portions = (n + portion - 1) / portion;
+    const int64_t tiles_max = (std::min(n, portion) + RS_TILE - 1) / RS_TILE;
     const size_t dyn_smem = RS_TILE * sizeof(uint64_t) + (has_vals ? RS_TILE * sizeof(uint32_t) : 0);
-    if (!g_attr_set) {
+    const bool attr_known = ctx->device >= 0 && ctx->device < kAttrDevices;
+    if (!attr_known || !g_attr_set[ctx->device].load()) {
         GB_CUDA(cudaFuncSetAttribute(rs_onesweep_kernel<true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)(RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t)))));
         GB_CUDA(cudaFuncSetAttribute(rs_onesweep_kernel<false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)(RS_TILE * sizeof(uint64_t))));
-        g_attr_set = true;
+        if (attr_known) g_attr_set[ctx->device].store(true);
     }
 
     unsigned long long *hist = nullptr, *base = nullptr;
@@ -266,8 +288,8 @@ gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
         for (int64_t q = 0; q < portions; ++q) {
-            const int64_t pb = q * RS_PORTION;
-            const int64_t pc = std::min(RS_PORTION, n - pb);
+            const int64_t pb = q * portion;
+            const int64_t pc = std::min(portion, n - pb);
             const int ntiles = (int)((pc + RS_TILE - 1) / RS_TILE);
             GB_CUDA(cudaMemsetAsync(status, 0, (1 + (size_t)ntiles * 256) * sizeof(unsigned), s));
             const unsigned long long *bin = base + ((size_t)p * (portions + 1) + q) * 256;

@@ -1,4 +1,7 @@
-"""Full-size checks that need no oracle run: at SCALE 24 (and SCALE 26 when
+"""Full-size checks that need no oracle run: at SCALE 24 and 26 the CSR must
+be exactly the set of distinct symmetrised non-loop input tuples (computed
+here with torch's own sort), which checks the chained multi-portion path the
+radix sort takes above 2^28 keys; at SCALE 24 (and SCALE 26 when
 GB_TEST_S26=1) the CSR must satisfy the Sec. 2.2 invariants and every BFS
 result must pass the Graph500 rules, which together force the levels to be
 the exact hop distances.  At SCALE 22 (the kernel-3 bench size) every
@@ -49,6 +52,51 @@ def tree_properties(off, col, rows, key, n, root, parent, level):
     pk = v * n + p
     pos = torch.searchsorted(key, pk).clamp(max=key.numel() - 1)
     assert bool((key[pos] == pk).all()), "parent is not a neighbour"
+
+
+def tuple_key_set(edges, n):
+    """Sorted distinct keys row * n + col of the symmetrised input tuples
+    without self-loops: what the CSR of Sec. 2.2 must hold, from torch.unique."""
+    keep = edges[0] != edges[1]
+    a, b = edges[0][keep], edges[1][keep]
+    del keep
+    tk = torch.cat([a * n + b, b * n + a])
+    del a, b
+    out = torch.unique(tk, sorted=True)
+    del tk
+    return out
+
+
+@pytest.mark.parametrize("scale", [24, 26])
+def test_full_size_csr_is_the_tuple_set(scale):
+    # above 2^28 keys (kernel 1 from SCALE 24, the SCALE 26 generator's
+    # shuffle) the radix sort chains several portions; a dropped or doubled
+    # portion changes this set
+    spec = W.GraphSpec(scale=scale)
+    n = spec.n
+    edges = gb.kron_generate(**spec.kron_args())
+    assert int(edges.min()) >= 0 and int(edges.max()) < n
+    want = tuple_key_set(edges, n)
+    g = gb.graph_build_csr(edges, scale)
+    off, col = g.csr()
+    assert g.nnz == want.numel()
+    deg = off[1:] - off[:-1]
+    rows = torch.repeat_interleave(torch.arange(n, device=col.device, dtype=torch.int64), deg)
+    assert torch.equal(rows * n + col.to(torch.int64), want), "CSR differs from the tuple set"
+    del rows, deg
+    g.free()
+    # the fused generate-and-build path (no edge list) gives the same graph
+    g = gb.graph_generate_csr(**spec.kron_args())
+    off2, col2 = g.csr()
+    assert g.nnz == want.numel()
+    deg = off2[1:] - off2[:-1]
+    rows = torch.repeat_interleave(torch.arange(n, device=col2.device, dtype=torch.int64), deg)
+    assert torch.equal(rows * n + col2.to(torch.int64), want), "fused CSR differs from the tuple set"
+    del rows, deg
+    g.free()
+    del want, edges
+    torch.cuda.empty_cache()
+    gb.gb_device_status()
 
 
 @pytest.mark.parametrize("scale", SCALES)
