@@ -178,7 +178,11 @@ bool gb_server::step_plain(GraphRun &G)
             P.q = -1;
             done.notify_all();
         }
-        int64_t t = -1;
+        // The query's root and buffers are copied out under the lock: other
+        // threads append to `q` meanwhile, and no element of it is read
+        // without the lock.
+        int64_t t = -1, root = 0;
+        int32_t *par = nullptr, *lev = nullptr;
         {
             std::lock_guard<std::mutex> lk(mu);
             const size_t need = out_bytes(G.g);
@@ -192,11 +196,13 @@ bool gb_server::step_plain(GraphRun &G)
             G.pending.pop_front();
             used += need;
             x.state = Q_RUNNING;
+            root = x.root;
+            par = x.par;
+            lev = x.lev;
         }
-        Query &x = q[(size_t)t];
         ++G.n_launch;
         ++G.n_admit;
-        gb_status rc = gb::bfs_impl(G.g, x.root, x.par, x.lev, P.stats, P.stream, G.plain_blocks, P.ws);
+        gb_status rc = gb::bfs_impl(G.g, root, par, lev, P.stats, P.stream, G.plain_blocks, P.ws);
         if (rc == GB_OK && cudaEventRecord(P.ev, P.stream) != cudaSuccess) rc = GB_ERR_CUDA;
         if (rc != GB_OK) {
             std::lock_guard<std::mutex> lk(mu);
