@@ -1,21 +1,27 @@
 #!/usr/bin/env python3
 """Graph500 BFS benchmark on GB300 (kernel 1 + kernel 2 of arXiv 2012.13548, Sec. 2).
 
-Default workload (SCALE 20, edgefactor 16, 64 roots): one step is
+Default workload (SCALE 26, edgefactor 16, 64 roots): one step is
   kernel 1 (CSR build from the device-resident Kronecker edge list),
   64 single-source direction-optimising BFS runs (one per root, each timed),
   one 64-root multi-source BFS of the same roots ("batched").
 `value` is the Graph500 figure: the harmonic mean over the timed roots of
 m_r / t_r, m_r = input tuples whose start vertex the search reached (Sec. 4.3),
 t_r = the bfs() call timed with CUDA events on its stream.  L2 is flushed (a
-256 MB write) before every timed call.
+256 MB write) before every timed call.  Beside it, outside the timed region:
+the batched-vs-plain comparison on the SCALE 22 graph (64 roots in one launch
+against the harmonic mean of 64 single-source runs), and the CPU baseline on
+the same SCALE 26 graph: the paper's parallel BFS (Sec. 2.3.2) on all host
+cores and the serial oracle BFS, on a graph the CPU builds itself (and which
+must equal the GPU's CSR).
 
-Other workloads (--workload): s26 (SCALE 26), s22ms (SCALE 22, plain vs one
+Other workloads (--workload): s20 (SCALE 20), s22ms (SCALE 22, plain vs one
 64-root launch), batch32 (32 graphs of SCALE 12..18, 8 roots each),
-serve6 (serving loop, p50/p99 latency).
+serve6 (serving loop, p50/p99 latency), sssp22 (kernel 3).
 
-`--impl reference` times the CPU oracle (serial C) on a bounded sample of the
-same workload and prints the same JSON line with "impl": "reference".
+`--impl reference` times the paper's parallel BFS (Sec. 2.3.2, OpenMP on all
+host cores; for sssp22 the serial oracle's Dijkstra) on a bounded sample of
+the same workload and prints the same JSON line with "impl": "reference".
 """
 import argparse
 import json
@@ -45,7 +51,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="s20",
+    p.add_argument("--workload", default="s26",
                    choices=["s20", "s26", "s22ms", "serve6", "batch32", "sssp22"])
     p.add_argument("--untuned", action="store_true", help="library defaults instead of tune_table.json")
     p.add_argument("--duration", type=float, default=3.0, help="serve6: seconds of arrivals")
@@ -54,7 +60,10 @@ def parse_args():
     p.add_argument("--canonical", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="CPU baseline: seconds of the paper's parallel BFS to time")
+    p.add_argument("--cpu-threads", type=int, default=0, help="CPU baseline threads (0: all)")
+    p.add_argument("--no-c4a", action="store_true", help="skip the SCALE 22 batched-vs-plain record")
     return p.parse_args()
 
 
@@ -168,25 +177,89 @@ class ClockSampler:
 # CPU oracle timing (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(scale, nroots, seconds):
-    """Time the serial oracle BFS over the workload's roots until `seconds` of
-    BFS work; returns (harmonic-mean GTEPS, roots timed, seconds spent)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_graph(spec, threads):
+    """The workload's graph built on the host by the paper's multicore method
+    (Sec. 2.1 generator, Sec. 2.2 CSR, a parallel radix sort as Sec. 4.2
+    proposes): (off, col, starts, seconds)."""
+    import oracle.parallel as P
+    t0 = time.perf_counter()
+    off, col, starts = P.kron_csr(**spec.kron_args(), threads=threads)
+    return off, col, starts, time.perf_counter() - t0
+
+
+def cpu_baseline(spec, roots, seconds, threads, gpu_graph=None, gpu_level_of=None):
+    """The CPU baseline on the same graph as the GPU line.
+
+    The paper's Algorithm "Parallel BFS" (Sec. 2.3.2, OpenMP on `threads`
+    host cores) is timed over the workload's roots until `seconds` of search;
+    the serial oracle BFS (Sec. 2.3.1) on the first root beside it.  The graph
+    is built on the host by the parallel CPU build; when the GPU's graph is
+    given, its CSR must equal the CPU's bit for bit, and the levels of the
+    first roots (gpu_level_of(root) -> host int32 array) must equal both CPU
+    searches' levels."""
     import oracle
-    spec = W.GraphSpec(scale=scale)
-    e = oracle.kron_generate(**spec.kron_args())
-    off, col = oracle.csr_build(e, scale)
-    roots = W.select_roots(off, nroots, spec.seeds()[3])
-    rates, spent, done = [], 0.0, 0
+    import oracle.parallel as P
+    th = threads or P.max_threads()
+    off, col, starts, build_s = cpu_graph(spec, th)
+    parity = {}
+    if gpu_graph is not None:
+        goff, gcol = gpu_graph.csr()
+        parity["csr_equal"] = bool(np.array_equal(goff.cpu().numpy(), off) and
+                                   np.array_equal(gcol.cpu().numpy(), col))
+    rates, spent, done, levels = [], 0.0, 0, {}
     for r in roots:
         t0 = time.perf_counter()
-        _, lev = oracle.bfs(off, col, int(r))
+        _, lev, _ = P.bfs(off, col, int(r), threads=th)
         dt = time.perf_counter() - t0
-        rates.append(oracle.teps_edges(e, lev) / dt / 1e9)
+        rates.append(P.teps_edges(starts, lev, th) / dt / 1e9)
         spent += dt
         done += 1
+        if done <= 2:
+            levels[int(r)] = lev
         if spent >= seconds:
             break
-    return harmonic_mean(rates), done, spent, (off, col, e)
+    r0 = int(roots[0])
+    t0 = time.perf_counter()
+    _, lev_serial = oracle.bfs(off, col, r0)
+    ds = time.perf_counter() - t0
+    serial = P.teps_edges(starts, lev_serial, th) / ds / 1e9
+    if gpu_level_of is not None:
+        same = [np.array_equal(gpu_level_of(r), lv) for r, lv in levels.items()]
+        parity["levels_equal_roots"] = int(sum(same))
+        parity["levels_checked_roots"] = len(same)
+        parity["serial_oracle_levels_equal"] = bool(np.array_equal(levels[r0], lev_serial))
+    model = cpu_model()
+    out = {"value": harmonic_mean(rates), "unit": "GTEPS", "cores": th, "kind": "paper-parallel-bfs",
+           "cpu_model": model, "nproc": os.cpu_count(),
+           "sample": "the paper's level-synchronous parallel BFS (Sec. 2.3.2, OpenMP, %d threads) on "
+                     "the SCALE %d graph built on the host (%.1f s), first %d of its %d roots "
+                     "(%.1f s of search)" % (th, spec.scale, build_s, done, len(roots), spent),
+           "cpu_kernel1_s": build_s,
+           "serial_oracle": {"value": serial, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": "serial C oracle queue BFS (Sec. 2.3.1, canonical parents "
+                                       "included) from the first root of the same graph (%.1f s)" % ds}}
+    if parity:
+        out["full_size_parity"] = parity
+    return out
 
 
 def oracle_weighted_graph(scale):
@@ -220,43 +293,46 @@ def oracle_sssp_sample(scale, nroots, seconds, graph=None):
 
 
 def run_reference(args, dist):
+    """The reference arm: the paper's parallel BFS (Sec. 2.3.2, OpenMP on all
+    host cores) on the workload's graph, built on the host; each step searches
+    from the next root.  Under torchrun only rank 0 runs it."""
     if dist.rank != 0:
         return
     wl = W.WORKLOADS[args.workload]
     if args.workload == "sssp22":
         return run_reference_sssp(args, wl)
+    if "scale" not in wl:
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the %s workload has no CPU counterpart" % args.workload}))
+        return
+    import oracle.parallel as P
     scale = wl["scale"]
-    import oracle
     spec = W.GraphSpec(scale=scale)
-    e = oracle.kron_generate(**spec.kron_args())
-    off, col = oracle.csr_build(e, scale)
+    th = args.cpu_threads or P.max_threads()
+    off, col, starts, build_s = cpu_graph(spec, th)
     roots = W.select_roots(off, args.roots, spec.seeds()[3])
-    per_step = max(1, min(len(roots), 4))
     rates, step_times = [], []
     i = 0
     for s in range(args.warmup + args.steps):
-        t_step = 0.0
-        for _ in range(per_step):
-            r = int(roots[i % len(roots)])
-            i += 1
-            t0 = time.perf_counter()
-            _, lev = oracle.bfs(off, col, r)
-            dt = time.perf_counter() - t0
-            t_step += dt
-            if s >= args.warmup:
-                rates.append(oracle.teps_edges(e, lev) / dt / 1e9)
+        r = int(roots[i % len(roots)])
+        i += 1
+        t0 = time.perf_counter()
+        _, lev, _ = P.bfs(off, col, r, threads=th)
+        dt = time.perf_counter() - t0
         if s >= args.warmup:
-            step_times.append(t_step)
+            rates.append(P.teps_edges(starts, lev, th) / dt / 1e9)
+            step_times.append(dt)
     v = harmonic_mean(rates)
-    sample = ("serial C oracle queue BFS on the SCALE %d graph (oracle-built), %d roots per step, "
-              "%d timed steps" % (scale, per_step, args.steps))
+    sample = ("the paper's level-synchronous parallel BFS (Sec. 2.3.2, OpenMP, %d threads) on the "
+              "SCALE %d graph built on the host (%.1f s, untimed), one root per step, %d timed steps"
+              % (th, scale, build_s, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(step_times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": workload_config(args, scale),
-            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": th, "kind": "paper-parallel-bfs",
+                             "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -401,7 +477,10 @@ def run_ours(args, dist):
         b0.record(stream)
         gb.bfs_batch(g, roots, P, L)
         b1.record(stream)
-        rec.append((k0, k1, per, b0, b1, g2))
+        # the step's kernel-1 graph (equal to g) is freed at once: graph_free
+        # waits for the step's work, and at SCALE 26 every graph holds 9 GB
+        g2.free()
+        rec.append((k0, k1, per, b0, b1))
 
     for _ in range(args.warmup):
         step([])
@@ -424,8 +503,6 @@ def run_ours(args, dist):
     clk = clocks.stop()
     gb.gb_device_status()
     total_ms = t_all0.elapsed_time(t_all1)
-    for r in rec:
-        r[5].free()
 
     # generator and kernel 1 fused (no edge list) against the generator plus kernel 1,
     # outside the timed region
@@ -489,14 +566,19 @@ def run_ours(args, dist):
     # end to end through the public API from pinned host memory
     e2e = None if args.no_e2e else run_e2e(args, gb, torch, edges, scale, roots, m_r, dist)
 
+    # batched vs plain on the SCALE 22 graph (64 roots in one launch against
+    # 64 single-source searches), outside the timed region
+    c4a = None
+    if not args.no_c4a and args.workload != "s22ms":
+        c4a = batched_vs_plain(args, gb, torch, 22, dist)
+        gb.bfs_set_options(canonical_parents=args.canonical, **tuned)
+
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cs = min(scale, 20)   # the serial oracle builds SCALE > 20 graphs too slowly
-        v, done, spent, _ = oracle_sample(cs, len(all_roots), args.cpu_seconds)
-        cpu = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": "serial C oracle queue BFS on the SCALE %d graph of this workload "
-                         "rebuilt by the oracle, first %d of its %d roots (%.1f s of BFS)" % (
-                             cs, done, len(all_roots), spent)}
+        def gpu_level_of(r):
+            gb.bfs(g, int(r), parent, level)
+            return level.cpu().numpy()
+        cpu = cpu_baseline(spec, all_roots, args.cpu_seconds, args.cpu_threads, g, gpu_level_of)
     if dist.rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": dist.world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -508,7 +590,8 @@ def run_ours(args, dist):
                              "peak_source": "measured" if peaks else "fallback"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "batched": {"gteps": batched_gteps, "ms": statistics.median(batch_ms),
-                            "vs_plain": batched_gteps / hm, "roots": len(roots)},
+                            "vs_plain": batched_gteps / hm, "roots": len(roots), "scale": scale},
+                "batched_scale22": c4a,
                 "kernel1": {"ms": statistics.median(k1_ms),
                             "gbs": k1_bytes / (statistics.median(k1_ms) * 1e-3) / 1e9,
                             "alg_bytes": k1_bytes,
@@ -525,6 +608,75 @@ def run_ours(args, dist):
                           "mean_levels": statistics.mean(s["nlevels"] for s in stats),
                           "mean_edges_examined": statistics.mean(s["edges_examined"] for s in stats)}}
         print(json.dumps(line))
+
+
+def batched_vs_plain(args, gb, torch, scale, dist):
+    """Batched multi-source BFS against the plain search on one graph: the
+    harmonic mean of 64 single-source searches (each timed, L2 flushed before
+    it) and one 64-root launch (median of 5), both on the SCALE `scale` graph
+    with the tuned options of that SCALE; every tree and row validated on the
+    device.  Untimed by the step clock."""
+    from paper_2012_13548_gb300 import autotune
+    spec = W.GraphSpec(scale=scale)
+    gb.bfs_set_options(canonical_parents=args.canonical,
+                       **(dict(autotune.tuned_options("plain", scale),
+                               **autotune.tuned_options("batched", scale)) if not args.untuned else {}))
+    stream = torch.cuda.current_stream()
+    edges = gb.kron_generate(**spec.kron_args())
+    g = gb.graph_build_csr(edges, scale)
+    off, _ = g.csr()
+    all_roots = W.select_roots(off.cpu().numpy(), args.roots * dist.world, spec.seeds()[3])
+    roots = shard_roots(all_roots, dist.rank, dist.world, args.roots)
+    n = g.n
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    m_r, bad = [], 0
+    for r in roots:
+        gb.bfs(g, int(r), parent, level)
+        v = gb.bfs_validate(g, int(r), parent, level, edges)
+        m_r.append(v["teps_edges"])
+        bad += v["code"] != 0
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    plain_rates = []
+    for rep in range(3):
+        per = []
+        for r in roots:
+            flush.fill_(rep)
+            a, b = ev(), ev()
+            a.record(stream)
+            gb.bfs(g, int(r), parent, level)
+            b.record(stream)
+            per.append((a, b))
+        torch.cuda.synchronize()
+        if rep > 0:
+            plain_rates += [m_r[i] / (per[i][0].elapsed_time(per[i][1]) * 1e-3) / 1e9
+                            for i in range(len(roots))]
+    P = torch.empty((len(roots), n), dtype=torch.int32, device="cuda")
+    L = torch.empty((len(roots), n), dtype=torch.int32, device="cuda")
+    bms = []
+    for rep in range(6):
+        flush.fill_(rep)
+        a, b = ev(), ev()
+        a.record(stream)
+        gb.bfs_batch(g, roots, P, L)
+        b.record(stream)
+        b.synchronize()
+        if rep > 0:
+            bms.append(a.elapsed_time(b))
+    for i, r in enumerate(roots):
+        bad += gb.bfs_validate(g, int(r), P[i], L[i])["code"] != 0
+    gb.gb_device_status()
+    plain = harmonic_mean(dist.gather(plain_rates))
+    t_b = dist.max(statistics.median(bms))
+    batched = sum(dist.gather(m_r)) / (t_b * 1e-3) / 1e9
+    g.free()
+    del P, L, edges
+    torch.cuda.empty_cache()
+    return {"scale": scale, "roots": len(roots) * dist.world,
+            "plain_gteps": plain * dist.world, "batched_gteps": batched,
+            "vs_plain": batched / (plain * dist.world), "batched_ms": t_b,
+            "invalid_trees": int(dist.max(float(bad)))}
 
 
 def kernel1_bytes(m, scale, nnz, n):

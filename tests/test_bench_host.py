@@ -81,3 +81,21 @@ def test_sssp_config_is_the_same_for_both_arms():
     assert bench.sssp_delta(tuned, wl) == autotune.tuned_options("sssp", 22).get("delta", wl["delta"])
     assert bench.sssp_delta(plain, wl) == wl["delta"]
     assert bench.sssp_config(tuned, wl)["delta"] == bench.sssp_delta(tuned, wl)
+
+
+def test_cpu_baseline_runs_the_papers_parallel_bfs_on_the_same_graph():
+    from paper_2012_13548_gb300 import workloads as W
+    import oracle.parallel as P
+    spec = W.GraphSpec(scale=12)
+    off, _, _ = P.kron_csr(**spec.kron_args())
+    roots = W.select_roots(off, 8, spec.seeds()[3])
+    out = bench.cpu_baseline(spec, roots, seconds=0.05, threads=2)
+    assert out["kind"] == "paper-parallel-bfs" and out["cores"] == 2 and out["value"] > 0
+    assert "SCALE 12" in out["sample"]
+    assert out["serial_oracle"]["cores"] == 1 and out["serial_oracle"]["value"] > 0
+    # with a stand-in for the GPU's levels (the oracle's), parity is reported
+    import oracle
+    out = bench.cpu_baseline(spec, roots, seconds=0.05, threads=2,
+                             gpu_level_of=lambda r: oracle.bfs(off, *P.kron_csr(**spec.kron_args())[1:2], r)[1])
+    assert out["full_size_parity"]["levels_equal_roots"] == out["full_size_parity"]["levels_checked_roots"]
+    assert out["full_size_parity"]["serial_oracle_levels_equal"]
