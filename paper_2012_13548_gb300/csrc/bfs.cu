@@ -9,7 +9,7 @@
 //
 //  top-down (Algorithm "Parallel BFS", Sec. 2.3.2): for every frontier vertex
 //    and every neighbour in parallel, an unvisited neighbour is claimed with
-//    an atomic OR on the visited bitmap; the winner writes parent and level
+//    an atomic OR on the visited bitmap; the winner records parent and level
 //    and appends the vertex to the next queue with one atomic per warp.
 //    Frontier vertices of degree <= big_degree are expanded 32 at a time by a
 //    warp that gathers their adjacency lists as one contiguous stream of
@@ -31,9 +31,11 @@
 //
 // Memory layout of one search: visited bitmap and a ring of four frontier
 // bitmaps (n/8 bytes each, L2-resident at SCALE 26: 8 MB), one int32 queue of
-// n entries holding every level's frontier back to back (the BFS order), a
-// list of big frontier vertices with their chunk bases, and four level
-// control records (ring).
+// n entries holding every level's frontier back to back (the BFS order), one
+// state byte per vertex (level and parent source, mostly L2-resident: 64 MB at
+// SCALE 26), a list of big frontier vertices with their chunk bases, and four
+// level control records (ring).  The level and parent outputs are written once,
+// by a last pass over all vertices.
 #include "common.cuh"
 #include "internal.h"
 
@@ -96,10 +98,13 @@ struct BfsArgs {
     int32_t root;
     int32_t *parent;
     int32_t *level;
+    uint8_t *st8;  // per vertex: level + 1 (7 bits) and "parent is the hub" (bit 7)
     unsigned *vis;
     unsigned *fb;  // 4 bitmaps of nw words
     int64_t nw;
     int32_t *queue;
+    int32_t *ulist;  // per warp a segment of useg entries: the vertices a bottom-up level left open (or null)
+    int64_t useg;
     BigEnt *bigq;
     int64_t bigcap;
     WsHeader *hdr;
@@ -109,6 +114,7 @@ struct BfsArgs {
     float beta;
     int big_deg;
     int canonical;
+    int vec_out;  // parent, level, hub and the state bytes allow 16-byte vector access
     uint64_t timeout_ns;
 };
 
@@ -126,6 +132,28 @@ __device__ __forceinline__ BigEnt load_big(const BigEnt *q, int64_t i)
 __device__ __forceinline__ unsigned nchunks(int64_t deg)
 {
     return (unsigned)((deg + BIG_CHUNK - 1) / BIG_CHUNK);
+}
+
+// The outputs are not written level by level: a search would then rewrite
+// scattered parts of almost every 32-byte sector of the two n-entry output
+// arrays at every large level, each a read-modify-write in DRAM.  A reached
+// vertex records one byte instead (its level + 1, and whether its parent is
+// its hub, which the bottom-up hub test then need not store), and the last
+// pass writes level and parent of every vertex as whole lines.  A parent
+// found any other way is written to the parent output at once (few: the
+// top-down claims and the row-pass finds).  Levels from ST_ESC - 1 up are
+// written to the level output directly and flagged ST_ESC.
+constexpr unsigned ST_HUB = 0x80u;
+constexpr unsigned ST_ESC = 0x7fu;
+
+__device__ __forceinline__ void mark_reached(const BfsArgs &a, int64_t v, int lvl, bool via_hub)
+{
+    unsigned e = (unsigned)lvl + 1u;
+    if (e >= ST_ESC) {
+        e = ST_ESC;
+        a.level[v] = lvl;
+    }
+    a.st8[v] = (uint8_t)(e | (via_hub ? ST_HUB : 0u));
 }
 
 // Discovered vertices are staged per warp in shared memory and moved to the
@@ -177,6 +205,33 @@ __device__ __forceinline__ void flush_big(WarpBuf &wb, int &bn, const BfsArgs &a
     }
     __syncwarp();
     bn = 0;
+}
+
+// Warp-collective: the lanes with `keep` stay open for the next level.  A
+// bottom-up level lists the vertices it leaves open in the warp's own segment
+// of the open list (no atomics: the warp owns the segment), and a bottom-up
+// level that follows lets the same warp walk that segment instead of its
+// words of the visited bitmap, compacting it in place (a vertex is written
+// back only after it and every vertex before it were read).
+__device__ __forceinline__ void append_open(bool keep, int32_t u, int32_t *seg, int &un)
+{
+    if (!seg) return;
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (keep) __stcg(&seg[un + __popc(bal & lanemask_lt())], u);
+    un += __popc(bal);
+}
+
+// Warp-collective: set the visited and next-frontier bits of the lanes with
+// `on`, one atomic per bitmap word among the lanes sharing it.
+__device__ __forceinline__ void set_bits(bool on, int32_t u, unsigned *vis, unsigned *Fn)
+{
+    const unsigned w = on ? (unsigned)u >> 5 : 0xffffffffu;
+    const unsigned peers = __match_any_sync(kFull, w);
+    const unsigned bits = __reduce_or_sync(peers, on ? 1u << (u & 31) : 0u);
+    if (on && (__ffs(peers) - 1) == (int)lane_id()) {
+        atomicOr(&vis[w], bits);
+        atomicOr(&Fn[w], bits);
+    }
 }
 
 // Warp-collective: the lanes with `won` join the next frontier.
@@ -242,7 +297,7 @@ __device__ __forceinline__ void td_visit(const bool (&valid)[TD_E], const int32_
     for (int t = 0; t < TD_E; ++t) {
         if (won[t]) {
             a.parent[v[t]] = src[t];
-            a.level[v[t]] = l + 1;
+            mark_reached(a, v[t], l + 1, false);
             atomicOr(&Fn[(unsigned)v[t] >> 5], 1u << (v[t] & 31));
         } else {
             dv[t] = 0;
@@ -320,27 +375,6 @@ __device__ __forceinline__ void bu_stream_rows(const BfsArgs &a, const unsigned 
     }
 }
 
-// Warp-collective: the lanes of visited word w that found a parent write it,
-// join the visited set and the next frontier (the warp owns the word).
-__device__ __forceinline__ void bu_commit_word(const BfsArgs &a, unsigned *Fn, int64_t w,
-                                               unsigned vw, int64_t u, int32_t found, int32_t deg,
-                                               int l, WarpBuf &wbuf, int &qn, int &bn,
-                                               unsigned long long &my_mf, LevelCtl *nxt,
-                                               int64_t qnext_base, int64_t bnext_base)
-{
-    const bool won = found >= 0 && GB_OK_IDX(a.st, u, a.n, 215);
-    if (won) {
-        a.parent[u] = found;
-        a.level[u] = l + 1;
-    }
-    const unsigned nm = __ballot_sync(kFull, won);
-    if (nm && lane_id() == 0) {
-        __stcg(&a.vis[w], vw | nm);
-        __stcg(&Fn[w], nm);
-    }
-    append_next(won, (int32_t)u, deg, a, wbuf, qn, bn, my_mf, nxt, qnext_base, bnext_base);
-}
-
 // Warp-collective bottom-up row pass over `cnt` (<= 32) vertices of the warp's
 // pending ring from position `head`, lane i taking entry head + i: the lane probes the first
 // BU_LANE_FIRST neighbours of its row, rows still open are streamed by the
@@ -349,7 +383,7 @@ __device__ __forceinline__ void bu_commit_word(const BfsArgs &a, unsigned *Fn, i
 // with atomics.
 __device__ __forceinline__ void bu_row_pass(const BfsArgs &a, const unsigned *F, unsigned *Fn,
                                             int head, int cnt, int l, WarpBuf &wb, int &qn, int &bn,
-                                            unsigned long long &my_mf,
+                                            int32_t *seg, int &un, unsigned long long &my_mf,
                                             unsigned long long &my_edges, LevelCtl *nxt,
                                             int64_t qnext_base, int64_t bnext_base)
 {
@@ -383,12 +417,13 @@ __device__ __forceinline__ void bu_row_pass(const BfsArgs &a, const unsigned *F,
     const bool won = act && found >= 0 && GB_OK_IDX(a.st, u, a.n, 224);
     if (won) {
         a.parent[u] = found;
-        a.level[u] = l + 1;
+        mark_reached(a, u, l + 1, false);
         const unsigned bit = 1u << (u & 31);
         atomicOr(&a.vis[(unsigned)u >> 5], bit);
         atomicOr(&Fn[(unsigned)u >> 5], bit);
     }
     append_next(won, u, d, a, wb, qn, bn, my_mf, nxt, qnext_base, bnext_base);
+    append_open(act && !won, u, seg, un);  // still no parent: open at the next level
 }
 
 // Canonical mode: the vertices claimed top-down at the previous level (queue
@@ -437,14 +472,12 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
     __shared__ unsigned long long s_mf;
     WarpBuf &wb = s_wb[threadIdx.x >> 5];
     int qn_buf = 0, bn_buf = 0;  // warp-uniform fill levels of wb
+    int un_open = 0;             // warp-uniform: vertices in this warp's open-list segment
     if (threadIdx.x == 0) s_mf = 0;
     unsigned long long my_mf = 0;
 
-    // ---- init: outputs to -1, bitmaps cleared, the root placed
-    for (int64_t v = gtid; v < n; v += gthreads) {
-        a.parent[v] = v == root ? root : -1;
-        a.level[v] = v == root ? 0 : -1;
-    }
+    // ---- init: bitmaps cleared, the root placed (the outputs are written
+    // by the last pass; a vertex's state byte counts only once it is visited)
     for (int64_t w = gtid; w < nw; w += gthreads) {
         const unsigned rb = (w == (root >> 5)) ? 1u << (root & 31) : 0u;
         // isolated vertices (and ids >= n) start as visited: no search reaches
@@ -457,6 +490,8 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
     }
     if (gtid == 0) {
         const int64_t dr = a.off[root + 1] - a.off[root];
+        a.parent[root] = root;
+        mark_reached(a, root, 0, false);
         a.queue[0] = root;
         h->ctl[0].qcnt = 1;
         h->ctl[0].mf = (unsigned long long)dr;
@@ -599,19 +634,68 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                 }
             }
         } else {
-            // bottom-up, in two passes over this warp's visited words.  Hub pass:
-            // BU_WORDS words per iteration, lane i owning vertex i of each; an
-            // unvisited vertex tests its hub (fast mode) against the frontier
-            // bitmap, and the words are committed.  Row offsets are loaded for
-            // unvisited lanes only.  The vertices left open queue up in the
-            // warp's pending list, and every 32 of them take a row pass (one
-            // vertex per lane), so the row probes run with full warps.
+            // bottom-up.  Hub pass: every open vertex tests its hub (fast mode),
+            // a neighbour of largest degree, against the frontier bitmap; a hit
+            // is its parent.  The vertices left open queue up in the warp's
+            // pending ring, and every 32 of them take a row pass (one vertex per
+            // lane), so the row probes run with full warps.  Vertices the row
+            // pass leaves open go to the open list.  A bottom-up level that
+            // follows another walks that list, 128 vertices per warp step, with
+            // no bitmap scan and no visited test (only the lane holding a vertex
+            // can visit it now); otherwise the warp walks its words of the
+            // visited bitmap, BU_WORDS words (lane i: vertex i of each) per step,
+            // and bulk-prefetches the next step's hub entries and row offsets
+            // into L2 (16-byte aligned arrays only: the library's own are; a
+            // caller's offsets may not be).
             int ph = 0, pt = 0;  // warp-uniform head and tail of the pending ring
-            // the next group's hub entries and row offsets are bulk-prefetched
-            // into L2 while this group is processed (16-byte aligned arrays only:
-            // the library's own are; a caller's offsets may not be)
-            const bool bulk_pf = ((reinterpret_cast<uintptr_t>(a.off) |
-                                   reinterpret_cast<uintptr_t>(a.hub)) & 15u) == 0;
+            int32_t *seg = a.ulist ? a.ulist + gwarp * a.useg : nullptr;
+            const bool from_list = seg && l > 0 && !prev_td;
+            const int64_t units = from_list ? un_open : nw;  // segment entries or bitmap words
+            un_open = 0;
+            const bool bulk_pf = !from_list && ((reinterpret_cast<uintptr_t>(a.off) |
+                                                 reinterpret_cast<uintptr_t>(a.hub)) & 15u) == 0;
+            if (from_list) {
+            // this warp's open-list segment, 32 * BU_WORDS entries per step
+            for (int64_t i0 = 0; i0 < units; i0 += 32 * BU_WORDS) {
+                int32_t u[BU_WORDS], dg[BU_WORDS], hb[BU_WORDS];
+                bool cand[BU_WORDS];
+#pragma unroll
+                for (int t = 0; t < BU_WORDS; ++t) {
+                    const int64_t i = i0 + t * 32 + lane;
+                    cand[t] = i < units;
+                    u[t] = cand[t] ? ldcg_i32(&seg[i]) : 0;
+                    cand[t] = cand[t] && GB_OK_IDX(a.st, u[t], a.n, 232);
+                }
+#pragma unroll
+                for (int t = 0; t < BU_WORDS; ++t) {
+                    dg[t] = cand[t] ? (int32_t)(__ldg(&a.off[u[t] + 1]) - __ldg(&a.off[u[t]])) : 0;
+                    hb[t] = cand[t] && a.hub ? __ldg(&a.hub[u[t]]) : -1;
+                }
+                unsigned fh[BU_WORDS];
+#pragma unroll
+                for (int t = 0; t < BU_WORDS; ++t)
+                    fh[t] = hb[t] >= 0 && GB_OK_IDX(a.st, hb[t], a.n, 233) ? ldcg_u32(&F[hb[t] >> 5]) : 0u;
+#pragma unroll
+                for (int t = 0; t < BU_WORDS; ++t) {
+                    const bool won = hb[t] >= 0 && ((fh[t] >> (hb[t] & 31)) & 1u);
+                    my_touched += (unsigned)cand[t];
+                    my_edges += (unsigned long long)(hb[t] >= 0);
+                    if (won) mark_reached(a, u[t], l + 1, true);
+                    set_bits(won, u[t], a.vis, Fn);
+                    append_next(won, u[t], dg[t], a, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
+                    const bool pend = cand[t] && !won;
+                    const unsigned pm = __ballot_sync(kFull, pend);
+                    if (pend) wb.pu[(pt + __popc(pm & lanemask_lt())) & (PBUF - 1)] = u[t];
+                    pt += __popc(pm);
+                }
+                while (pt - ph >= 32) {
+                    bu_row_pass(a, F, Fn, ph, 32, l, wb, qn_buf, bn_buf, seg, un_open, my_mf, my_edges,
+                                nxt, qnext_base, bnext_base);
+                    ph += 32;
+                }
+            }
+            } else {
+            // this warp's words of the visited bitmap, BU_WORDS per step
             for (int64_t w0 = gwarp * BU_WORDS; w0 < nw; w0 += nwarps * BU_WORDS) {
                 const int64_t wn = w0 + nwarps * BU_WORDS;
                 if (bulk_pf && lane == 0 && (wn + BU_WORDS) * 32 <= n) {
@@ -644,30 +728,37 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                     fh[t] = hb[t] >= 0 && GB_OK_IDX(a.st, hb[t], a.n, 220) ? ldcg_u32(&F[hb[t] >> 5]) : 0u;
 #pragma unroll
                 for (int t = 0; t < BU_WORDS; ++t) {
-                    if (vw[t] == kFull) continue;  // warp-uniform
+                    if (vw[t] == kFull) continue;  // a fully visited word (warp-uniform)
                     const int64_t w = w0 + t;
                     const int64_t u = w * 32 + lane;
                     const bool cand = !((vw[t] >> lane) & 1u) && u < n;
                     const int32_t found = hb[t] >= 0 && ((fh[t] >> (hb[t] & 31)) & 1u) ? hb[t] : -1;
                     my_touched += (unsigned)cand;
                     my_edges += (unsigned long long)(hb[t] >= 0);
-                    bu_commit_word(a, Fn, w, vw[t], u, found, dg[t], l, wb, qn_buf, bn_buf, my_mf,
-                                   nxt, qnext_base, bnext_base);
+                    const bool won = found >= 0;
+                    if (won) mark_reached(a, u, l + 1, true);
+                    // the warp owns word w: commit it with two plain stores
+                    const unsigned nm = __ballot_sync(kFull, won);
+                    if (nm && lane == 0) {
+                        __stcg(&a.vis[w], vw[t] | nm);
+                        __stcg(&Fn[w], nm);
+                    }
+                    append_next(won, (int32_t)u, dg[t], a, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
                     const bool pend = cand && found < 0 && dg[t] > 0;
                     const unsigned pm = __ballot_sync(kFull, pend);
                     if (pend) wb.pu[(pt + __popc(pm & lanemask_lt())) & (PBUF - 1)] = (int32_t)u;
                     pt += __popc(pm);
                 }
-                // row passes, 32 pending vertices at a time (at most 31 stay behind)
                 while (pt - ph >= 32) {
-                    bu_row_pass(a, F, Fn, ph, 32, l, wb, qn_buf, bn_buf, my_mf, my_edges, nxt,
-                                qnext_base, bnext_base);
+                    bu_row_pass(a, F, Fn, ph, 32, l, wb, qn_buf, bn_buf, seg, un_open, my_mf, my_edges,
+                                nxt, qnext_base, bnext_base);
                     ph += 32;
                 }
             }
+            }
             if (pt > ph)
-                bu_row_pass(a, F, Fn, ph, pt - ph, l, wb, qn_buf, bn_buf, my_mf, my_edges, nxt,
-                            qnext_base, bnext_base);
+                bu_row_pass(a, F, Fn, ph, pt - ph, l, wb, qn_buf, bn_buf, seg, un_open, my_mf, my_edges,
+                            nxt, qnext_base, bnext_base);
         }
         // end of level: flush the staged vertices and add the block's degree sum
         flush_queue(wb, qn_buf, a, nxt, qnext_base);
@@ -697,6 +788,70 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
         }
     }
 
+    // ---- outputs: level and parent of every vertex, whole lines per warp.
+    // Reached = visited and not isolated (isolated vertices start visited),
+    // or the root; everyone else gets -1.  The state bytes, parents and
+    // escaped levels were written by other blocks before the last barrier.
+    // Each lane takes 4 consecutive vertices: one 4-byte load of their state
+    // bytes, and the hub and parent entries loaded as 16-byte vectors at the
+    // same time (not after the state bytes: one memory round trip per
+    // group), so that a warp moves 128 vertices per step.
+    if (a.vec_out) {
+        for (int64_t g0 = gwarp * 128; g0 < n; g0 += nwarps * 128) {
+            const int64_t v0 = g0 + 4 * (int64_t)lane;
+            if (v0 + 3 < n) {
+                const int64_t w = v0 >> 5;
+                const unsigned sh = (unsigned)(v0 & 31);
+                const unsigned rbits = ((ldcg_u32(&a.vis[w]) & __ldg(&a.nz[w])) >> sh) & 15u;
+                const unsigned sw = __ldcg(reinterpret_cast<const unsigned *>(a.st8 + v0));
+                const int4 hv = a.hub ? __ldg(reinterpret_cast<const int4 *>(a.hub + v0)) : make_int4(-1, -1, -1, -1);
+                const int4 pv = __ldcg(reinterpret_cast<const int4 *>(a.parent + v0));
+                int lv[4], pr[4];
+                const int hh[4] = {hv.x, hv.y, hv.z, hv.w};
+                const int pp[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const unsigned b = (sw >> (8 * t)) & 255u;
+                    const bool reached = ((rbits >> t) & 1u) || v0 + t == root;
+                    lv[t] = -1;
+                    pr[t] = -1;
+                    if (reached) {
+                        lv[t] = (b & ST_ESC) == ST_ESC ? ldcg_i32(&a.level[v0 + t]) : (int32_t)(b & ST_ESC) - 1;
+                        pr[t] = (b & ST_HUB) ? hh[t] : pp[t];
+                    }
+                }
+                *reinterpret_cast<int4 *>(a.level + v0) = make_int4(lv[0], lv[1], lv[2], lv[3]);
+                *reinterpret_cast<int4 *>(a.parent + v0) = make_int4(pr[0], pr[1], pr[2], pr[3]);
+            } else {
+                for (int64_t v = v0; v < n && v < v0 + 4; ++v) {
+                    const bool reached = ((ldcg_u32(&a.vis[v >> 5]) & __ldg(&a.nz[v >> 5])) >> (v & 31) & 1u) ||
+                                         v == root;
+                    int32_t lvv = -1, prv = -1;
+                    if (reached) {
+                        const unsigned b = __ldcg(&a.st8[v]);
+                        lvv = (b & ST_ESC) == ST_ESC ? ldcg_i32(&a.level[v]) : (int32_t)(b & ST_ESC) - 1;
+                        prv = (b & ST_HUB) ? __ldg(&a.hub[v]) : ldcg_i32(&a.parent[v]);
+                    }
+                    a.level[v] = lvv;
+                    a.parent[v] = prv;
+                }
+            }
+        }
+    } else {
+        for (int64_t v = gtid; v < n; v += gthreads) {
+            const bool reached = ((ldcg_u32(&a.vis[v >> 5]) & __ldg(&a.nz[v >> 5])) >> (v & 31) & 1u) ||
+                                 v == root;
+            int32_t lvv = -1, prv = -1;
+            if (reached) {
+                const unsigned b = __ldcg(&a.st8[v]);
+                lvv = (b & ST_ESC) == ST_ESC ? ldcg_i32(&a.level[v]) : (int32_t)(b & ST_ESC) - 1;
+                prv = (b & ST_HUB) ? __ldg(&a.hub[v]) : ldcg_i32(&a.parent[v]);
+            }
+            a.level[v] = lvv;
+            a.parent[v] = prv;
+        }
+    }
+
     // ---- statistics: block partial sums, the last block publishes them
     my_edges = warp_sum(my_edges);
     my_touched = warp_sum(my_touched);
@@ -723,6 +878,15 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
 
 }  // namespace
 
+// The output pass uses 16-byte vector access when every array it touches
+// allows it (a caller's outputs may start anywhere).
+static int vec_ok(const BfsArgs &a)
+{
+    const uintptr_t m = reinterpret_cast<uintptr_t>(a.parent) | reinterpret_cast<uintptr_t>(a.level) |
+                        reinterpret_cast<uintptr_t>(a.hub) | reinterpret_cast<uintptr_t>(a.st8);
+    return (m & 15u) == 0 ? 1 : 0;
+}
+
 int bfs_pick_blocks(int num_sms, int minb)
 {
     int per_sm = 0;
@@ -734,11 +898,29 @@ int bfs_pick_blocks(int num_sms, int minb)
 }
 
 namespace {
+// Entries of the open list: every warp of the grid gets a segment for the
+// vertices of its bitmap words (it owns BU_WORDS words of every
+// nwarps * BU_WORDS), i.e. n rounded up per warp; room for grids of up to
+// kOpenMaxWarps warps.
+constexpr int64_t kOpenMaxWarps = 8192;
+int64_t open_list_cap(int64_t n) { return ((n + 31) / 32) * 32 + kOpenMaxWarps * 32 * BU_WORDS; }
+
+// Segment length per warp for a grid of nwarps warps, or 0 if the list cannot
+// hold them (the search then walks the bitmap at every bottom-up level).
+int64_t open_list_seg(int64_t n, int64_t nwarps)
+{
+    const int64_t nw = (n + 31) / 32;
+    const int64_t steps = (nw + nwarps * BU_WORDS - 1) / (nwarps * BU_WORDS);
+    const int64_t seg = steps * BU_WORDS * 32;
+    return seg * nwarps <= open_list_cap(n) ? seg : 0;
+}
+
 struct WsLayout {
-    size_t off_vis, off_fb, off_q, off_big, total;
+    size_t off_vis, off_fb, off_q, off_st, off_ul, off_big, total;
     int64_t bigcap;
 };
-// one buffer: header | visited | 4 frontier bitmaps | queue | big list
+// one buffer: header | visited | 4 frontier bitmaps | queue | state bytes |
+// open list | big list
 WsLayout ws_layout(const gb_graph *g, int big_deg)
 {
     WsLayout L;
@@ -747,7 +929,9 @@ WsLayout ws_layout(const gb_graph *g, int big_deg)
     L.off_vis = (sizeof(WsHeader) + 255) & ~size_t(255);
     L.off_fb = L.off_vis + ((nw * 4 + 255) & ~size_t(255));
     L.off_q = L.off_fb + ((4 * nw * 4 + 255) & ~size_t(255));
-    L.off_big = L.off_q + ((n * 4 + 255) & ~size_t(255));
+    L.off_st = L.off_q + ((n * 4 + 255) & ~size_t(255));
+    L.off_ul = L.off_st + ((nw * 32 + 255) & ~size_t(255));
+    L.off_big = L.off_ul + ((open_list_cap(n) * 4 + 255) & ~size_t(255));
     L.total = L.off_big + L.bigcap * sizeof(BigEnt);
     return L;
 }
@@ -771,7 +955,8 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     const int64_t bigcap = Lw.bigcap;
     const size_t off_vis = Lw.off_vis, off_fb = Lw.off_fb, off_q = Lw.off_q, off_big = Lw.off_big;
     unsigned char *ws = given_ws;
-    if (!ws) GB_CUDA(cudaMallocAsync((void **)&ws, Lw.total, s));
+    Scratch tmp(s);
+    if (!ws) GB_CUDA(tmp.alloc(&ws, Lw.total));
     GB_CUDA(cudaMemsetAsync(ws, 0, sizeof(WsHeader), s));
     BfsArgs a;
     a.off = g->off;
@@ -789,6 +974,8 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.fb = reinterpret_cast<unsigned *>(ws + off_fb);
     a.nw = nw;
     a.queue = reinterpret_cast<int32_t *>(ws + off_q);
+    a.st8 = ws + Lw.off_st;
+    a.ulist = reinterpret_cast<int32_t *>(ws + Lw.off_ul);
     a.bigq = reinterpret_cast<BigEnt *>(ws + off_big);
     a.bigcap = bigcap;
     a.st = ctx->status;
@@ -797,6 +984,7 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.beta = (float)o.beta;
     a.big_deg = big_deg;
     a.canonical = o.canonical_parents;
+    a.vec_out = vec_ok(a);
     a.timeout_ns = timeout_ns();
     void *args[] = {&a};
     // 1 block per SM runs the 2-per-SM kernel on half its grid
@@ -804,11 +992,12 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     const int full = minb == 3 ? ctx->bfs_blocks
                                : (o.blocks_per_sm == 1 ? std::max(1, ctx->bfs_blocks2 / 2) : ctx->bfs_blocks2);
     const int blocks = grid > 0 && grid < full ? grid : full;
+    a.useg = open_list_seg(n, (int64_t)blocks * (BFS_THREADS / 32));
+    if (a.useg == 0) a.ulist = nullptr;
     const void *kern = minb == 2 ? (const void *)bfs_kernel<2> : (const void *)bfs_kernel<3>;
     GB_CUDA(cudaLaunchCooperativeKernel(kern, dim3(blocks),
                                         dim3(BFS_THREADS), args, 0, s));
     note_launch();
-    if (!given_ws) GB_CUDA(cudaFreeAsync(ws, s));
     return GB_OK;
 }
 
@@ -831,7 +1020,8 @@ constexpr size_t kNaVis = 1024;
 constexpr size_t kNaFb = kNaVis + kNaWords * 4;
 constexpr size_t kNaNz = kNaFb + 4 * kNaWords * 4;
 constexpr size_t kNaQueue = kNaNz + kNaWords * 4;
-constexpr size_t kNaBig = kNaQueue + kNaMaxN * 4;
+constexpr size_t kNaSt = kNaQueue + kNaMaxN * 4;
+constexpr size_t kNaBig = kNaSt + kNaMaxN;
 constexpr size_t kNaStatus = kNaBig + kNaBigCap * sizeof(BigEnt);
 constexpr size_t kNaStats = kNaStatus + 256;
 constexpr size_t kNaBytes = kNaStats + ((sizeof(BfsDevStats) + 255) & ~size_t(255));
@@ -931,6 +1121,9 @@ gb_status bfs_noalloc_impl(const int64_t *off, const int32_t *col, int64_t n, in
     a.fb = reinterpret_cast<unsigned *>(ws + kNaFb);
     a.nw = nw;
     a.queue = reinterpret_cast<int32_t *>(ws + kNaQueue);
+    a.st8 = ws + kNaSt;
+    a.ulist = nullptr;  // no open list: every bottom-up level walks the bitmap
+    a.useg = 0;
     a.bigq = reinterpret_cast<BigEnt *>(ws + kNaBig);
     a.bigcap = kNaBigCap;
     a.st = reinterpret_cast<DevStatus *>(ws + kNaStatus);
@@ -939,6 +1132,7 @@ gb_status bfs_noalloc_impl(const int64_t *off, const int32_t *col, int64_t n, in
     a.beta = (float)o.beta;
     a.big_deg = std::max(o.big_degree, 1);
     a.canonical = o.canonical_parents;
+    a.vec_out = vec_ok(a);
     a.timeout_ns = timeout_ns();
     void *args[] = {&a};
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfs_kernel<2>, dim3(d.blocks),
