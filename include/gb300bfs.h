@@ -80,6 +80,17 @@ uint64_t gb_kernel_launches(void);
 gb_status gb_set_sort_portion(int64_t keys);
 int64_t gb_sort_portion(void);
 
+/* Fault injection for tests (library bookkeeping; the paper has no
+ * counterpart).  Every device allocation of the library goes through one
+ * wrapper; after this call the next `skip` allocations succeed and the `count`
+ * after them fail as if the device were out of memory (the call then reports
+ * GB_ERR_NOMEM, or, in the server, waits and retries); count = 0 disarms.
+ * Process-wide.  gb_debug_live_allocations() is the number of device blocks
+ * the library holds at the moment (allocated and not yet freed), so a test
+ * can check that a failed call leaks nothing. */
+gb_status gb_debug_fail_allocations(int64_t skip, int64_t count);
+int64_t gb_debug_live_allocations(void);
+
 /* Synchronise `s`, then return and clear the device status word: GB_OK, or
  * the first GB_ERR_RANGE / GB_ERR_TIMEOUT a kernel recorded since the last
  * call. */
@@ -441,16 +452,44 @@ gb_status sssp_validate(const gb_graph *g, int64_t root, const int32_t *parent, 
 /* Serving: resident graphs, BFS queries admitted as they arrive.            */
 /* ------------------------------------------------------------------------ */
 
+/* How a server serves its graphs (server_default_options fills the defaults).
+ *   single_source_min_vertices  graphs with at least this many vertices are
+ *                   served by concurrent single-source searches, smaller ones
+ *                   as the bits of one multi-source search (default 2^14;
+ *                   0 serves every graph by single-source searches)
+ *   slots_per_graph concurrent single-source searches per such graph, 1..8
+ *                   (default 2), each on its own stream and workspace
+ *   full_grid       0 (default): each search of a graph runs on an equal
+ *                   share of the SMs, each multi-source graph on a share
+ *                   proportional to its size; 1: every launch takes the whole
+ *                   grid (the launches then queue behind one another)
+ *   verbose         1: print per-graph launch and admission counters to
+ *                   stderr when the server is destroyed */
+typedef struct gb_server_options {
+    int64_t single_source_min_vertices;
+    int slots_per_graph;
+    int full_grid;
+    int verbose;
+} gb_server_options;
+
+gb_status server_default_options(gb_server_options *out);
+
 /* Create a server over ng resident graphs (borrowed; they must outlive the
  * server).  Queries are admitted as they arrive, whenever a slot is free and
  * their output buffers (8 * n_graph bytes) fit within mem_budget bytes of
- * device memory; admitted queries run concurrently on the device.  On a graph
- * of 2^14 or more vertices a slot is one of two concurrent single-source
- * searches, each on its own stream and half of the SMs; on a smaller graph
- * up to 64 queries run together as the bits of one multi-source BFS, a query
- * joining at the next level boundary.  The server runs its own host thread.
- * Results follow the canonical_parents option like bfs(). */
+ * device memory; admitted queries run concurrently on the device.  The
+ * budget also holds the server's own state (every single-source slot's search
+ * workspace, each multi-source search state), counted at creation:
+ * GB_ERR_NOMEM if that alone exceeds it.  On a graph of 2^14 or more vertices
+ * a slot is one of two concurrent single-source searches, each on its own
+ * stream and half of the SMs; on a smaller graph up to 64 queries run
+ * together as the bits of one multi-source BFS, a query joining at the next
+ * level boundary.  The server runs its own host thread.  Results follow the
+ * canonical_parents option like bfs().  server_create uses the default
+ * options. */
 gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb_server **out);
+gb_status server_create_with_options(const gb_graph *const *gs, int ng, size_t mem_budget,
+                                     const gb_server_options *opt, gb_server **out);
 
 /* Queue a query (graph index, root).  *ticket identifies it.  Never blocks;
  * GB_ERR_RANGE for a bad graph or root. */
@@ -464,6 +503,29 @@ gb_status server_poll(gb_server *srv, int64_t ticket, const int32_t **parent,
 
 /* Return a finished query's buffers to the server. */
 gb_status server_release(gb_server *srv, int64_t ticket);
+
+/* Cancel a query: a queued one never runs; a running one runs out and its
+ * buffers return to the server as soon as it finishes; a finished one is
+ * released.  Polling a cancelled ticket gives GB_ERR_INVALID.  GB_ERR_INVALID
+ * for an unknown, released or already cancelled ticket. */
+gb_status server_cancel(gb_server *srv, int64_t ticket);
+
+/* Counters of a server (host output): its memory budget, the bytes of its own
+ * state, the bytes counted against the budget now (that state plus the
+ * buffers of admitted queries), and how many queries are queued, running,
+ * done (not yet released), released and cancelled. */
+typedef struct gb_server_stats {
+    int64_t budget_bytes;
+    int64_t fixed_bytes;
+    int64_t used_bytes;
+    int64_t queued;
+    int64_t running;
+    int64_t done;
+    int64_t released;
+    int64_t cancelled;
+} gb_server_stats;
+
+gb_status server_stats(gb_server *srv, gb_server_stats *out);
 
 /* Replay an open-loop arrival trace: query i arrives t_arrival_s[i] seconds
  * after the call starts (ascending), on graph graph_id[i] from root[i].

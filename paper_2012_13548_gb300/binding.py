@@ -57,6 +57,16 @@ class gb_sssp_stats(ctypes.Structure):
         [("delta", ctypes.c_double), ("phase_ns", ctypes.c_int64 * 4)]
 
 
+class gb_server_options(ctypes.Structure):
+    _fields_ = [("single_source_min_vertices", ctypes.c_int64), ("slots_per_graph", ctypes.c_int),
+                ("full_grid", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class gb_server_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("budget_bytes", "fixed_bytes", "used_bytes", "queued",
+                                              "running", "done", "released", "cancelled")]
+
+
 class gb_sssp_validation(ctypes.Structure):
     _fields_ = [("code", ctypes.c_int32), ("pad", ctypes.c_int32), ("where", ctypes.c_int64),
                 ("reached", ctypes.c_int64), ("component_edges", ctypes.c_int64),
@@ -82,6 +92,8 @@ def lib():
             "gb_abi_version": (ctypes.c_int, []),
             "gb_kernel_launches": (ctypes.c_uint64, []),
             "gb_set_sort_portion": (ctypes.c_int, [_i64]),
+            "gb_debug_fail_allocations": (ctypes.c_int, [_i64, _i64]),
+            "gb_debug_live_allocations": (_i64, []),
             "gb_sort_portion": (_i64, []),
             "gb_device_status": (ctypes.c_int, [_vp]),
             "kron_generate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -118,6 +130,13 @@ def lib():
                                              ctypes.POINTER(gb_sssp_validation), _vp]),
             "server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t,
                                              ctypes.POINTER(_vp)]),
+            "server_default_options": (ctypes.c_int, [ctypes.POINTER(gb_server_options)]),
+            "server_create_with_options": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int,
+                                                          ctypes.c_size_t,
+                                                          ctypes.POINTER(gb_server_options),
+                                                          ctypes.POINTER(_vp)]),
+            "server_cancel": (ctypes.c_int, [_vp, _i64]),
+            "server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gb_server_stats)]),
             "server_submit": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.POINTER(_i64)]),
             "server_poll": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
             "server_release": (ctypes.c_int, [_vp, _i64]),
@@ -135,12 +154,14 @@ def lib():
 def exported_symbols():
     """Names of the C-ABI functions this binding wraps."""
     return ["gb_last_error", "gb_abi_version", "gb_kernel_launches", "gb_set_sort_portion",
-            "gb_sort_portion", "gb_device_status", "kron_generate",
+            "gb_sort_portion", "gb_debug_fail_allocations", "gb_debug_live_allocations",
+            "gb_device_status", "kron_generate",
             "graph_build_csr", "graph_build_csr_counting", "graph_from_csr", "graph_generate_csr",
             "graph_free", "graph_info", "graph_csr_view",
             "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
             "bfs_last_stats", "bfs_noalloc", "bfs_validate", "kron_weights", "graph_build_csr_weighted",
             "graph_weights_view", "sssp", "sssp_last_stats", "sssp_validate", "server_create",
+            "server_default_options", "server_create_with_options", "server_cancel", "server_stats",
             "server_submit", "server_poll", "server_release", "server_run_trace", "server_destroy"]
 
 
@@ -230,6 +251,17 @@ def sort_portion(keys=None):
     if keys is not None:
         _check(lib().gb_set_sort_portion(int(keys)))
     return int(lib().gb_sort_portion())
+
+
+def debug_fail_allocations(skip=0, count=0):
+    """Make the library's next `count` device allocations, after `skip` more,
+    fail as if the device were out of memory (count 0 disarms)."""
+    _check(lib().gb_debug_fail_allocations(int(skip), int(count)))
+
+
+def debug_live_allocations():
+    """Device blocks the library holds now (allocated and not yet freed)."""
+    return int(lib().gb_debug_live_allocations())
 
 
 def gb_device_status(stream=None):
@@ -411,16 +443,36 @@ def bfs_last_stats():
 class Server:
     """Continuous-batching BFS server over resident graphs (C ABI server_*).
 
-    Queries are admitted at BFS level boundaries into one of 64 bit-slots per
-    graph while their output buffers fit in `mem_budget` bytes; finished
-    queries are retired at the next boundary."""
+    Queries are admitted as slots free up while their output buffers fit in
+    `mem_budget` bytes (which also holds the server's own search state):
+    concurrent single-source searches on large graphs, bit-slots of one
+    multi-source search (admitted at level boundaries) on small ones."""
 
-    def __init__(self, graphs, mem_budget):
+    def __init__(self, graphs, mem_budget, **options):
+        """options: any of single_source_min_vertices, slots_per_graph,
+        full_grid, verbose (gb_server_options); the rest keep their defaults."""
         self.graphs = list(graphs)
         arr = (_vp * len(self.graphs))(*[g.handle.value for g in self.graphs])
+        o = gb_server_options()
+        _check(lib().server_default_options(ctypes.byref(o)))
+        names = {f for f, _ in gb_server_options._fields_}
+        if set(options) - names:
+            raise KeyError("unknown server options %s" % sorted(set(options) - names))
+        for k, v in options.items():
+            setattr(o, k, int(v))
         h = _vp()
-        _check(lib().server_create(arr, len(self.graphs), int(mem_budget), ctypes.byref(h)))
+        _check(lib().server_create_with_options(arr, len(self.graphs), int(mem_budget), ctypes.byref(o),
+                                                ctypes.byref(h)))
         self._h = h
+
+    def cancel(self, ticket):
+        _check(lib().server_cancel(self._h, int(ticket)))
+
+    def stats(self):
+        """Budget, fixed and used bytes and the query counts (server_stats)."""
+        st = gb_server_stats()
+        _check(lib().server_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in gb_server_stats._fields_}
 
     def submit(self, graph_id, root):
         t = _i64()

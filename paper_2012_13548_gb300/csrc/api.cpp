@@ -20,6 +20,9 @@ namespace gb {
 
 namespace {
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<long long> g_live_allocs{0};  // device blocks the library holds
+std::mutex g_fail_mu;                      // injected allocation failures
+long long g_fail_skip = 0, g_fail_count = 0;
 thread_local std::string t_err;
 std::mutex g_ctx_mu;
 std::vector<Context *> g_ctx;  // indexed by device
@@ -62,11 +65,11 @@ SsspDevStats *sssp_stats_buffer()
         int old = 0;
         cudaGetDevice(&old);
         cudaSetDevice(t_sssp.device);
-        cudaFree(t_sssp.dev);
+        gb::dfree(t_sssp.dev);
         cudaSetDevice(old);
         t_sssp.dev = nullptr;
     }
-    if (cudaMalloc((void **)&t_sssp.dev, sizeof(SsspDevStats)) != cudaSuccess) return nullptr;
+    if (gb::dmalloc((void **)&t_sssp.dev, sizeof(SsspDevStats)) != cudaSuccess) return nullptr;
     t_sssp.device = dev;
     t_sssp.valid = false;
     return t_sssp.dev;
@@ -82,6 +85,55 @@ gb_status check_graph(const gb_graph *g)
 }
 
 }  // namespace
+
+// True if an injected failure takes this allocation.
+static bool injected_failure()
+{
+    std::lock_guard<std::mutex> lk(g_fail_mu);
+    if (g_fail_count <= 0) return false;
+    if (g_fail_skip > 0) {
+        --g_fail_skip;
+        return false;
+    }
+    --g_fail_count;
+    return true;
+}
+
+cudaError_t dmalloc_raw(void **p, size_t bytes)
+{
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+    return e;
+}
+
+cudaError_t dmalloc_async_raw(void **p, size_t bytes, cudaStream_t s)
+{
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+    return e;
+}
+
+cudaError_t dfree(void *p)
+{
+    if (!p) return cudaSuccess;
+    g_live_allocs.fetch_sub(1);
+    return cudaFree(p);
+}
+
+cudaError_t dfree_async(void *p, cudaStream_t s)
+{
+    if (!p) return cudaSuccess;
+    g_live_allocs.fetch_sub(1);
+    return cudaFreeAsync(p, s);
+}
 
 void set_error(const std::string &msg) { t_err = msg; }
 void note_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -122,7 +174,7 @@ Context *context()
     c->device = dev;
     if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev)) !=
             cudaSuccess ||
-        (e = cudaMalloc((void **)&c->status, sizeof(DevStatus))) != cudaSuccess ||
+        (e = gb::dmalloc((void **)&c->status, sizeof(DevStatus))) != cudaSuccess ||
         (e = cudaMemset(c->status, 0, sizeof(DevStatus))) != cudaSuccess) {
         cuda_fail(e, "library context");
         delete c;
@@ -150,11 +202,11 @@ BfsDevStats *stats_buffer()
         int old = 0;
         cudaGetDevice(&old);
         cudaSetDevice(t_stats.device);
-        cudaFree(t_stats.dev);
+        gb::dfree(t_stats.dev);
         cudaSetDevice(old);
         t_stats.dev = nullptr;
     }
-    if (cudaMalloc((void **)&t_stats.dev, sizeof(BfsDevStats)) != cudaSuccess) return nullptr;
+    if (gb::dmalloc((void **)&t_stats.dev, sizeof(BfsDevStats)) != cudaSuccess) return nullptr;
     t_stats.device = dev;
     t_stats.valid = false;
     return t_stats.dev;
@@ -204,6 +256,20 @@ uint64_t gb_kernel_launches(void) { return launches(); }
 
 gb_status gb_set_sort_portion(int64_t keys) { return set_sort_portion(keys); }
 
+gb_status gb_debug_fail_allocations(int64_t skip, int64_t count)
+{
+    if (skip < 0 || count < 0) {
+        set_error("gb_debug_fail_allocations: skip and count must be >= 0");
+        return GB_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_fail_mu);
+    g_fail_skip = skip;
+    g_fail_count = count;
+    return GB_OK;
+}
+
+int64_t gb_debug_live_allocations(void) { return (int64_t)g_live_allocs.load(); }
+
 int64_t gb_sort_portion(void) { return sort_portion(); }
 
 gb_status gb_device_status(gb_stream s)
@@ -248,10 +314,10 @@ gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *
         gb_graph *g = new gb_graph();
         gb_status rc = build_csr(edges, m, scale, g, as_stream(s));
         if (rc != GB_OK) {
-            if (g->off) cudaFree(g->off);
-            if (g->col) cudaFree(g->col);
-            if (g->nz) cudaFree(g->nz);
-            if (g->hub) cudaFree(g->hub);
+            if (g->off) gb::dfree(g->off);
+            if (g->col) gb::dfree(g->col);
+            if (g->nz) gb::dfree(g->nz);
+            if (g->hub) gb::dfree(g->hub);
             delete g;
             return rc;
         }
@@ -272,10 +338,10 @@ gb_status graph_build_csr_counting(const int64_t *edges, int64_t m, int scale, g
         gb_graph *g = new gb_graph();
         gb_status rc = build_csr_counting(edges, m, scale, g, as_stream(s));
         if (rc != GB_OK) {
-            if (g->off) cudaFree(g->off);
-            if (g->col) cudaFree(g->col);
-            if (g->nz) cudaFree(g->nz);
-            if (g->hub) cudaFree(g->hub);
+            if (g->off) gb::dfree(g->off);
+            if (g->col) gb::dfree(g->col);
+            if (g->nz) gb::dfree(g->nz);
+            if (g->hub) gb::dfree(g->hub);
             delete g;
             return rc;
         }
@@ -309,12 +375,12 @@ gb_status graph_build_csr_weighted(const int64_t *edges, const float *w, int64_t
         gb_status rc = build_csr_weighted(edges, w, m, scale, g, as_stream(s));
         if (rc != GB_OK) {
             cudaStreamSynchronize(as_stream(s));
-            if (g->off) cudaFree(g->off);
-            if (g->col) cudaFree(g->col);
-            if (g->nz) cudaFree(g->nz);
-            if (g->hub) cudaFree(g->hub);
-            if (g->wgt) cudaFree(g->wgt);
-            if (g->wadj) cudaFree(g->wadj);
+            if (g->off) gb::dfree(g->off);
+            if (g->col) gb::dfree(g->col);
+            if (g->nz) gb::dfree(g->nz);
+            if (g->hub) gb::dfree(g->hub);
+            if (g->wgt) gb::dfree(g->wgt);
+            if (g->wadj) gb::dfree(g->wadj);
             delete g;
             return rc;
         }
@@ -416,10 +482,10 @@ gb_status graph_generate_csr(int scale, int edgefactor, double a, double b, doub
         gb_graph *g = new gb_graph();
         gb_status rc = kron_csr(scale, edgefactor, a, b, c, seed_gen, seed_perm, g, as_stream(s));
         if (rc != GB_OK) {
-            if (g->off) cudaFree(g->off);
-            if (g->col) cudaFree(g->col);
-            if (g->nz) cudaFree(g->nz);
-            if (g->hub) cudaFree(g->hub);
+            if (g->off) gb::dfree(g->off);
+            if (g->col) gb::dfree(g->col);
+            if (g->nz) gb::dfree(g->nz);
+            if (g->hub) gb::dfree(g->hub);
             delete g;
             return rc;
         }
@@ -465,23 +531,23 @@ gb_status graph_from_csr(const int64_t *off, const int32_t *col, int64_t n, int6
         g->scale = -1;
         g->device = ctx->device;
         cudaError_t e;
-        if ((e = cudaMalloc(&g->off, (n + 1) * sizeof(int64_t))) != cudaSuccess ||
-            (e = cudaMalloc(&g->col, std::max<int64_t>(nnz, 4) * sizeof(int32_t))) != cudaSuccess ||
+        if ((e = gb::dmalloc(&g->off, (n + 1) * sizeof(int64_t))) != cudaSuccess ||
+            (e = gb::dmalloc(&g->col, std::max<int64_t>(nnz, 4) * sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMemcpyAsync(g->off, off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
             (nnz && (e = cudaMemcpyAsync(g->col, col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st)) != cudaSuccess) ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-            cudaFree(g->off);
-            cudaFree(g->col);
+            gb::dfree(g->off);
+            gb::dfree(g->col);
             delete g;
             return cuda_fail(e, "graph_from_csr");
         }
         gb_status rc = build_graph_aux(g, st);
         if (rc == GB_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "graph_from_csr");
         if (rc != GB_OK) {
-            cudaFree(g->off);
-            cudaFree(g->col);
-            if (g->nz) cudaFree(g->nz);
-            if (g->hub) cudaFree(g->hub);
+            gb::dfree(g->off);
+            gb::dfree(g->col);
+            if (g->nz) gb::dfree(g->nz);
+            if (g->hub) gb::dfree(g->hub);
             delete g;
             return rc;
         }
@@ -495,12 +561,12 @@ gb_status graph_free(gb_graph *g)
     return guarded([&]() -> gb_status {
         if (!g) return GB_OK;
         cudaDeviceSynchronize();
-        if (g->off) cudaFree(g->off);
-        if (g->col) cudaFree(g->col);
-        if (g->nz) cudaFree(g->nz);
-        if (g->hub) cudaFree(g->hub);
-        if (g->wgt) cudaFree(g->wgt);
-        if (g->wadj) cudaFree(g->wadj);
+        if (g->off) gb::dfree(g->off);
+        if (g->col) gb::dfree(g->col);
+        if (g->nz) gb::dfree(g->nz);
+        if (g->hub) gb::dfree(g->hub);
+        if (g->wgt) gb::dfree(g->wgt);
+        if (g->wadj) gb::dfree(g->wadj);
         g->off = nullptr;
         g->col = nullptr;
         g->nz = nullptr;

@@ -274,27 +274,27 @@ gb_status build_graph_aux(gb_graph *g, cudaStream_t s)
     Context *ctx = context();
     if (!ctx) return GB_ERR_CUDA;
     const int64_t nw = (g->n + 31) / 32;
-    GB_CUDA(cudaMalloc(&g->nz, nw * sizeof(uint32_t)));
+    GB_CUDA(gb::dmalloc(&g->nz, nw * sizeof(uint32_t)));
     nz_bitmap_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->off, g->n, g->nz, nw);
     note_launch();
     GB_CUDA(cudaGetLastError());
-    GB_CUDA(cudaMalloc(&g->hub, std::max<int64_t>(g->n, 1) * sizeof(int32_t)));
+    GB_CUDA(gb::dmalloc(&g->hub, std::max<int64_t>(g->n, 1) * sizeof(int32_t)));
     uint8_t *key = nullptr;
-    GB_CUDA(alloc_async(&key, (size_t)g->n, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&key, (size_t)g->n));
     deg_key_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->off, g->n, key);
     note_launch();
     hub_kernel<<<ctx->num_sms * 8, HUB_THREADS, 0, s>>>(g->off, g->col, key, g->n, g->nnz, g->hub,
                                                         ctx->status);
     note_launch();
     GB_CUDA(cudaGetLastError());
-    GB_CUDA(cudaFreeAsync(key, s));
     return GB_OK;
 }
 
 namespace {
 
 // Stages 2-4 on the symmetrised keys k0[0..nk) (k1: the sort's second buffer
-// of nk keys); both buffers are freed here, on every path.
+// of nk keys; the caller owns both).
 gb_status csr_from_keys(uint64_t *k0, uint64_t *k1, int64_t nk, int scale, gb_graph *g,
                         cudaStream_t s)
 {
@@ -302,16 +302,13 @@ gb_status csr_from_keys(uint64_t *k0, uint64_t *k1, int64_t nk, int scale, gb_gr
     const int64_t n = g->n;
     uint64_t *ks = nullptr;
     gb_status rc = radix_sort(k0, k1, nullptr, nullptr, nk, 0, 2 * scale, &ks, nullptr, s);
-    if (rc != GB_OK) {
-        cudaFreeAsync(k0, s);
-        cudaFreeAsync(k1, s);
-        return rc;
-    }
+    if (rc != GB_OK) return rc;
     const int64_t ntiles = (nk + FIN_TILE - 1) / FIN_TILE;
     unsigned *tcnt = nullptr;
     unsigned long long *tbase = nullptr;
-    GB_CUDA(alloc_async(&tcnt, (size_t)ntiles, s));
-    GB_CUDA(alloc_async(&tbase, (size_t)ntiles + 1, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&tcnt, (size_t)ntiles));
+    GB_CUDA(tmp.alloc(&tbase, (size_t)ntiles + 1));
     k1_count_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tcnt);
     note_launch();
     k1_scan_tiles_kernel<<<1, 1024, 0, s>>>(tcnt, ntiles, tbase);
@@ -324,26 +321,17 @@ gb_status csr_from_keys(uint64_t *k0, uint64_t *k1, int64_t nk, int scale, gb_gr
     GB_CUDA(cudaStreamSynchronize(s));
     if (hst.code != 0) {
         GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
-        cudaFreeAsync(k0, s);
-        cudaFreeAsync(k1, s);
-        cudaFreeAsync(tcnt, s);
-        cudaFreeAsync(tbase, s);
-        cudaStreamSynchronize(s);
         set_error(hst.code == GB_ERR_RANGE ? "graph_build_csr: an edge endpoint is outside [0, 2^scale)"
                                            : "graph_build_csr: device error during the build");
         return (gb_status)hst.code;
     }
     g->nnz = (int64_t)nnz;
-    GB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(int64_t)));
-    GB_CUDA(cudaMalloc(&g->col, std::max<int64_t>(g->nnz, 4) * sizeof(int32_t)));
+    GB_CUDA(gb::dmalloc(&g->off, (n + 1) * sizeof(int64_t)));
+    GB_CUDA(gb::dmalloc(&g->col, std::max<int64_t>(g->nnz, 4) * sizeof(int32_t)));
     k1_write_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tbase, n, g->off, g->col,
                                                              g->nnz, ctx->status);
     note_launch();
     GB_CUDA(cudaGetLastError());
-    GB_CUDA(cudaFreeAsync(k0, s));
-    GB_CUDA(cudaFreeAsync(k1, s));
-    GB_CUDA(cudaFreeAsync(tcnt, s));
-    GB_CUDA(cudaFreeAsync(tbase, s));
     return build_graph_aux(g, s);
 }
 
@@ -351,8 +339,8 @@ gb_status csr_from_keys(uint64_t *k0, uint64_t *k1, int64_t nk, int scale, gb_gr
 gb_status empty_csr(gb_graph *g, cudaStream_t s)
 {
     g->nnz = 0;
-    GB_CUDA(cudaMalloc(&g->off, (g->n + 1) * sizeof(int64_t)));
-    GB_CUDA(cudaMalloc(&g->col, 16));
+    GB_CUDA(gb::dmalloc(&g->off, (g->n + 1) * sizeof(int64_t)));
+    GB_CUDA(gb::dmalloc(&g->col, 16));
     GB_CUDA(cudaMemsetAsync(g->off, 0, (g->n + 1) * sizeof(int64_t), s));
     gb_status r0 = build_graph_aux(g, s);
     if (r0 != GB_OK) return r0;
@@ -373,8 +361,9 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
     GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
     if (nk == 0) return empty_csr(g, s);
     uint64_t *k0 = nullptr, *k1 = nullptr;
-    GB_CUDA(alloc_async(&k0, (size_t)nk, s));
-    GB_CUDA(alloc_async(&k1, (size_t)nk, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&k0, (size_t)nk));
+    GB_CUDA(tmp.alloc(&k1, (size_t)nk));
     k1_sym_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(edges, m, scale,
                                                    reinterpret_cast<ulonglong2 *>(k0), ctx->status);
     note_launch();
@@ -401,14 +390,11 @@ gb_status kron_csr(int scale, int edgefactor, double a, double b, double c, uint
     g->device = ctx->device;
     GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
     uint64_t *k0 = nullptr, *k1 = nullptr;
-    GB_CUDA(alloc_async(&k0, (size_t)nk, s));
-    GB_CUDA(alloc_async(&k1, (size_t)nk, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&k0, (size_t)nk));
+    GB_CUDA(tmp.alloc(&k1, (size_t)nk));
     gb_status rc = kron_keys_impl(scale, edgefactor, a, b, c, seed_gen, seed_perm, k0, s);
-    if (rc != GB_OK) {
-        cudaFreeAsync(k0, s);
-        cudaFreeAsync(k1, s);
-        return rc;
-    }
+    if (rc != GB_OK) return rc;
     return csr_from_keys(k0, k1, nk, scale, g, s);
 }
 
@@ -706,8 +692,9 @@ gb_status cs_scan(const unsigned *cnt, int64_t n, int64_t *out, cudaStream_t s)
     const int64_t nchunks = std::max<int64_t>(1, (n + CS_CHUNK - 1) / CS_CHUNK);
     unsigned *sums = nullptr;
     unsigned long long *base = nullptr;
-    GB_CUDA(alloc_async(&sums, (size_t)nchunks, s));
-    GB_CUDA(alloc_async(&base, (size_t)nchunks + 1, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&sums, (size_t)nchunks));
+    GB_CUDA(tmp.alloc(&base, (size_t)nchunks + 1));
     cs_chunk_sum_kernel<<<(unsigned)nchunks, CS_THREADS, 0, s>>>(cnt, n, sums);
     note_launch();
     k1_scan_tiles_kernel<<<1, 1024, 0, s>>>(sums, nchunks, base);
@@ -715,8 +702,6 @@ gb_status cs_scan(const unsigned *cnt, int64_t n, int64_t *out, cudaStream_t s)
     cs_chunk_write_kernel<<<(unsigned)nchunks, CS_THREADS, 0, s>>>(cnt, n, base, nchunks, out);
     note_launch();
     GB_CUDA(cudaGetLastError());
-    GB_CUDA(cudaFreeAsync(sums, s));
-    GB_CUDA(cudaFreeAsync(base, s));
     return GB_OK;
 }
 
@@ -740,9 +725,10 @@ gb_status build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_grap
     const int grid = ctx->num_sms * 8;
     unsigned *cnt = nullptr, *dcnt = nullptr;
     int64_t *s0 = nullptr;
-    GB_CUDA(alloc_async(&cnt, (size_t)n, s));
-    GB_CUDA(alloc_async(&dcnt, (size_t)n, s));
-    GB_CUDA(alloc_async(&s0, (size_t)n + 1, s));
+    Scratch scr(s);
+    GB_CUDA(scr.alloc(&cnt, (size_t)n));
+    GB_CUDA(scr.alloc(&dcnt, (size_t)n));
+    GB_CUDA(scr.alloc(&s0, (size_t)n + 1));
     // 1-2: entries per row, then the row starts
     GB_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(unsigned), s));
     cs_count_kernel<<<grid, 256, 0, s>>>(edges, m, n, cnt, ctx->status);
@@ -756,25 +742,21 @@ gb_status build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_grap
     GB_CUDA(cudaStreamSynchronize(s));
     if (hst.code != 0) {
         GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
-        cudaFreeAsync(cnt, s);
-        cudaFreeAsync(dcnt, s);
-        cudaFreeAsync(s0, s);
-        cudaStreamSynchronize(s);
         set_error(hst.code == GB_ERR_RANGE ? "graph_build_csr_counting: an edge endpoint is outside [0, 2^scale)"
                                            : "graph_build_csr_counting: device error during the build");
         return (gb_status)hst.code;
     }
     // 3: scatter into the rows (cnt reused as the fill counters)
     int32_t *tmp = nullptr;
-    GB_CUDA(alloc_async(&tmp, (size_t)std::max<int64_t>(nnz0, 1), s));
+    GB_CUDA(scr.alloc(&tmp, (size_t)std::max<int64_t>(nnz0, 1)));
     GB_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(unsigned), s));
     cs_scatter_kernel<<<grid, 256, 0, s>>>(edges, m, n, s0, cnt, tmp, ctx->status);
     note_launch();
     // 4: rows sorted by length class
     int32_t *lists = nullptr;
     unsigned long long *counts = nullptr;
-    GB_CUDA(alloc_async(&lists, 3 * (size_t)n, s));
-    GB_CUDA(alloc_async(&counts, 3, s));
+    GB_CUDA(scr.alloc(&lists, 3 * (size_t)n));
+    GB_CUDA(scr.alloc(&counts, 3));
     GB_CUDA(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s));
     cs_classify_kernel<<<grid, 256, 0, s>>>(s0, n, dcnt, lists, counts);
     note_launch();
@@ -795,8 +777,9 @@ gb_status build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_grap
         const int32_t *lrows = lists + 2 * n;
         unsigned *llen = nullptr;
         int64_t *g0 = nullptr;
-        GB_CUDA(alloc_async(&llen, (size_t)nl, s));
-        GB_CUDA(alloc_async(&g0, (size_t)nl + 1, s));
+        Scratch lt(s);  // the long rows' temporaries, freed at the end of this block
+        GB_CUDA(lt.alloc(&llen, (size_t)nl));
+        GB_CUDA(lt.alloc(&g0, (size_t)nl + 1));
         cs_long_len_kernel<<<grid, 256, 0, s>>>(lrows, nl, s0, llen);
         note_launch();
         rc = cs_scan(llen, nl, g0, s);
@@ -807,8 +790,8 @@ gb_status build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_grap
         int rbits = 1;
         while ((int64_t(1) << rbits) < nl) ++rbits;
         uint64_t *k0 = nullptr, *k1 = nullptr, *ks = nullptr;
-        GB_CUDA(alloc_async(&k0, (size_t)tl, s));
-        GB_CUDA(alloc_async(&k1, (size_t)tl, s));
+        GB_CUDA(lt.alloc(&k0, (size_t)tl));
+        GB_CUDA(lt.alloc(&k1, (size_t)tl));
         const unsigned lb = (unsigned)std::min<int64_t>(nl, (int64_t)ctx->num_sms * 8);
         cs_long_gather_kernel<<<lb, CS_THREADS, 0, s>>>(lrows, nl, s0, g0, tmp, scale, k0);
         note_launch();
@@ -817,29 +800,19 @@ gb_status build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_grap
         cs_long_scatter_kernel<<<lb, CS_THREADS, 0, s>>>(lrows, nl, s0, g0, ks, scale, tmp, dcnt);
         note_launch();
         GB_CUDA(cudaGetLastError());
-        GB_CUDA(cudaFreeAsync(k0, s));
-        GB_CUDA(cudaFreeAsync(k1, s));
-        GB_CUDA(cudaFreeAsync(llen, s));
-        GB_CUDA(cudaFreeAsync(g0, s));
     }
     // 5: offsets from the distinct counts, then the columns
-    GB_CUDA(cudaMalloc(&g->off, (n + 1) * sizeof(int64_t)));
+    GB_CUDA(gb::dmalloc(&g->off, (n + 1) * sizeof(int64_t)));
     rc = cs_scan(dcnt, n, g->off, s);
     if (rc != GB_OK) return rc;
     int64_t nnz = 0;
     GB_CUDA(cudaMemcpyAsync(&nnz, g->off + n, sizeof(nnz), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     g->nnz = nnz;
-    GB_CUDA(cudaMalloc(&g->col, std::max<int64_t>(nnz, 4) * sizeof(int32_t)));
+    GB_CUDA(gb::dmalloc(&g->col, std::max<int64_t>(nnz, 4) * sizeof(int32_t)));
     cs_compact_kernel<<<grid, 256, 0, s>>>(s0, g->off, n, tmp, g->col, nnz, ctx->status);
     note_launch();
     GB_CUDA(cudaGetLastError());
-    GB_CUDA(cudaFreeAsync(cnt, s));
-    GB_CUDA(cudaFreeAsync(dcnt, s));
-    GB_CUDA(cudaFreeAsync(s0, s));
-    GB_CUDA(cudaFreeAsync(tmp, s));
-    GB_CUDA(cudaFreeAsync(lists, s));
-    GB_CUDA(cudaFreeAsync(counts, s));
     return build_graph_aux(g, s);
 }
 

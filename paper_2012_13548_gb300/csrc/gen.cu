@@ -196,11 +196,12 @@ gb_status kron_generate_impl(int scale, int edgefactor, double a, double b, doub
     uint64_t *k0 = nullptr, *k1 = nullptr, *ks = nullptr;
     uint32_t *v0 = nullptr, *v1 = nullptr, *vs = nullptr;
     int32_t *pi = nullptr;
-    GB_CUDA(alloc_async(&k0, (size_t)m, s));
-    GB_CUDA(alloc_async(&k1, (size_t)m, s));
-    GB_CUDA(alloc_async(&v0, (size_t)m, s));
-    GB_CUDA(alloc_async(&v1, (size_t)m, s));
-    GB_CUDA(alloc_async(&pi, (size_t)n, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&k0, (size_t)m));
+    GB_CUDA(tmp.alloc(&k1, (size_t)m));
+    GB_CUDA(tmp.alloc(&v0, (size_t)m));
+    GB_CUDA(tmp.alloc(&v1, (size_t)m));
+    GB_CUDA(tmp.alloc(&pi, (size_t)n));
     rc = kron_perm(n, seed_perm, k0, k1, v0, v1, pi, s);
     if (rc != GB_OK) return rc;
     // Edge shuffle order.
@@ -213,11 +214,6 @@ gb_status kron_generate_impl(int scale, int edgefactor, double a, double b, doub
                                             ctx->status);
     note_launch();
     GB_CUDA(cudaGetLastError());
-    GB_CUDA(cudaFreeAsync(k0, s));
-    GB_CUDA(cudaFreeAsync(k1, s));
-    GB_CUDA(cudaFreeAsync(v0, s));
-    GB_CUDA(cudaFreeAsync(v1, s));
-    GB_CUDA(cudaFreeAsync(pi, s));
     return GB_OK;
 }
 
@@ -232,22 +228,18 @@ gb_status kron_keys_impl(int scale, int edgefactor, double a, double b, double c
     uint64_t *k0 = nullptr, *k1 = nullptr;
     uint32_t *v0 = nullptr, *v1 = nullptr;
     int32_t *pi = nullptr;
-    GB_CUDA(alloc_async(&k0, (size_t)P.n, s));
-    GB_CUDA(alloc_async(&k1, (size_t)P.n, s));
-    GB_CUDA(alloc_async(&v0, (size_t)P.n, s));
-    GB_CUDA(alloc_async(&v1, (size_t)P.n, s));
-    GB_CUDA(alloc_async(&pi, (size_t)P.n, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&k0, (size_t)P.n));
+    GB_CUDA(tmp.alloc(&k1, (size_t)P.n));
+    GB_CUDA(tmp.alloc(&v0, (size_t)P.n));
+    GB_CUDA(tmp.alloc(&v1, (size_t)P.n));
+    GB_CUDA(tmp.alloc(&pi, (size_t)P.n));
     rc = kron_perm(P.n, seed_perm, k0, k1, v0, v1, pi, s);
     if (rc != GB_OK) return rc;
     gen_keys_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(scale, P.m, P.t_ab, P.t_a, P.t_c, seed_gen, pi,
                                                      reinterpret_cast<ulonglong2 *>(keys));
     note_launch();
     GB_CUDA(cudaGetLastError());
-    GB_CUDA(cudaFreeAsync(k0, s));
-    GB_CUDA(cudaFreeAsync(k1, s));
-    GB_CUDA(cudaFreeAsync(v0, s));
-    GB_CUDA(cudaFreeAsync(v1, s));
-    GB_CUDA(cudaFreeAsync(pi, s));
     return GB_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "gb300bfs.h"
 
@@ -52,12 +53,69 @@ unsigned long long launches();
 gb_bfs_options &options();
 uint64_t timeout_ns();
 
+// Device memory of the library.  Every allocation and free goes through
+// these: they count the blocks the library holds (gb_debug_live_allocations)
+// and fail on request like an exhausted device (gb_debug_fail_allocations),
+// so that tests can check the error paths for leaks without a real failure.
+cudaError_t dmalloc_raw(void **p, size_t bytes);
+cudaError_t dmalloc_async_raw(void **p, size_t bytes, cudaStream_t s);
+cudaError_t dfree(void *p);
+cudaError_t dfree_async(void *p, cudaStream_t s);
+template <typename T>
+inline cudaError_t dmalloc(T **p, size_t bytes)
+{
+    return dmalloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T>
+inline cudaError_t dmalloc_async(T **p, size_t bytes, cudaStream_t s)
+{
+    return dmalloc_async_raw(reinterpret_cast<void **>(p), bytes, s);
+}
+
 // Stream-ordered temporaries.
 template <typename T>
 inline cudaError_t alloc_async(T **p, size_t count, cudaStream_t s)
 {
-    return cudaMallocAsync((void **)p, count * sizeof(T) + (count == 0 ? 16 : 0), s);
+    return dmalloc_async(p, count * sizeof(T) + (count == 0 ? 16 : 0), s);
 }
+
+// The stream-ordered temporaries of one call: every block taken with alloc()
+// is freed on the call's stream when the guard goes out of scope, whichever
+// way the call returns (a failed allocation or CUDA call midway leaks
+// nothing); drop() frees one earlier.  Frees are stream-ordered, so kernels
+// already queued on the stream finish with the memory first.
+class Scratch {
+  public:
+    explicit Scratch(cudaStream_t s) : s_(s) {}
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    ~Scratch()
+    {
+        for (void *p : p_)
+            if (p) dfree_async(p, s_);
+    }
+    template <typename T>
+    cudaError_t alloc(T **p, size_t count)
+    {
+        const cudaError_t e = alloc_async(p, count, s_);
+        if (e == cudaSuccess) p_.push_back(*p);
+        return e;
+    }
+    cudaError_t drop(const void *q)
+    {
+        for (void *&p : p_)
+            if (p == q) {
+                void *x = p;
+                p = nullptr;
+                return dfree_async(x, s_);
+            }
+        return cudaSuccess;
+    }
+
+  private:
+    cudaStream_t s_;
+    std::vector<void *> p_;
+};
 
 // ---------------------------------------------------------------------------
 // Radix sort (sort.cu): ascending LSD sort of uint64 keys by bits
@@ -183,6 +241,8 @@ struct MsSlots {              // per-bit outputs and start levels
 struct MsServe;
 gb_status ms_serve_create(const gb_graph *g, int blocks, MsServe **out, cudaStream_t s);
 void ms_serve_destroy(MsServe *m);
+// Device bytes the state holds.
+size_t ms_serve_bytes(const MsServe *m);
 // Place `count` new queries (bit, root) into the frontier of `level` (the next
 // level to run); `table` is the full slot table to upload.
 gb_status ms_serve_admit(MsServe *m, int level, int count, const int *bits, const int64_t *roots,

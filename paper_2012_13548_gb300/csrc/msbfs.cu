@@ -797,12 +797,13 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     const size_t o_big = o_act + up(3 * (size_t)ntot * sizeof(int32_t));
     const size_t total = o_big + 2 * bigcap * sizeof(unsigned long long);
     unsigned char *ws = nullptr;
-    GB_CUDA(cudaMallocAsync((void **)&ws, total, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&ws, total));
     // vertex-major staging of parents and levels, [ntot][k] each
     int32_t *stage = nullptr;
-    GB_CUDA(cudaMallocAsync((void **)&stage, 2 * (size_t)ntot * k * sizeof(int32_t), s));
+    GB_CUDA(tmp.alloc(&stage, 2 * (size_t)ntot * k));
     T *hist = nullptr;  // reached-bit masks of the first MS_HIST levels
-    GB_CUDA(cudaMallocAsync((void **)&hist, (size_t)MS_HIST * np * sizeof(T), s));
+    GB_CUDA(tmp.alloc(&hist, (size_t)MS_HIST * np));
     GB_CUDA(cudaMemsetAsync(hist, 0, (size_t)MS_HIST * np * sizeof(T), s));
     for (int i = 0; i < ng; ++i) {
         gs[i].pst = stage + gs[i].voff * k;
@@ -843,9 +844,6 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)ms_kernel<T>, dim3(ctx->ms_blocks),
                                         dim3(MS_THREADS), args, 0, s));
     note_launch();
-    GB_CUDA(cudaFreeAsync(ws, s));
-    GB_CUDA(cudaFreeAsync(stage, s));
-    GB_CUDA(cudaFreeAsync(hist, s));
     return GB_OK;
 }
 
@@ -961,6 +959,7 @@ struct MsServe {
     int64_t bigcap = 0;
     int64_t mstride = 0;
     int blocks = 0;
+    size_t ws_bytes = 0;
     MsGraph graph_host;
 };
 
@@ -982,7 +981,8 @@ gb_status ms_serve_create(const gb_graph *g, int blocks, MsServe **out, cudaStre
     const size_t o_act = o_m + up(3 * m->mstride * 8);
     const size_t o_big = o_act + up(3 * (size_t)n * 4);
     const size_t total = o_big + 2 * m->bigcap * 8;
-    cudaError_t e = cudaMalloc((void **)&m->ws, total);
+    m->ws_bytes = total;
+    cudaError_t e = gb::dmalloc((void **)&m->ws, total);
     if (e != cudaSuccess) {
         delete m;
         return cuda_fail(e, "server workspace");
@@ -1006,20 +1006,28 @@ gb_status ms_serve_create(const gb_graph *g, int blocks, MsServe **out, cudaStre
     G.lst = nullptr;
     G.kst = 0;
     m->graph_host = G;
-    GB_CUDA(cudaMemsetAsync(m->ws, 0, o_big, s));
-    GB_CUDA(cudaMemcpyAsync(m->graph_dev, &m->graph_host, sizeof(MsGraph), cudaMemcpyHostToDevice, s));
-    ms_admit_clear_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->nz, n, m->seen, ~0ull);
-    note_launch();
-    GB_CUDA(cudaGetLastError());
-    GB_CUDA(cudaStreamSynchronize(s));
+    if ((e = cudaMemsetAsync(m->ws, 0, o_big, s)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(m->graph_dev, &m->graph_host, sizeof(MsGraph), cudaMemcpyHostToDevice, s)) ==
+            cudaSuccess) {
+        ms_admit_clear_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->nz, n, m->seen, ~0ull);
+        note_launch();
+        if ((e = cudaGetLastError()) == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        gb::dfree(m->ws);
+        delete m;
+        return cuda_fail(e, "server workspace");
+    }
     *out = m;
     return GB_OK;
 }
 
+size_t ms_serve_bytes(const MsServe *m) { return m ? m->ws_bytes : 0; }
+
 void ms_serve_destroy(MsServe *m)
 {
     if (!m) return;
-    if (m->ws) cudaFree(m->ws);
+    if (m->ws) gb::dfree(m->ws);
     delete m;
 }
 

@@ -45,7 +45,7 @@ double now_s()
     return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
 }
 
-enum QState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2, Q_RELEASED = 3 };
+enum QState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2, Q_RELEASED = 3, Q_CANCELLED = 4 };
 
 constexpr int64_t kPlainMinN = int64_t(1) << 14;  // graphs served one query per launch
 constexpr int kPlainSlots = 2;                    // concurrent searches per such graph
@@ -72,6 +72,7 @@ struct Query {
     double t_arrive = 0;
     double t_done = 0;
     int state = Q_QUEUED;
+    bool cancel = false;  // cancelled while running: released as soon as it finishes
     int slot = -1;
     int32_t *par = nullptr;
     int32_t *lev = nullptr;
@@ -90,7 +91,7 @@ struct GraphRun {
     std::deque<int64_t> pending;
     gb::MsSlots slots;
     bool plain = false;  // one query per launch (large graph)
-    // counters printed by server_destroy when GB_SERVE_DEBUG=1
+    // counters printed by server_destroy with the verbose option
     int64_t n_launch = 0, n_admit = 0;
     double t_launch = 0, busy_s = 0;
     int plain_blocks = 0;
@@ -111,9 +112,9 @@ bool take_out(GraphRun &G, OutBuf &b)
         return true;
     }
     OutBuf nb;
-    if (cudaMalloc((void **)&nb.par, (size_t)G.g->n * 4) != cudaSuccess) return false;
-    if (cudaMalloc((void **)&nb.lev, (size_t)G.g->n * 4) != cudaSuccess) {
-        cudaFree(nb.par);
+    if (gb::dmalloc(&nb.par, (size_t)G.g->n * 4) != cudaSuccess) return false;
+    if (gb::dmalloc(&nb.lev, (size_t)G.g->n * 4) != cudaSuccess) {
+        gb::dfree(nb.par);
         return false;
     }
     G.all_out.push_back(nb);
@@ -127,7 +128,9 @@ bool take_out(GraphRun &G, OutBuf &b)
 struct gb_server {
     int device = 0;
     size_t budget = 0;
-    size_t used = 0;
+    size_t used = 0;        // device bytes counted against the budget: fixed + admitted outputs
+    size_t fixed = 0;       // the server's own state (search workspaces, multi-source states)
+    gb_server_options opt;
     std::vector<GraphRun> gr;
     std::deque<Query> q;
     std::mutex mu;
@@ -143,6 +146,7 @@ struct gb_server {
     void run();
     bool step_graph(GraphRun &G);
     bool step_plain(GraphRun &G);
+    void finish(GraphRun &G, int64_t t, double when);
 };
 
 namespace {
@@ -150,6 +154,25 @@ namespace {
 size_t out_bytes(const gb_graph *g) { return (size_t)g->n * 8; }
 
 }  // namespace
+
+// A query's search ended (call with mu held): done, or, if it was cancelled
+// while running, released at once.
+void gb_server::finish(GraphRun &G, int64_t t, double when)
+{
+    Query &x = q[(size_t)t];
+    x.t_done = when;
+    x.slot = -1;
+    if (x.cancel) {
+        G.free_out.push_back(OutBuf{x.par, x.lev});
+        x.par = x.lev = nullptr;
+        x.state = Q_CANCELLED;
+        used -= out_bytes(G.g);
+        cv.notify_one();
+    } else {
+        x.state = Q_DONE;
+        if (tracing) finished.push_back(t);
+    }
+}
 
 // One pass over a large graph: finish completed searches, start new ones in
 // free slots while their outputs fit the budget.
@@ -171,10 +194,7 @@ bool gb_server::step_plain(GraphRun &G)
                 done.notify_all();
                 return false;
             }
-            Query &x = q[(size_t)P.q];
-            x.state = Q_DONE;
-            x.t_done = now_s();
-            if (tracing) finished.push_back(P.q);
+            finish(G, P.q, now_s());
             P.q = -1;
             done.notify_all();
         }
@@ -240,11 +260,7 @@ bool gb_server::step_graph(GraphRun &G)
         for (int b = 0; b < 64; ++b) {
             const unsigned long long bit = 1ull << b;
             if ((G.active & bit) && !(adv & bit)) {  // nothing new: this BFS is complete
-                Query &x = q[(size_t)G.slot_q[b]];
-                x.state = Q_DONE;
-                x.t_done = t;
-                x.slot = -1;
-                if (tracing) finished.push_back(G.slot_q[b]);
+                finish(G, G.slot_q[b], t);
                 G.active &= ~bit;
                 G.slot_q[b] = -1;
             }
@@ -322,7 +338,7 @@ void gb_server::run()
         }
         if (busy) std::this_thread::yield();
     }
-    if (std::getenv("GB_SERVE_DEBUG")) {
+    if (opt.verbose) {
         std::fprintf(stderr, "[server] worker iterations %lld over %.3f s\n", (long long)iters,
                      now_s() - t_start);
         for (size_t i = 0; i < gr.size(); ++i)
@@ -334,10 +350,36 @@ void gb_server::run()
 
 extern "C" {
 
+gb_status server_default_options(gb_server_options *out)
+{
+    if (!out) {
+        gb::set_error("server_default_options: NULL");
+        return GB_ERR_INVALID;
+    }
+    out->single_source_min_vertices = kPlainMinN;
+    out->slots_per_graph = kPlainSlots;
+    out->full_grid = 0;
+    out->verbose = 0;
+    return GB_OK;
+}
+
 gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb_server **out)
 {
-    if (!out || !gs || ng < 1) {
-        gb::set_error("server_create: need graphs and out");
+    gb_server_options o;
+    server_default_options(&o);
+    return server_create_with_options(gs, ng, mem_budget, &o, out);
+}
+
+gb_status server_create_with_options(const gb_graph *const *gs, int ng, size_t mem_budget,
+                                     const gb_server_options *opt, gb_server **out)
+{
+    if (!out || !gs || ng < 1 || !opt) {
+        gb::set_error("server_create: need graphs, options and out");
+        return GB_ERR_INVALID;
+    }
+    if (opt->slots_per_graph < 1 || opt->slots_per_graph > kMaxPlainSlots ||
+        opt->single_source_min_vertices < 0) {
+        gb::set_error("server_create: slots_per_graph must be 1..8 and single_source_min_vertices >= 0");
         return GB_ERR_INVALID;
     }
     *out = nullptr;
@@ -346,22 +388,11 @@ gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb
     gb_server *srv = new gb_server();
     srv->device = ctx->device;
     srv->budget = mem_budget;
+    srv->opt = *opt;
     srv->gr.resize(ng);
-    // GB_SERVE_PLAIN_MIN_SCALE overrides the size from which a graph is served
-    // one query per launch (1: every graph, 31: none).
-    int64_t plain_min = kPlainMinN;
-    if (const char *env = std::getenv("GB_SERVE_PLAIN_MIN_SCALE")) {
-        const int sc = std::atoi(env);
-        if (sc >= 0 && sc <= 31) plain_min = int64_t(1) << sc;
-    }
-    // GB_SERVE_SLOTS: concurrent single-source searches per graph (1..8), each
-    // on an equal share of the device's SMs (GB_SERVE_FULL_GRID=1: whole grid each)
-    int nplain = kPlainSlots;
-    if (const char *env = std::getenv("GB_SERVE_SLOTS")) {
-        const int k = std::atoi(env);
-        if (k >= 1 && k <= kMaxPlainSlots) nplain = k;
-    }
-    const bool full_grid = std::getenv("GB_SERVE_FULL_GRID") != nullptr;
+    const int64_t plain_min = opt->single_source_min_vertices;
+    const int nplain = opt->slots_per_graph;
+    const bool full_grid = opt->full_grid != 0;
     int64_t ntot = 0;  // vertices of the graphs batched as bits (the small ones)
     for (int i = 0; i < ng; ++i) ntot += (gs[i] && gs[i]->n < plain_min) ? gs[i]->n : 0;
     gb_status rc = GB_OK;
@@ -385,13 +416,14 @@ gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb
             G.plain_blocks = full_grid ? ctx->bfs_blocks2 : std::max(8, ctx->bfs_blocks2 / nplain);
             for (int k = 0; k < nplain && rc == GB_OK; ++k) {
                 PlainSlot &P = G.ps[k];
-                if (cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking) != cudaSuccess ||
-                    cudaEventCreateWithFlags(&P.ev, cudaEventDisableTiming) != cudaSuccess ||
-                    cudaMalloc((void **)&P.stats, sizeof(gb::BfsDevStats)) != cudaSuccess ||
-                    cudaMalloc((void **)&P.ws, gb::bfs_workspace_bytes(G.g)) != cudaSuccess) {
-                    gb::set_error("server_create: stream/event/stats buffer");
-                    rc = GB_ERR_CUDA;
+                cudaError_t e = cudaSuccess;
+                if ((e = cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+                    (e = cudaEventCreateWithFlags(&P.ev, cudaEventDisableTiming)) != cudaSuccess ||
+                    (e = gb::dmalloc(&P.stats, sizeof(gb::BfsDevStats))) != cudaSuccess ||
+                    (e = gb::dmalloc(&P.ws, gb::bfs_workspace_bytes(G.g))) != cudaSuccess) {
+                    rc = gb::cuda_fail(e, "server_create: slot stream, event or workspace");
                 }
+                srv->fixed += sizeof(gb::BfsDevStats) + gb::bfs_workspace_bytes(G.g);
             }
             continue;
         }
@@ -408,12 +440,20 @@ gb_status server_create(const gb_graph *const *gs, int ng, size_t mem_budget, gb
             break;
         }
         rc = gb::ms_serve_create(G.g, blocks, &G.ms, G.stream);
+        if (rc == GB_OK) srv->fixed += gb::ms_serve_bytes(G.ms);
     }
+    if (rc == GB_OK && srv->fixed > mem_budget) {
+        gb::set_error("server_create: the memory budget (" + std::to_string(mem_budget) +
+                      " bytes) does not hold the server's own search state (" +
+                      std::to_string(srv->fixed) + " bytes)");
+        rc = GB_ERR_NOMEM;
+    }
+    srv->used = srv->fixed;
     if (rc != GB_OK) {
         for (auto &G : srv->gr) {
             for (auto &P : G.ps) {
-                if (P.ws) cudaFree(P.ws);
-                if (P.stats) cudaFree(P.stats);
+                if (P.ws) gb::dfree(P.ws);
+                if (P.stats) gb::dfree(P.stats);
                 if (P.ev) cudaEventDestroy(P.ev);
                 if (P.stream) cudaStreamDestroy(P.stream);
             }
@@ -471,8 +511,9 @@ gb_status server_poll(gb_server *srv, int64_t ticket, const int32_t **parent,
         return GB_ERR_INVALID;
     }
     const Query &x = srv->q[(size_t)ticket];
-    if (x.state == Q_RELEASED) {
-        gb::set_error("server_poll: ticket already released");
+    if (x.state == Q_RELEASED || x.state == Q_CANCELLED || x.cancel) {
+        gb::set_error(x.state == Q_RELEASED ? "server_poll: ticket already released"
+                                            : "server_poll: query cancelled");
         return GB_ERR_INVALID;
     }
     if (x.state != Q_DONE) return GB_ERR_BUSY;
@@ -500,6 +541,62 @@ gb_status server_release(gb_server *srv, int64_t ticket)
     x.state = Q_RELEASED;
     srv->used -= out_bytes(G.g);
     srv->cv.notify_one();
+    return GB_OK;
+}
+
+gb_status server_cancel(gb_server *srv, int64_t ticket)
+{
+    if (!srv) return GB_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (ticket < 0 || ticket >= (int64_t)srv->q.size()) {
+        gb::set_error("server_cancel: unknown ticket");
+        return GB_ERR_INVALID;
+    }
+    Query &x = srv->q[(size_t)ticket];
+    GraphRun &G = srv->gr[x.graph];
+    switch (x.state) {
+    case Q_QUEUED: {
+        auto it = std::find(G.pending.begin(), G.pending.end(), ticket);
+        if (it != G.pending.end()) G.pending.erase(it);
+        x.state = Q_CANCELLED;
+        return GB_OK;
+    }
+    case Q_RUNNING:
+        if (x.cancel) break;
+        x.cancel = true;  // its search runs out; finish() releases it
+        return GB_OK;
+    case Q_DONE:
+        G.free_out.push_back(OutBuf{x.par, x.lev});
+        x.par = x.lev = nullptr;
+        x.state = Q_CANCELLED;
+        srv->used -= out_bytes(G.g);
+        srv->cv.notify_one();
+        return GB_OK;
+    default:
+        break;
+    }
+    gb::set_error("server_cancel: query already released or cancelled");
+    return GB_ERR_INVALID;
+}
+
+gb_status server_stats(gb_server *srv, gb_server_stats *out)
+{
+    if (!srv || !out) {
+        gb::set_error("server_stats: NULL");
+        return GB_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *out = gb_server_stats{};
+    out->budget_bytes = (int64_t)srv->budget;
+    out->fixed_bytes = (int64_t)srv->fixed;
+    out->used_bytes = (int64_t)srv->used;
+    for (const Query &x : srv->q) {
+        if (x.state == Q_QUEUED) ++out->queued;
+        else if (x.state == Q_RUNNING) ++out->running;
+        else if (x.state == Q_DONE) ++out->done;
+        else if (x.state == Q_RELEASED) ++out->released;
+        else if (x.state == Q_CANCELLED) ++out->cancelled;
+    }
     return GB_OK;
 }
 
@@ -604,12 +701,12 @@ gb_status server_destroy(gb_server *srv)
     }
     for (auto &G : srv->gr) {
         for (auto &b : G.all_out) {
-            cudaFree(b.par);
-            cudaFree(b.lev);
+            gb::dfree(b.par);
+            gb::dfree(b.lev);
         }
         for (auto &P : G.ps) {
-            if (P.ws) cudaFree(P.ws);
-            if (P.stats) cudaFree(P.stats);
+            if (P.ws) gb::dfree(P.ws);
+            if (P.stats) gb::dfree(P.stats);
             if (P.ev) cudaEventDestroy(P.ev);
             if (P.stream) cudaStreamDestroy(P.stream);
         }

@@ -270,9 +270,10 @@ gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_
 
     unsigned long long *hist = nullptr, *base = nullptr;
     unsigned *status = nullptr;
-    GB_CUDA(alloc_async(&hist, (size_t)passes * 256, s));
-    GB_CUDA(alloc_async(&base, (size_t)passes * (portions + 1) * 256, s));
-    GB_CUDA(alloc_async(&status, 1 + (size_t)tiles_max * 256, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&hist, (size_t)passes * 256));
+    GB_CUDA(tmp.alloc(&base, (size_t)passes * (portions + 1) * 256));
+    GB_CUDA(tmp.alloc(&status, 1 + (size_t)tiles_max * 256));
     GB_CUDA(cudaMemsetAsync(hist, 0, (size_t)passes * 256 * sizeof(unsigned long long), s));
 
     const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 4, (n + 511) / 512));
@@ -307,9 +308,6 @@ gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_
         std::swap(kc, ka);
         std::swap(vc, va);
     }
-    GB_CUDA(cudaFreeAsync(hist, s));
-    GB_CUDA(cudaFreeAsync(base, s));
-    GB_CUDA(cudaFreeAsync(status, s));
     *keys_out = kc;
     if (vals_out) *vals_out = vc;
     return GB_OK;

@@ -870,7 +870,7 @@ gb_status build_csr_weighted(const int64_t *edges, const float *w, int64_t m, in
     gb_status rc = build_csr(edges, m, scale, g, s);
     if (rc != GB_OK) return rc;
     Context *ctx = context();
-    GB_CUDA(cudaMalloc(&g->wgt, std::max<int64_t>(g->nnz, 4) * sizeof(uint32_t)));
+    GB_CUDA(gb::dmalloc(&g->wgt, std::max<int64_t>(g->nnz, 4) * sizeof(uint32_t)));
     GB_CUDA(cudaMemsetAsync(g->wgt, 0xff, std::max<int64_t>(g->nnz, 4) * sizeof(uint32_t), s));
     if (m > 0) {
         wt_attach_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(edges, w, m, g->off, g->col, g->n, g->wgt,
@@ -890,14 +890,15 @@ gb_status build_csr_weighted(const int64_t *edges, const float *w, int64_t m, in
     }
     // the rows by ascending weight: one sort of (row << 25 | weight) keys with the columns
     const int64_t nnz = g->nnz;
-    GB_CUDA(cudaMalloc(&g->wadj, std::max<int64_t>(nnz, 4) * sizeof(uint2)));
+    GB_CUDA(gb::dmalloc(&g->wadj, std::max<int64_t>(nnz, 4) * sizeof(uint2)));
     if (nnz > 0) {
         uint64_t *k0 = nullptr, *k1 = nullptr, *ks = nullptr;
         uint32_t *v0 = nullptr, *v1 = nullptr, *vs = nullptr;
-        GB_CUDA(alloc_async(&k0, (size_t)nnz, s));
-        GB_CUDA(alloc_async(&k1, (size_t)nnz, s));
-        GB_CUDA(alloc_async(&v0, (size_t)nnz, s));
-        GB_CUDA(alloc_async(&v1, (size_t)nnz, s));
+        Scratch tmp(s);
+        GB_CUDA(tmp.alloc(&k0, (size_t)nnz));
+        GB_CUDA(tmp.alloc(&k1, (size_t)nnz));
+        GB_CUDA(tmp.alloc(&v0, (size_t)nnz));
+        GB_CUDA(tmp.alloc(&v1, (size_t)nnz));
         wsort_keys_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(g->off, g->col, g->wgt, g->n, k0, v0);
         note_launch();
         GB_CUDA(cudaGetLastError());
@@ -906,10 +907,6 @@ gb_status build_csr_weighted(const int64_t *edges, const float *w, int64_t m, in
         wsort_pack_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(ks, vs, nnz, g->wadj);
         note_launch();
         GB_CUDA(cudaGetLastError());
-        GB_CUDA(cudaFreeAsync(k0, s));
-        GB_CUDA(cudaFreeAsync(k1, s));
-        GB_CUDA(cudaFreeAsync(v0, s));
-        GB_CUDA(cudaFreeAsync(v1, s));
     }
     GB_CUDA(cudaStreamSynchronize(s));
     return GB_OK;
@@ -940,7 +937,8 @@ gb_status sssp_impl(const gb_graph *g, int64_t root, double delta, double *dist,
     const size_t o_bq = o_sq + al(4 * (size_t)n);
     const size_t total = o_bq + al(24 * (size_t)bigcap);
     unsigned char *ws = nullptr;
-    GB_CUDA(cudaMallocAsync((void **)&ws, total, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&ws, total));
     GB_CUDA(cudaMemsetAsync(ws, 0, sizeof(SpHeader), s));
     SpArgs a;
     a.off = g->off;
@@ -980,7 +978,6 @@ gb_status sssp_impl(const gb_graph *g, int64_t root, double delta, double *dist,
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)sssp_kernel, dim3(blocks), dim3(SP_THREADS), args,
                                         0, s));
     note_launch();
-    GB_CUDA(cudaFreeAsync(ws, s));
     return GB_OK;
 }
 
@@ -1008,7 +1005,8 @@ gb_status sssp_validate_impl(const gb_graph *g, int64_t root, const int32_t *par
         return GB_OK;
     }
     SvAcc *acc = nullptr;
-    GB_CUDA(alloc_async(&acc, 1, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&acc, 1));
     const int grid = ctx->num_sms * 8;
     sv_init_kernel<<<1, 1, 0, s>>>(acc);
     note_launch();
@@ -1027,7 +1025,7 @@ gb_status sssp_validate_impl(const gb_graph *g, int64_t root, const int32_t *par
     GB_CUDA(cudaGetLastError());
     SvAcc h;
     GB_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaFreeAsync(acc, s));
+    GB_CUDA(tmp.drop(acc));
     GB_CUDA(cudaStreamSynchronize(s));
     r.reached = (int64_t)h.reached;
     r.component_edges = (int64_t)(h.deg_sum / 2);

@@ -222,7 +222,8 @@ gb_status validate_impl(const gb_graph *g, int64_t root, const int32_t *parent, 
         return GB_OK;
     }
     ValAcc *acc = nullptr;
-    GB_CUDA(alloc_async(&acc, 1, s));
+    Scratch tmp(s);
+    GB_CUDA(tmp.alloc(&acc, 1));
     const int grid = ctx->num_sms * 8;
     val_init_kernel<<<1, 1, 0, s>>>(acc);
     note_launch();
@@ -241,7 +242,7 @@ gb_status validate_impl(const gb_graph *g, int64_t root, const int32_t *parent, 
     GB_CUDA(cudaGetLastError());
     ValAcc h;
     GB_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaFreeAsync(acc, s));
+    GB_CUDA(tmp.drop(acc));
     GB_CUDA(cudaStreamSynchronize(s));
     r.reached = (int64_t)h.reached;
     r.component_edges = (int64_t)(h.deg_sum / 2);

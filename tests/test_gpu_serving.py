@@ -67,10 +67,19 @@ def test_burst_larger_than_the_slots(resident, canonical):
     gb.gb_device_status()
 
 
+def fixed_bytes(graphs, **options):
+    """The device bytes of a server's own state over these graphs."""
+    srv = gb.Server(graphs, mem_budget=1 << 40, **options)
+    f = srv.stats()["fixed_bytes"]
+    srv.close()
+    return f
+
+
 def test_admission_by_memory(resident):
     graphs, offs = resident
-    # room for the outputs of two queries on the largest graph at a time
-    budget = 2 * 8 * graphs[-1].n
+    # room for the server's own state and the outputs of two queries on the
+    # largest graph at a time
+    budget = fixed_bytes(graphs) + 2 * 8 * graphs[-1].n
     srv = gb.Server(graphs, mem_budget=budget)
     rng = np.random.default_rng(12)
     queries = [(3, int(r)) for r in W.root_from_draw(offs[3], rng.integers(0, 2**62, size=40))]
@@ -136,14 +145,126 @@ def test_large_graphs_run_one_search_per_query():
     for _ in range(60):
         gi = int(rng.integers(0, 2))
         queries.append((gi, int(W.root_from_draw(offs[gi], rng.integers(0, 2**62, size=1))[0])))
-    srv = gb.Server(graphs, mem_budget=3 * 8 * big.n)   # at most three large-graph queries at once
+    # at most three large-graph queries at once
+    srv = gb.Server(graphs, mem_budget=fixed_bytes(graphs) + 3 * 8 * big.n)
     tickets = [srv.submit(gi, r) for gi, r in queries]
     for t, (gi, r) in zip(tickets, queries):
         par, lev = srv.result(t, gi)
         p_alone, l_alone = gb.bfs(graphs[gi], r)
         assert torch.equal(lev, l_alone), (gi, r)
         assert torch.equal(par, p_alone), (gi, r)
+        # and against the oracle: levels and the canonical (smallest-id) tree
+        _, off, col = oracle_graph(21 if gi == 1 else 12)
+        p_ref, l_ref = oracle.bfs(off, col, r)
+        assert np.array_equal(lev.cpu().numpy(), l_ref), (gi, r)
+        assert np.array_equal(par.cpu().numpy(), p_ref), (gi, r)
         srv.release(t)
     srv.close()
     gb.bfs_set_options(canonical_parents=0)
     gb.gb_device_status()
+
+
+def test_budget_must_hold_the_servers_own_state(resident):
+    graphs, _ = resident
+    f = fixed_bytes(graphs)
+    assert f > 0
+    with pytest.raises(gb.GbError, match="NOMEM"):
+        gb.Server(graphs, mem_budget=f - 1)
+    srv = gb.Server(graphs, mem_budget=f)    # holds its state, admits nothing yet
+    st = srv.stats()
+    assert st["fixed_bytes"] == f and st["used_bytes"] == f and st["budget_bytes"] == f
+    srv.close()
+
+
+@pytest.mark.parametrize("options", [dict(single_source_min_vertices=0),
+                                     dict(single_source_min_vertices=1 << 40),
+                                     dict(slots_per_graph=1), dict(slots_per_graph=8),
+                                     dict(full_grid=1)])
+def test_server_options_give_the_same_results(resident, options):
+    # every way of serving (single-source slots for every graph, bit slots for
+    # every graph, one or eight slots per graph, whole-grid launches) gives
+    # each query the result it has alone
+    graphs, offs = resident
+    gb.bfs_set_options(canonical_parents=1)
+    rng = np.random.default_rng(31)
+    queries = [(gi, int(W.root_from_draw(offs[gi], rng.integers(0, 2**62, size=1))[0]))
+               for gi in rng.integers(0, len(graphs), size=80)]
+    srv = gb.Server(graphs, mem_budget=1 << 34, **options)
+    tickets = [srv.submit(gi, r) for gi, r in queries]
+    _check_results(srv, graphs, tickets, queries, canonical=True)
+    srv.close()
+    gb.bfs_set_options(canonical_parents=0)
+    with pytest.raises(gb.GbError, match="INVALID"):
+        gb.Server(graphs, mem_budget=1 << 30, slots_per_graph=9)
+    with pytest.raises(KeyError):
+        gb.Server(graphs, mem_budget=1 << 30, no_such_option=1)
+
+
+def test_cancelled_queries_free_their_memory_and_others_complete(resident):
+    graphs, offs = resident
+    rng = np.random.default_rng(41)
+    f = fixed_bytes(graphs)
+    srv = gb.Server(graphs, mem_budget=f + 4 * 8 * graphs[-1].n)
+    queries = [(int(gi), int(W.root_from_draw(offs[gi], rng.integers(0, 2**62, size=1))[0]))
+               for gi in rng.integers(0, len(graphs), size=120)]
+    tickets = [srv.submit(gi, r) for gi, r in queries]
+    cancelled = set(tickets[::3])              # queued, running or done: all cancellable
+    for t in sorted(cancelled):
+        srv.cancel(t)
+    with pytest.raises(gb.GbError, match="INVALID"):
+        srv.cancel(tickets[0])                  # twice
+    keep = [(t, q) for t, q in zip(tickets, queries) if t not in cancelled]
+    _check_results(srv, graphs, [t for t, _ in keep], [q for _, q in keep], canonical=False)
+    for t in sorted(cancelled):
+        with pytest.raises(gb.GbError, match="INVALID"):
+            srv.poll(t)
+    # every buffer is back: running cancelled queries release theirs as they end
+    import time
+    t0 = time.time()
+    while srv.stats()["used_bytes"] != f and time.time() - t0 < 30:
+        time.sleep(0.01)
+    st = srv.stats()
+    assert st["used_bytes"] == f, st
+    assert st["cancelled"] == len(cancelled) and st["released"] == len(keep), st
+    srv.close()
+    gb.gb_device_status()
+
+
+def test_a_slow_consumer_holds_its_memory_and_the_rest_waits(resident):
+    # a client that keeps its results (does not release them) holds their
+    # memory: with room for two queries, the third waits until one is
+    # released, then completes; nothing is lost or run twice
+    graphs, offs = resident
+    f = fixed_bytes(graphs)
+    srv = gb.Server(graphs, mem_budget=f + 2 * 8 * graphs[-1].n)
+    roots = [int(r) for r in W.root_from_draw(offs[-1], np.arange(3, dtype=np.uint64) * 977 + 5)]
+    t = [srv.submit(len(graphs) - 1, r) for r in roots]
+    srv.result(t[0], len(graphs) - 1)
+    srv.result(t[1], len(graphs) - 1)
+    import time
+    time.sleep(0.2)
+    assert srv.poll(t[2]) is None               # still waiting for memory
+    assert srv.stats()["queued"] == 1
+    srv.release(t[0])
+    par, lev = srv.result(t[2], len(graphs) - 1)
+    _, l_alone = gb.bfs(graphs[-1], roots[2])
+    assert torch.equal(lev, l_alone)
+    srv.release(t[1])
+    srv.release(t[2])
+    srv.close()
+
+
+def test_injected_allocation_failures_delay_queries_but_lose_none(resident):
+    # output buffers that cannot be allocated now are retried: the queries wait
+    # and complete once allocations succeed again
+    graphs, offs = resident
+    srv = gb.Server(graphs, mem_budget=1 << 34)
+    gb.debug_fail_allocations(0, 6)
+    queries = [(gi, int(W.root_from_draw(offs[gi], np.array([7 + gi], dtype=np.uint64))[0]))
+               for gi in range(len(graphs))]
+    tickets = [srv.submit(gi, r) for gi, r in queries]
+    import time
+    time.sleep(0.2)
+    gb.debug_fail_allocations(0, 0)
+    _check_results(srv, graphs, tickets, queries, canonical=False)
+    srv.close()
