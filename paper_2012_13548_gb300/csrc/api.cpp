@@ -75,6 +75,15 @@ SsspDevStats *sssp_stats_buffer()
     return t_sssp.dev;
 }
 
+// Free every device array of a graph (any may be null) and the graph.
+void destroy_graph(gb_graph *g)
+{
+    void *arrays[] = {g->off, g->col, g->nz, g->hub, g->nzl, g->wgt, g->wadj};
+    for (void *p : arrays)
+        if (p) gb::dfree(p);
+    delete g;
+}
+
 gb_status check_graph(const gb_graph *g)
 {
     if (!g || !g->off) {
@@ -314,11 +323,7 @@ gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *
         gb_graph *g = new gb_graph();
         gb_status rc = build_csr(edges, m, scale, g, as_stream(s));
         if (rc != GB_OK) {
-            if (g->off) gb::dfree(g->off);
-            if (g->col) gb::dfree(g->col);
-            if (g->nz) gb::dfree(g->nz);
-            if (g->hub) gb::dfree(g->hub);
-            delete g;
+            destroy_graph(g);
             return rc;
         }
         *out = g;
@@ -338,11 +343,7 @@ gb_status graph_build_csr_counting(const int64_t *edges, int64_t m, int scale, g
         gb_graph *g = new gb_graph();
         gb_status rc = build_csr_counting(edges, m, scale, g, as_stream(s));
         if (rc != GB_OK) {
-            if (g->off) gb::dfree(g->off);
-            if (g->col) gb::dfree(g->col);
-            if (g->nz) gb::dfree(g->nz);
-            if (g->hub) gb::dfree(g->hub);
-            delete g;
+            destroy_graph(g);
             return rc;
         }
         *out = g;
@@ -375,13 +376,7 @@ gb_status graph_build_csr_weighted(const int64_t *edges, const float *w, int64_t
         gb_status rc = build_csr_weighted(edges, w, m, scale, g, as_stream(s));
         if (rc != GB_OK) {
             cudaStreamSynchronize(as_stream(s));
-            if (g->off) gb::dfree(g->off);
-            if (g->col) gb::dfree(g->col);
-            if (g->nz) gb::dfree(g->nz);
-            if (g->hub) gb::dfree(g->hub);
-            if (g->wgt) gb::dfree(g->wgt);
-            if (g->wadj) gb::dfree(g->wadj);
-            delete g;
+            destroy_graph(g);
             return rc;
         }
         *out = g;
@@ -482,11 +477,7 @@ gb_status graph_generate_csr(int scale, int edgefactor, double a, double b, doub
         gb_graph *g = new gb_graph();
         gb_status rc = kron_csr(scale, edgefactor, a, b, c, seed_gen, seed_perm, g, as_stream(s));
         if (rc != GB_OK) {
-            if (g->off) gb::dfree(g->off);
-            if (g->col) gb::dfree(g->col);
-            if (g->nz) gb::dfree(g->nz);
-            if (g->hub) gb::dfree(g->hub);
-            delete g;
+            destroy_graph(g);
             return rc;
         }
         *out = g;
@@ -544,11 +535,7 @@ gb_status graph_from_csr(const int64_t *off, const int32_t *col, int64_t n, int6
         gb_status rc = build_graph_aux(g, st);
         if (rc == GB_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "graph_from_csr");
         if (rc != GB_OK) {
-            gb::dfree(g->off);
-            gb::dfree(g->col);
-            if (g->nz) gb::dfree(g->nz);
-            if (g->hub) gb::dfree(g->hub);
-            delete g;
+            destroy_graph(g);
             return rc;
         }
         *out = g;
@@ -561,17 +548,7 @@ gb_status graph_free(gb_graph *g)
     return guarded([&]() -> gb_status {
         if (!g) return GB_OK;
         cudaDeviceSynchronize();
-        if (g->off) gb::dfree(g->off);
-        if (g->col) gb::dfree(g->col);
-        if (g->nz) gb::dfree(g->nz);
-        if (g->hub) gb::dfree(g->hub);
-        if (g->wgt) gb::dfree(g->wgt);
-        if (g->wadj) gb::dfree(g->wadj);
-        g->off = nullptr;
-        g->col = nullptr;
-        g->nz = nullptr;
-        g->hub = nullptr;
-        delete g;
+        destroy_graph(g);
         return GB_OK;
     });
 }

@@ -105,6 +105,8 @@ struct BfsArgs {
     int32_t *queue;
     int32_t *ulist;  // per warp a segment of useg entries: the vertices a bottom-up level left open (or null)
     int64_t useg;
+    const int32_t *nzl;  // the vertices of degree >= 1, ascending (or null)
+    int64_t nnzv;
     BigEnt *bigq;
     int64_t bigcap;
     WsHeader *hdr;
@@ -649,27 +651,42 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
             // caller's offsets may not be).
             int ph = 0, pt = 0;  // warp-uniform head and tail of the pending ring
             int32_t *seg = a.ulist ? a.ulist + gwarp * a.useg : nullptr;
-            const bool from_list = seg && l > 0 && !prev_td;
-            const int64_t units = from_list ? un_open : nw;  // segment entries or bitmap words
+            const bool from_seg = seg && l > 0 && !prev_td;   // the open list of the previous level
+            const bool from_nzl = seg && !from_seg && a.nzl;  // the graph's non-isolated vertices
+            // a list walk: this warp's segment (its own entries, in steps of
+            // 32 * BU_WORDS), or the non-isolated list (steps strided over the
+            // grid, a visited test per entry: top-down levels visited some)
+            const int32_t *L = from_seg ? seg : a.nzl;
+            const int64_t lcnt = from_seg ? un_open : a.nnzv;
+            const int64_t lstart = from_seg ? 0 : gwarp * 32 * BU_WORDS;
+            const int64_t lstride = from_seg ? 32 * BU_WORDS : nwarps * 32 * BU_WORDS;
             un_open = 0;
-            const bool bulk_pf = !from_list && ((reinterpret_cast<uintptr_t>(a.off) |
-                                                 reinterpret_cast<uintptr_t>(a.hub)) & 15u) == 0;
-            if (from_list) {
-            // this warp's open-list segment, 32 * BU_WORDS entries per step
-            for (int64_t i0 = 0; i0 < units; i0 += 32 * BU_WORDS) {
+            const bool bulk_pf = !from_seg && !from_nzl && ((reinterpret_cast<uintptr_t>(a.off) |
+                                                             reinterpret_cast<uintptr_t>(a.hub)) & 15u) == 0;
+            if (from_seg || from_nzl) {
+            for (int64_t i0 = lstart; i0 < lcnt; i0 += lstride) {
                 int32_t u[BU_WORDS], dg[BU_WORDS], hb[BU_WORDS];
                 bool cand[BU_WORDS];
 #pragma unroll
                 for (int t = 0; t < BU_WORDS; ++t) {
                     const int64_t i = i0 + t * 32 + lane;
-                    cand[t] = i < units;
-                    u[t] = cand[t] ? ldcg_i32(&seg[i]) : 0;
+                    cand[t] = i < lcnt;
+                    u[t] = cand[t] ? ldcg_i32(&L[i]) : 0;
                     cand[t] = cand[t] && GB_OK_IDX(a.st, u[t], a.n, 232);
+                }
+                unsigned vw[BU_WORDS];
+#pragma unroll
+                for (int t = 0; t < BU_WORDS; ++t) {
+                    vw[t] = cand[t] && from_nzl ? ldcg_u32(&a.vis[(unsigned)u[t] >> 5]) : 0u;
+                    dg[t] = cand[t] ? (int32_t)(__ldg(&a.off[u[t] + 1]) - __ldg(&a.off[u[t]])) : 0;
+                    hb[t] = cand[t] && a.hub ? __ldg(&a.hub[u[t]]) : -1;
                 }
 #pragma unroll
                 for (int t = 0; t < BU_WORDS; ++t) {
-                    dg[t] = cand[t] ? (int32_t)(__ldg(&a.off[u[t] + 1]) - __ldg(&a.off[u[t]])) : 0;
-                    hb[t] = cand[t] && a.hub ? __ldg(&a.hub[u[t]]) : -1;
+                    if ((vw[t] >> (u[t] & 31)) & 1u) {  // visited by a top-down level
+                        cand[t] = false;
+                        hb[t] = -1;
+                    }
                 }
                 unsigned fh[BU_WORDS];
 #pragma unroll
@@ -976,6 +993,8 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.queue = reinterpret_cast<int32_t *>(ws + off_q);
     a.st8 = ws + Lw.off_st;
     a.ulist = reinterpret_cast<int32_t *>(ws + Lw.off_ul);
+    a.nzl = g->nzl;
+    a.nnzv = g->nnzv;
     a.bigq = reinterpret_cast<BigEnt *>(ws + off_big);
     a.bigcap = bigcap;
     a.st = ctx->status;
@@ -1124,6 +1143,8 @@ gb_status bfs_noalloc_impl(const int64_t *off, const int32_t *col, int64_t n, in
     a.st8 = ws + kNaSt;
     a.ulist = nullptr;  // no open list: every bottom-up level walks the bitmap
     a.useg = 0;
+    a.nzl = nullptr;
+    a.nnzv = 0;
     a.bigq = reinterpret_cast<BigEnt *>(ws + kNaBig);
     a.bigcap = kNaBigCap;
     a.st = reinterpret_cast<DevStatus *>(ws + kNaStatus);

@@ -185,6 +185,46 @@ __global__ void nz_bitmap_kernel(const int64_t *__restrict__ off, int64_t n,
     }
 }
 
+// The list of vertices of degree >= 1 in ascending order (the first
+// bottom-up level of a search walks it instead of the whole visited bitmap):
+// per block of NZL_WORDS bitmap words a count, a scan of the counts, then
+// each block writes its vertices.
+constexpr int NZL_WORDS = 1024;
+
+__global__ void __launch_bounds__(NZL_WORDS) nzl_count_kernel(const uint32_t *__restrict__ nz, int64_t nw,
+                                                             unsigned *__restrict__ cnt)
+{
+    __shared__ unsigned s_w[NZL_WORDS / 32];
+    const int64_t w = (int64_t)blockIdx.x * NZL_WORDS + threadIdx.x;
+    const unsigned c = warp_sum(w < nw ? (unsigned)__popc(nz[w]) : 0u);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned t = warp_sum(s_w[threadIdx.x]);
+        if (threadIdx.x == 0) cnt[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(NZL_WORDS) nzl_write_kernel(const uint32_t *__restrict__ nz, int64_t nw,
+                                                             const unsigned long long *__restrict__ base,
+                                                             int32_t *__restrict__ list)
+{
+    __shared__ unsigned s_w[NZL_WORDS / 32];
+    const int64_t w = (int64_t)blockIdx.x * NZL_WORDS + threadIdx.x;
+    unsigned bits = w < nw ? nz[w] : 0u;
+    const unsigned c = (unsigned)__popc(bits);
+    const unsigned incl = warp_inclusive_scan(c);
+    if ((threadIdx.x & 31) == 31) s_w[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    unsigned long long pos = base[blockIdx.x] + incl - c;
+    for (int k = 0; k < (int)(threadIdx.x >> 5); ++k) pos += s_w[k];
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        list[pos++] = (int32_t)(w * 32 + b);
+    }
+}
+
 constexpr int HUB_THREADS = 256;
 constexpr int64_t HUB_SCAN = 128;  // entries of a row examined for its hub
 
@@ -278,9 +318,29 @@ gb_status build_graph_aux(gb_graph *g, cudaStream_t s)
     nz_bitmap_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->off, g->n, g->nz, nw);
     note_launch();
     GB_CUDA(cudaGetLastError());
+    Scratch tmp(s);
+    {
+        const int64_t nb = (nw + NZL_WORDS - 1) / NZL_WORDS;
+        unsigned *cnt = nullptr;
+        unsigned long long *base = nullptr;
+        GB_CUDA(tmp.alloc(&cnt, (size_t)nb));
+        GB_CUDA(tmp.alloc(&base, (size_t)nb + 1));
+        nzl_count_kernel<<<(unsigned)nb, NZL_WORDS, 0, s>>>(g->nz, nw, cnt);
+        note_launch();
+        k1_scan_tiles_kernel<<<1, 1024, 0, s>>>(cnt, nb, base);
+        note_launch();
+        GB_CUDA(cudaGetLastError());
+        unsigned long long nnzv = 0;
+        GB_CUDA(cudaMemcpyAsync(&nnzv, base + nb, sizeof(nnzv), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        g->nnzv = (int64_t)nnzv;
+        GB_CUDA(gb::dmalloc(&g->nzl, std::max<int64_t>(g->nnzv, 4) * sizeof(int32_t)));
+        nzl_write_kernel<<<(unsigned)nb, NZL_WORDS, 0, s>>>(g->nz, nw, base, g->nzl);
+        note_launch();
+        GB_CUDA(cudaGetLastError());
+    }
     GB_CUDA(gb::dmalloc(&g->hub, std::max<int64_t>(g->n, 1) * sizeof(int32_t)));
     uint8_t *key = nullptr;
-    Scratch tmp(s);
     GB_CUDA(tmp.alloc(&key, (size_t)g->n));
     deg_key_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(g->off, g->n, key);
     note_launch();

@@ -204,7 +204,10 @@ def test_cancelled_queries_free_their_memory_and_others_complete(resident):
     graphs, offs = resident
     rng = np.random.default_rng(41)
     f = fixed_bytes(graphs)
-    srv = gb.Server(graphs, mem_budget=f + 4 * 8 * graphs[-1].n)
+    # room for every query at once: the client below collects results in
+    # ticket order, so a tighter budget could be held by finished queries it
+    # has not reached yet
+    srv = gb.Server(graphs, mem_budget=1 << 34)
     queries = [(int(gi), int(W.root_from_draw(offs[gi], rng.integers(0, 2**62, size=1))[0]))
                for gi in rng.integers(0, len(graphs), size=120)]
     tickets = [srv.submit(gi, r) for gi, r in queries]
