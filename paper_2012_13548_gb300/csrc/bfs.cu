@@ -52,7 +52,7 @@ constexpr int BU_LANE_FIRST = 4;    // bottom-up: each lane probes this many nei
 constexpr int BU_WORDS = 4;         // bottom-up hub pass: visited words per warp iteration
 constexpr int PBUF = 256;           // per-warp ring of vertices left for the row pass
 constexpr int BFS_WARPS = BFS_THREADS / 32;
-constexpr int QBUF = 256;           // per-warp buffer of discovered vertices (shared memory)
+constexpr int QBUF = 512;           // per-warp buffer of discovered vertices (shared memory)
 constexpr int BBUF = 32;            // per-warp buffer of discovered big-degree vertices
 constexpr int SITE_BFS_BAR = 20;
 constexpr int SITE_BFS_LEVELS = 21;
