@@ -560,7 +560,7 @@ def run_ours(args, dist):
     mean_bytes = statistics.mean(alg)
     mean_ms = statistics.mean(flat_ms)
     achieved = mean_bytes / (mean_ms * 1e-3) / 1e9
-    traffic = read_traffic(scale)
+    traffic, traffic_note = read_traffic(scale, mean_bytes)
     k1_bytes = kernel1_bytes(edges.shape[1], scale, g.nnz, n)
 
     # end to end through the public API from pinned host memory
@@ -586,6 +586,8 @@ def run_ours(args, dist):
                 "dtype": "int32", "data": "synthetic", "config": workload_config(args, scale),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic,
+                             "traffic_note": traffic_note,
+                             "alg_bytes_per_launch": mean_bytes, "mean_launch_ms": mean_ms,
                              "kernel": "bfs_kernel (persistent, one launch per root)",
                              "peak_source": "measured" if peaks else "fallback"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -594,6 +596,7 @@ def run_ours(args, dist):
                 "batched_scale22": c4a,
                 "kernel1": {"ms": statistics.median(k1_ms),
                             "gbs": k1_bytes / (statistics.median(k1_ms) * 1e-3) / 1e9,
+                            "frac_of_hbm_peak": k1_bytes / (statistics.median(k1_ms) * 1e-3) / 1e9 / peak,
                             "alg_bytes": k1_bytes,
                             "generator_ms": min(gen_ms),
                             "fused_generate_build_ms": min(fused_ms),
@@ -688,20 +691,28 @@ def kernel1_bytes(m, scale, nnz, n):
     return 16 * m + 8 * nk + 8 * nk + passes * 16 * nk + 16 * nk + 4 * nnz + 8 * (n + 1)
 
 
-def read_traffic(scale):
-    """DRAM bytes per bfs_kernel launch from the committed ncu summary, if it
-    was taken at this SCALE on the current kernel source; else None."""
+def read_traffic(scale, alg_bytes_per_launch):
+    """DRAM bytes per bfs_kernel launch from the committed ncu summary of this
+    SCALE, if it was taken on the current kernel source: measured at this
+    SCALE (bytes_per_launch), or measured at a smaller one as a ratio of DRAM
+    to algorithmic bytes (dram_per_alg_bytes) and scaled by this run's
+    algorithmic bytes per launch.  Returns (bytes or None, how it was got)."""
     path = os.path.join(ROOT, "profiles", "bfs_kernel_s%d_traffic.txt" % scale)
     if not os.path.exists(path):
-        return None
+        return None, "no DRAM-counter summary for this SCALE"
     kv = {}
     for line in open(path):
         if "=" in line and not line.lstrip().startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
     if kv.get("source_hash") != kernel_source_hash():
-        return None
-    return int(kv["bytes_per_launch"])
+        return None, "the DRAM-counter summary was taken on another kernel source"
+    if "bytes_per_launch" in kv:
+        return int(kv["bytes_per_launch"]), "ncu DRAM bytes per launch at this SCALE"
+    ratio = float(kv["dram_per_alg_bytes"])
+    return int(ratio * alg_bytes_per_launch), (
+        "ncu DRAM bytes / algorithmic bytes = %.2f measured at SCALE %s, times this run's "
+        "algorithmic bytes per launch" % (ratio, kv.get("measured_scale", "?")))
 
 
 def kernel_source_hash(main="bfs.cu"):

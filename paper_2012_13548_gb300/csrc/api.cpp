@@ -523,7 +523,7 @@ gb_status graph_from_csr(const int64_t *off, const int32_t *col, int64_t n, int6
         g->device = ctx->device;
         cudaError_t e;
         if ((e = gb::dmalloc(&g->off, (n + 1) * sizeof(int64_t))) != cudaSuccess ||
-            (e = gb::dmalloc(&g->col, std::max<int64_t>(nnz, 4) * sizeof(int32_t))) != cudaSuccess ||
+            (e = gb::dmalloc(&g->col, col_alloc_entries(nnz) * sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMemcpyAsync(g->off, off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
             (nnz && (e = cudaMemcpyAsync(g->col, col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st)) != cudaSuccess) ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess) {

@@ -117,6 +117,7 @@ struct BfsArgs {
     int big_deg;
     int canonical;
     int vec_out;  // parent, level, hub and the state bytes allow 16-byte vector access
+    int vec_col;  // col is 16-byte aligned and padded to a multiple of 4 entries
     uint64_t timeout_ns;
 };
 
@@ -131,9 +132,14 @@ __device__ __forceinline__ BigEnt load_big(const BigEnt *q, int64_t i)
     return b;
 }
 
+// Chunks of a big vertex start at 16-byte boundaries of the column array
+// (the row start rounded down to a multiple of 4 entries, then every
+// BIG_CHUNK entries), so that every lane reads its four entries of a chunk
+// with one aligned 16-byte load; a row of deg entries spans at most this
+// many such chunks (one may come out empty).
 __device__ __forceinline__ unsigned nchunks(int64_t deg)
 {
-    return (unsigned)((deg + BIG_CHUNK - 1) / BIG_CHUNK);
+    return (unsigned)((deg + 3 + BIG_CHUNK - 1) / BIG_CHUNK);
 }
 
 // The outputs are not written level by level: a search would then rewrite
@@ -271,6 +277,7 @@ __device__ __forceinline__ void append_next(bool won, int32_t v, int64_t dv, con
 // the claiming atomics together with the candidates' degree loads (a winner
 // needs its degree for the next frontier's counters).
 constexpr int TD_E = 4;
+static_assert(BIG_CHUNK == 32 * TD_E, "a big-vertex chunk is one TD_E-entry group per lane");
 __device__ __forceinline__ void td_visit(const bool (&valid)[TD_E], const int32_t (&src)[TD_E],
                                          const int32_t (&v)[TD_E], int l, const BfsArgs &a,
                                          unsigned *Fn, WarpBuf &wb, int &qn, int &bn,
@@ -575,23 +582,38 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                             be = load_big(a.bigq, bbase + ow);
                         }
                         if (!GB_OK_IDX(a.st, be.u, a.n, 206)) continue;
-                        const int64_t s = a.off[be.u] + (c - (int64_t)be.cbase) * BIG_CHUNK;
-                        const int64_t eu = a.off[be.u + 1];
-                        const int64_t e = s + BIG_CHUNK < eu ? s + BIG_CHUNK : eu;
+                        const int64_t su = a.off[be.u], eu = a.off[be.u + 1];
+                        const int64_t cs = (su & ~int64_t(3)) + (c - (int64_t)be.cbase) * BIG_CHUNK;
+                        const int64_t s = su > cs ? su : cs;
+                        const int64_t e = cs + BIG_CHUNK < eu ? cs + BIG_CHUNK : eu;
+                        if (s >= e) continue;  // the empty chunk a row may end with
                         if (lane == 0) my_edges += (unsigned long long)(e - s);
-                        for (int64_t b = s; b < e; b += 32 * TD_E) {
-                            bool valid[TD_E];
-                            int32_t sv[TD_E], vv[TD_E];
+                        // lane i: entries cs + 4i .. cs + 4i + 3, one 16-byte load when
+                        // the column array allows it (the library's own graphs)
+                        const int64_t j0 = cs + 4 * (int64_t)lane;
+                        bool valid[TD_E];
+                        int32_t sv[TD_E], vv[TD_E];
+                        if (a.vec_col) {
+                            int4 x = make_int4(0, 0, 0, 0);
+                            if (j0 < e && GB_OK_IDX(a.st, j0 + 3, col_alloc_entries(a.nnz), 207))
+                                x = __ldg(reinterpret_cast<const int4 *>(a.col + j0));
+                            vv[0] = x.x;
+                            vv[1] = x.y;
+                            vv[2] = x.z;
+                            vv[3] = x.w;
+#pragma unroll
+                            for (int t = 0; t < TD_E; ++t) valid[t] = j0 + t >= s && j0 + t < e;
+                        } else {
 #pragma unroll
                             for (int t = 0; t < TD_E; ++t) {
-                                const int64_t j = b + t * 32 + lane;
-                                valid[t] = j < e && GB_OK_IDX(a.st, j, a.nnz, 207);
-                                vv[t] = valid[t] ? __ldg(&a.col[j]) : 0;
-                                sv[t] = be.u;
+                                valid[t] = j0 + t >= s && j0 + t < e && GB_OK_IDX(a.st, j0 + t, a.nnz, 207);
+                                vv[t] = valid[t] ? __ldg(&a.col[j0 + t]) : 0;
                             }
-                            td_visit(valid, sv, vv, l, a, Fn, wb, qn_buf, bn_buf, my_mf, nxt,
-                                     qnext_base, bnext_base);
                         }
+#pragma unroll
+                        for (int t = 0; t < TD_E; ++t) sv[t] = be.u;
+                        td_visit(valid, sv, vv, l, a, Fn, wb, qn_buf, bn_buf, my_mf, nxt,
+                                 qnext_base, bnext_base);
                     }
                 }
             }
@@ -1004,6 +1026,7 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.big_deg = big_deg;
     a.canonical = o.canonical_parents;
     a.vec_out = vec_ok(a);
+    a.vec_col = (reinterpret_cast<uintptr_t>(a.col) & 15u) == 0;  // allocated with col_alloc_entries
     a.timeout_ns = timeout_ns();
     void *args[] = {&a};
     // 1 block per SM runs the 2-per-SM kernel on half its grid
@@ -1154,6 +1177,7 @@ gb_status bfs_noalloc_impl(const int64_t *off, const int32_t *col, int64_t n, in
     a.big_deg = std::max(o.big_degree, 1);
     a.canonical = o.canonical_parents;
     a.vec_out = vec_ok(a);
+    a.vec_col = 0;  // a caller's columns: neither alignment nor padding is known
     a.timeout_ns = timeout_ns();
     void *args[] = {&a};
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfs_kernel<2>, dim3(d.blocks),

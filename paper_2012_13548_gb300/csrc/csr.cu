@@ -387,7 +387,7 @@ gb_status csr_from_keys(uint64_t *k0, uint64_t *k1, int64_t nk, int scale, gb_gr
     }
     g->nnz = (int64_t)nnz;
     GB_CUDA(gb::dmalloc(&g->off, (n + 1) * sizeof(int64_t)));
-    GB_CUDA(gb::dmalloc(&g->col, std::max<int64_t>(g->nnz, 4) * sizeof(int32_t)));
+    GB_CUDA(gb::dmalloc(&g->col, col_alloc_entries(g->nnz) * sizeof(int32_t)));
     k1_write_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tbase, n, g->off, g->col,
                                                              g->nnz, ctx->status);
     note_launch();
@@ -869,7 +869,7 @@ gb_status build_csr_counting(const int64_t *edges, int64_t m, int scale, gb_grap
     GB_CUDA(cudaMemcpyAsync(&nnz, g->off + n, sizeof(nnz), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     g->nnz = nnz;
-    GB_CUDA(gb::dmalloc(&g->col, std::max<int64_t>(nnz, 4) * sizeof(int32_t)));
+    GB_CUDA(gb::dmalloc(&g->col, col_alloc_entries(nnz) * sizeof(int32_t)));
     cs_compact_kernel<<<grid, 256, 0, s>>>(s0, g->off, n, tmp, g->col, nnz, ctx->status);
     note_launch();
     GB_CUDA(cudaGetLastError());

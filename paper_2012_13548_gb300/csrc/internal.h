@@ -152,6 +152,11 @@ struct gb_graph {
 
 namespace gb {
 
+// Entries allocated for a graph's columns: nnz rounded up to a multiple of 4
+// (at least 4), so that 16-byte loads of an aligned group of four entries
+// never leave the allocation.
+inline int64_t col_alloc_entries(int64_t nnz) { return nnz < 4 ? 4 : (nnz + 3) & ~int64_t(3); }
+
 // Kernel 1 pieces (csr.cu).
 gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cudaStream_t s);
 // Kernel 1 by counting sort (rows scattered, then sorted one by one), m < 2^31 (csr.cu).
