@@ -131,9 +131,12 @@ gb_status kron_generate(int scale, int edgefactor, double a, double b, double c,
  * Synchronises `s` (the column count is needed on the host).  Returns
  * GB_ERR_RANGE if an endpoint is outside [0, 2^scale).  *out receives a
  * library-owned graph; free it with graph_free.  Besides the CSR every graph
- * holds two arrays the search reads: a degree >= 1 bitmap (n/8 bytes) and a
- * hub per vertex (4 * n bytes: a neighbour of largest degree among the first
- * 128 of its row, tested first by the bottom-up step). */
+ * holds three arrays the search reads: a degree >= 1 bitmap (n/8 bytes), the
+ * list of the vertices of degree >= 1 in ascending order (4 bytes each; the
+ * first bottom-up level walks it) and a hub per vertex (4 * n bytes: a
+ * neighbour of largest degree among the first 128 of its row, tested first by
+ * the bottom-up step).  The column array is padded to a multiple of 4
+ * entries. */
 gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph **out,
                           gb_stream s);
 
@@ -224,9 +227,11 @@ gb_status bfs_set_options(const gb_bfs_options *opt);
  * [n].  On return (after `s` syncs) level[v] is the hop distance from root or
  * -1, parent[root] = root, parent[v] is a neighbour of v with level one less,
  * and parent[v] = -1 for every unreached v.  GB_ERR_RANGE if root is outside
- * [0, n).  One persistent cooperative kernel runs all levels; temporary
- * device memory (about 4.2 * n bytes) is taken from the stream-ordered
- * pool. */
+ * [0, n).  One persistent cooperative kernel runs all levels and writes both
+ * outputs once, at the end (every entry of parent and level is written);
+ * temporary device memory (about 10 * n bytes: bitmaps, the BFS queue, a
+ * state byte per vertex and the list of vertices a bottom-up level leaves
+ * open) is taken from the stream-ordered pool. */
 gb_status bfs(const gb_graph *g, int64_t root, int32_t *parent, int32_t *level, gb_stream s);
 
 /* Multi-source BFS: k (1..64) roots (host array) in one persistent launch,
@@ -250,7 +255,7 @@ gb_status bfs_multi_graph(const gb_graph *const *gs, int ng, const int64_t *root
  * the device's memory, a real-time or embedded host loop that must not stall
  * on the allocator, or code running where allocation is not allowed.  This
  * entry point runs the same kernel as bfs() but keeps every temporary in one
- * file-scope device array built into the library (about 13 MB, held on every
+ * file-scope device array built into the library (about 14.4 MB, held on every
  * GPU that loads the library until the process exits), so it never allocates.
  *   off, col   caller's CSR in device memory: off int64 [n+1], col int32
  *              [nnz], rows sorted ascending, symmetric, no self-loops
