@@ -230,13 +230,24 @@ __device__ __forceinline__ void append_open(bool keep, int32_t u, int32_t *seg, 
 }
 
 // Warp-collective: set the visited and next-frontier bits of the lanes with
-// `on`, one atomic per bitmap word among the lanes sharing it.
+// `on`.  Lanes that hold vertices of the same bitmap word next to each other
+// (the lists are in increasing vertex order) form a run; an OR scan within
+// the runs gives the last lane of each run the run's bits, and that lane sets
+// them with one atomic per bitmap.  Lanes of one word that are not adjacent
+// only cost an extra atomic.
 __device__ __forceinline__ void set_bits(bool on, int32_t u, unsigned *vis, unsigned *Fn)
 {
-    const unsigned w = on ? (unsigned)u >> 5 : 0xffffffffu;
-    const unsigned peers = __match_any_sync(kFull, w);
-    const unsigned bits = __reduce_or_sync(peers, on ? 1u << (u & 31) : 0u);
-    if (on && (__ffs(peers) - 1) == (int)lane_id()) {
+    const int lane = (int)lane_id();
+    const int w = on ? (int)((unsigned)u >> 5) : -1;
+    unsigned bits = on ? 1u << (u & 31) : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned ob = __shfl_up_sync(kFull, bits, d);
+        const int ow = __shfl_up_sync(kFull, w, d);
+        if (lane >= d && ow == w) bits |= ob;
+    }
+    const int wnext = __shfl_down_sync(kFull, w, 1);
+    if (on && (lane == 31 || wnext != w)) {
         atomicOr(&vis[w], bits);
         atomicOr(&Fn[w], bits);
     }
