@@ -300,6 +300,32 @@ def test_bfs_large_scales(scale, k, canonical):
             assert oracle.validate(off_ref, col_ref, r, np_(parent), np_(level)) == 0, r
 
 
+@pytest.mark.parametrize("mode", ["default", "bottom_up_early", "flip_flop"])
+@pytest.mark.parametrize("canonical", [0, 1])
+def test_bfs_rows_longer_than_65535(canonical, mode):
+    """The bottom-up list walks read a 16-bit degree saturated at 65535 and
+    take the exact one from the offsets for a saturated vertex; a wrong degree
+    would cut the vertex's chunks at the next top-down level.  Vertex 1 has
+    100001 neighbours (the root and 100000 leaves); its hub is the root, so a
+    bottom-up first level finds it through the hub and queues it as a big
+    vertex, whose chunks the next (top-down, in flip-flop mode) level expands."""
+    gb.bfs_set_options(canonical_parents=canonical, **SWITCHES[mode])
+    D, F = 100000, 64
+    n = 2 + D + F
+    leaves = np.arange(2, 2 + D, dtype=np.int64)
+    filler = np.arange(2 + D, n, dtype=np.int64)
+    e = np.concatenate([np.stack([np.zeros(1, np.int64), np.ones(1, np.int64)]),
+                        np.stack([np.ones(D, np.int64), leaves]),
+                        np.stack([np.zeros(F, np.int64), filler])], axis=1)
+    off, col = oracle.csr_build(e, (n - 1).bit_length())
+    off = off[: n + 1].copy()
+    assert off[2] - off[1] == D + 1
+    G = gb.graph_from_csr(torch.as_tensor(off).cuda(), torch.as_tensor(col).cuda())
+    for root in (0, 1, 2, int(filler[0])):
+        check_bfs(G, off, col, root, canonical)
+    G.free()
+
+
 def test_bfs_isolated_root_and_bad_root():
     _, off_ref, col_ref = oracle_graph(10)
     _, G = gpu_graph(10)
