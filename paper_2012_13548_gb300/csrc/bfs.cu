@@ -19,7 +19,8 @@
 //    frontier bitmap, which is therefore the smallest-id parent.  Outside
 //    canonical mode it first tests its hub (a neighbour of largest degree,
 //    built with the graph): a hub in the frontier is a valid parent, found
-//    without reading the row.
+//    without reading the row, and a row of one entry whose hub is not in the
+//    frontier is settled without reading it either.
 //
 // The switch follows Beamer: top-down -> bottom-up when the frontier's edges
 // exceed (edges of unvisited vertices) / alpha, back when the frontier is
@@ -737,7 +738,10 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                     if (won) mark_reached(a, u[t], l + 1, true);
                     set_bits(won, u[t], a.vis, Fn);
                     append_next(won, u[t], dg[t], a, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
-                    const bool pend = cand[t] && !won;
+                    // a row of one entry was settled by the hub test: still open
+                    const bool whole = hb[t] >= 0 && dg[t] == 1;
+                    append_open(cand[t] && !won && whole, u[t], seg, un_open);
+                    const bool pend = cand[t] && !won && !whole;
                     const unsigned pm = __ballot_sync(kFull, pend);
                     if (pend) wb.pu[(pt + __popc(pm & lanemask_lt())) & (PBUF - 1)] = u[t];
                     pt += __popc(pm);
@@ -798,7 +802,8 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
                         __stcg(&Fn[w], nm);
                     }
                     append_next(won, (int32_t)u, dg[t], a, wb, qn_buf, bn_buf, my_mf, nxt, qnext_base, bnext_base);
-                    const bool pend = cand && found < 0 && dg[t] > 0;
+                    // no row pass for an empty row, nor for a row of one entry (its hub)
+                    const bool pend = cand && found < 0 && dg[t] > (hb[t] >= 0 ? 1 : 0);
                     const unsigned pm = __ballot_sync(kFull, pend);
                     if (pend) wb.pu[(pt + __popc(pm & lanemask_lt())) & (PBUF - 1)] = (int32_t)u;
                     pt += __popc(pm);
