@@ -17,10 +17,15 @@
 //    the smallest-id parent -- and writes levels and parents.
 //  bottom-up level: every vertex with unseen bits scans its sorted adjacency
 //    list, collecting M_l bits until all its unseen bits are found; the first
-//    neighbour to supply a bit is its parent.
-//  Rows longer than 32 entries are scanned by the whole warp, 32 neighbours a
-//  round, with a prefix-OR over the lanes so that each bit is credited to its
-//  first (smallest-id) neighbour.
+//    neighbour to supply a bit is its parent.  A warp takes 32 consecutive
+//    vertices and streams their rows together, every open row getting an
+//    equal share of 32 lanes x 4 consecutive entries per round; a segmented
+//    prefix-OR over the lanes credits each bit to its first (smallest-id)
+//    neighbour.  On the first bottom-up level after top-down ones nearly every
+//    row is scanned to its end, so rows longer than MS_HUGE entries (listed
+//    once per batch call) are scanned first, one per warp, and the groups of
+//    32 are then handed out by a counter: a warp that drew a long row takes
+//    fewer groups, instead of holding the level barrier.
 //
 // Outputs of batch calls: as bits are found their parents and levels go to
 // vertex-major staging arrays ([n][k]: the bits of one vertex share a few
@@ -57,6 +62,7 @@ constexpr int MS_WARPS = MS_THREADS / 32;
 constexpr int MS_QBUF = 256;  // per-warp staging of newly active vertices
 constexpr int MS_BBUF = 32;   // per-warp staging of newly active big vertices
 constexpr int MS_HIST = 8;    // batch calls: levels whose reached-bit masks are kept
+constexpr int MS_HUGE = 4096; // bottom-up: rows longer than this are scanned first, one per warp
 constexpr int SITE_MS_BAR = 30;
 constexpr int SITE_MS_LEVELS = 31;
 
@@ -83,6 +89,8 @@ struct MsHeader {
     unsigned long long acc[6];
     unsigned long long na_hist[4];  // active-list length of each level (ring)
     unsigned long long t0;          // global timer at the start of the current level
+    unsigned long long gnext[4];    // bottom-up: next group of 32 vertices (ring by level)
+    unsigned long long nhuge;       // entries of the huge-row list
 };
 
 namespace {
@@ -115,6 +123,8 @@ struct MsArgs {
     int do_init;            // 1: clear state and place the roots first (batch calls)
     unsigned long long active;  // serving: bits in use; ignored when do_init
     const MsSlots *slots;   // serving: per-bit outputs; nullptr = graph outputs [k][n]
+    int vec_col;            // 1: every graph's column array is 16-byte aligned and padded
+    int32_t *huge;          // single-graph batch calls: vertices of degree > MS_HUGE (else null)
 };
 
 template <typename T>
@@ -345,8 +355,6 @@ __device__ __forceinline__ T ms_rows(const MsGraph *s_g, const MsSlots *S, const
                                      int64_t lu, int64_t s, int64_t e, T need,
                                      unsigned long long &edges)
 {
-    constexpr int E = 4;
-    constexpr int SLOTS = 32 * E;
     const int lane = (int)lane_id();
     T found = 0;
     int64_t pos = s;
@@ -354,65 +362,121 @@ __device__ __forceinline__ T ms_rows(const MsGraph *s_g, const MsSlots *S, const
         const bool act = need != 0 && found != need && pos < e;
         const unsigned am = __ballot_sync(kFull, act);
         if (!am) break;
-        const int q = SLOTS / __popc(am);
+        // each open row gets 32 / (open rows) lanes of 4 consecutive slots
+        const int per = 32 / __popc(am);
         const int64_t rem = act ? e - pos : 0;
-        const int len = (int)(rem < q ? rem : q);
-        const int incl = warp_inclusive_scan(len);
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - len;
-        int own[E];
-        int32_t vv[E];
-        T mm[E];
+        const int len = (int)(rem < 4 * per ? rem : 4 * per);
+        const int nl = (len + 3) >> 2;
+        const int incl = warp_inclusive_scan(nl);
+        const int excl = incl - nl;
+        int o = 0;  // the row this lane serves: the last one starting at or before it
 #pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const int k = t * 32 + lane;
-            int o = 0;
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int c = o + step;
+            if (__shfl_sync(kFull, excl, c) <= lane) o = c;
+        }
+        const int seg0 = __shfl_sync(kFull, excl, o);
+        const int i = lane - seg0;
+        const int leno = __shfl_sync(kFull, len, o);
+        const int cnt = 4 * i < leno ? (leno - 4 * i < 4 ? leno - 4 * i : 4) : 0;
+        const int64_t po = __shfl_sync(kFull, pos, o) + 4 * i;
+        const int go = __shfl_sync(kFull, g, o);
+        const T need_o = shfl_mask(need, o);
+        const T found_o = shfl_mask(found, o);
+        const MsGraph &G = s_g[go];
+        int32_t c[4];
+        T m[4];
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int c = o + step;
-                if (__shfl_sync(kFull, excl, c) <= k) o = c;
+        for (int t = 0; t < 4; ++t) c[t] = t < cnt ? __ldg(&G.col[po + t]) : -1;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) m[t] = c[t] >= 0 ? (T)(ld_mask(&M[G.voff + c[t]]) & need_o) : (T)0;
+        const T lb = (T)(m[0] | m[1] | m[2] | m[3]);
+        // inclusive OR over the earlier lanes of the same row (slot order)
+        T x = lb;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T y = shfl_up_mask(x, d);
+            if (lane - d >= seg0) x |= y;
+        }
+        const T y1 = shfl_up_mask(x, 1);
+        const T before = lane > seg0 ? y1 : (T)0;
+        T mine = (T)(lb & (T)~before & (T)~found_o);
+        const int64_t luo = __shfl_sync(kFull, lu, o);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const T bt = (T)(mine & m[t]);
+            if (bt) {
+                write_parents(G, S, luo, bt, c[t]);
+                mine &= (T)~bt;
             }
-            own[t] = o;
-            const int64_t po = __shfl_sync(kFull, pos, o);
-            const int eo = __shfl_sync(kFull, excl, o);
-            const int go = __shfl_sync(kFull, g, o);
-            vv[t] = k < total ? __ldg(&s_g[go].col[po + (k - eo)]) : -1;
         }
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const int go = __shfl_sync(kFull, g, own[t]);
-            mm[t] = vv[t] >= 0 ? ld_mask(&M[s_g[go].voff + vv[t]]) : (T)0;
-        }
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const int o = own[t];
-            const T need_o = shfl_mask(need, o);
-            const T found_o = shfl_mask(found, o);
-            const T h = mm[t] & need_o & (T)~found_o;
-            // inclusive OR over the earlier slots of the same row in this group
-            int seg0 = __shfl_sync(kFull, excl, o) - t * 32;
-            seg0 = seg0 > 0 ? seg0 : 0;
-            T x = h;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const T y = shfl_up_mask(x, d);
-                if (lane - d >= seg0) x |= y;
-            }
-            const T y1 = shfl_up_mask(x, 1);
-            const T before = lane > seg0 ? y1 : (T)0;
-            const T mine = h & (T)~before;
-            const int go = __shfl_sync(kFull, g, o);
-            const int64_t luo = __shfl_sync(kFull, lu, o);
-            if (mine) write_parents(s_g[go], S, luo, mine, vv[t]);
-            // each row collects the OR of its slots in this group (its last slot)
-            const int a0 = excl - t * 32, a1 = excl + len - t * 32;
-            const bool has = len > 0 && a1 > 0 && a0 < 32;
-            const int last = has ? (a1 < 32 ? a1 : 32) - 1 : 0;
-            const T got = shfl_mask(x, last);
-            if (has) found |= got;
-        }
+        // each row takes the OR of its slots from its last lane
+        const T got = shfl_mask(x, nl > 0 ? incl - 1 : 0);
+        if (nl > 0) found |= got;
         pos += len;
         edges += (unsigned long long)len;
+    }
+    return found;
+}
+
+// Warp-collective bottom-up scan of one long row [s, e) of graph g (local id
+// lu) for the bits `need`, 128 entries a round: lane i takes entries
+// 4i..4i+3 of the round (one 16-byte load when the columns are aligned) and
+// ORs their masks in order; an exclusive prefix-OR over the lanes then gives
+// each bit's first supplier in row order (the smallest-id parent), which the
+// supplying lane writes.  Stops once every needed bit is found.  Returns the
+// bits found (warp-uniform).
+template <typename T>
+__device__ __forceinline__ T ms_row_warp(const MsGraph *s_g, const MsSlots *S, const T *M, int g,
+                                         int64_t lu, int64_t s, int64_t e, T need, bool vec,
+                                         unsigned long long &edges)
+{
+    const int lane = (int)lane_id();
+    const MsGraph &G = s_g[g];
+    const T *Mg = M + G.voff;
+    T found = 0;
+    const int64_t s4 = vec ? (s & ~int64_t(3)) : s;
+    for (int64_t b = s4; b < e; b += 128) {
+        const int64_t p = b + 4 * lane;
+        int32_t c[4];
+        if (vec) {
+            int4 x = make_int4(-1, -1, -1, -1);
+            if (p < e) x = __ldg(reinterpret_cast<const int4 *>(G.col + p));
+            c[0] = x.x; c[1] = x.y; c[2] = x.z; c[3] = x.w;
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) c[t] = p + t < e ? __ldg(&G.col[p + t]) : -1;
+        }
+        T m[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const bool valid = p + t >= s && p + t < e;
+            if (!valid) c[t] = -1;
+            m[t] = valid ? (T)(ld_mask(&Mg[c[t]]) & need) : (T)0;
+        }
+        const T lb = (T)(m[0] | m[1] | m[2] | m[3]);
+        // inclusive OR over lanes 0..lane
+        T incl = lb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = shfl_up_mask(incl, o);
+            if (lane >= o) incl |= y;
+        }
+        const T up = shfl_up_mask(incl, 1);
+        const T before = lane == 0 ? (T)0 : up;
+        T mine = (T)(lb & (T)~before & (T)~found);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const T bt = (T)(mine & m[t]);
+            if (bt) {
+                write_parents(G, S, lu, bt, c[t]);
+                mine &= (T)~bt;
+            }
+        }
+        found |= shfl_mask(incl, 31);
+        const int64_t lo = b > s ? b : s, hi = b + 128 < e ? b + 128 : e;
+        if (lane == 0) edges += (unsigned long long)(hi - lo);
+        if (found == need) break;
     }
     return found;
 }
@@ -464,6 +528,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             a.mbuf[i] = 0;
             a.mbuf[a.mstride + i] = 0;
             a.mbuf[2 * a.mstride + i] = 0;
+            if (a.huge && i < ntot && s_g[0].off[i + 1] - s_g[0].off[i] > MS_HUGE)
+                a.huge[atomicAdd(&h->nhuge, 1ull)] = (int32_t)i;
         }
         if (!grid_sync(&h->bar, bar_target, a.st, a.timeout_ns, SITE_MS_BAR)) return;
         // roots: bit b of graph g at its root; roots that coincide share one entry
@@ -500,6 +566,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
 
     unsigned long long my_edges = 0, my_touched = 0, reached_new = 0, my_mf = 0;
     T my_any = 0;
+    bool prev_td = true;  // the roots' level counts as top-down
     int l = a.l0;
     for (;; ++l) {
         if (a.max_levels > 0 && l >= a.l0 + a.max_levels) break;
@@ -532,6 +599,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
         if (gtid == 0) {
             MsCtl z = {0, 0, 0, 0};
             h->ctl[(l + 2) % 3] = z;
+            h->gnext[(l + 2) & 3] = 0;
         }
 
         if (td) {
@@ -645,8 +713,47 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                 }
             }
         } else {
-            // bottom-up over all vertices with unseen bits, 32 consecutive ids per warp
-            for (int64_t b0 = gwarp * 32; b0 < ntot; b0 += nwarps * 32) {
+            // bottom-up over all vertices with unseen bits.  First the huge
+            // rows (single-graph batches), one per warp, so that the longest
+            // scans start at once; then groups of 32 consecutive vertices,
+            // handed out by a counter (the next index fetched one group ahead)
+            const int64_t nh = a.huge ? (int64_t)ldcg_u64(&h->nhuge) : 0;
+            for (int64_t hi = gwarp; hi < nh; hi += nwarps) {
+                const int64_t gu = ldcg_i32(&a.huge[hi]);
+                const T sn = ld_mask(&a.seen[gu]);
+                const T need = all & (T)~sn;
+                const int64_t rs = s_g[0].off[gu], re = s_g[0].off[gu + 1];
+                T found = 0;
+                if (need) {
+                    my_touched += (lane == 0);
+                    found = ms_row_warp(s_g, S, M, 0, gu, rs, re, need, a.vec_col != 0, my_edges);
+                }
+                if (found && lane == 0) {
+                    write_levels(s_g[0], S, gu, found, l + 1);
+                    st_mask(&a.seen[gu], (T)(sn | found));
+                    st_mask(&Mn[gu], found);
+                    if (a.hist && l + 1 < MS_HIST) a.hist[(size_t)(l + 1) * a.mstride + gu] = found;
+                    reached_new += __popcll((unsigned long long)found);
+                    my_any |= found;
+                }
+                ms_append(lane == 0 && found != 0, gu, re - rs, wb, qn_buf, bn_buf, my_mf, nxt, act_next,
+                          bigq_next);
+            }
+            const int64_t ngroups = (ntot + 31) / 32;
+            // Only the first bottom-up level after top-down ones, where every
+            // row is scanned in full, needs it; later levels keep the static
+            // split (cheaper for groups that are mostly done), and so do
+            // serving launches (their levels may advance without a launch,
+            // which the counter ring does not allow).
+            const bool dyn = a.slots == nullptr && prev_td;
+            unsigned long long *gctr = &h->gnext[l & 3];
+            unsigned long long gnx = dyn ? (lane == 0 ? atomicAdd(gctr, 1ull) : 0ull) : (unsigned long long)gwarp;
+            for (;;) {
+                const int64_t gi = dyn ? (int64_t)__shfl_sync(kFull, gnx, 0) : (int64_t)gnx;
+                if (gi >= ngroups) break;
+                if (!dyn) gnx += (unsigned long long)nwarps;
+                else if (lane == 0) gnx = atomicAdd(gctr, 1ull);
+                const int64_t b0 = gi * 32;
                 const int64_t gu = b0 + lane;
                 T need = 0;
                 int g = 0;
@@ -659,7 +766,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                         g = find_graph(s_voff, a.ng, gu);
                         lu = gu - s_g[g].voff;
                         deg = s_g[g].off[lu + 1] - s_g[g].off[lu];
-                        if (deg == 0) need = 0;
+                        if (deg == 0 || (a.huge && deg > MS_HUGE)) need = 0;  // huge: done above
                     }
                 }
                 int64_t rs = 0, re = 0;
@@ -700,6 +807,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                 s_any = 0;
             }
         }
+        prev_td = td;
         if (gtid == 0) {
             h->na_hist[l & 3] = (unsigned long long)na;
             atomicAdd(&h->acc[td ? 4 : 5], 1ull);
@@ -795,7 +903,9 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     const size_t o_m = o_seen + up(np * sizeof(T));
     const size_t o_act = o_m + up(3 * np * sizeof(T));
     const size_t o_big = o_act + up(3 * (size_t)ntot * sizeof(int32_t));
-    const size_t total = o_big + 2 * bigcap * sizeof(unsigned long long);
+    const size_t o_huge = o_big + up(2 * bigcap * sizeof(unsigned long long));
+    const int64_t hugecap = ng == 1 ? nnz_tot / (MS_HUGE + 1) + 1 : 0;
+    const size_t total = o_huge + hugecap * sizeof(int32_t);
     unsigned char *ws = nullptr;
     Scratch tmp(s);
     GB_CUDA(tmp.alloc(&ws, total));
@@ -840,6 +950,10 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     a.do_init = 1;
     a.active = 0;
     a.slots = nullptr;
+    a.huge = hugecap ? reinterpret_cast<int32_t *>(ws + o_huge) : nullptr;
+    a.vec_col = 1;
+    for (int i = 0; i < ng; ++i)
+        if (reinterpret_cast<uintptr_t>(gs[i].col) & 15u) a.vec_col = 0;
     void *args[] = {&a};
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)ms_kernel<T>, dim3(ctx->ms_blocks),
                                         dim3(MS_THREADS), args, 0, s));
@@ -1093,6 +1207,8 @@ gb_status ms_serve_step(MsServe *m, int level, unsigned long long active, MsCtl 
     a.do_init = 0;
     a.active = active;
     a.slots = m->slots_dev;
+    a.vec_col = (reinterpret_cast<uintptr_t>(m->g->col) & 15u) == 0;
+    a.huge = nullptr;
     void *args[] = {&a};
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)ms_kernel<unsigned long long>, dim3(m->blocks),
                                         dim3(MS_THREADS), args, 0, s));

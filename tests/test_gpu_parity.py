@@ -401,6 +401,42 @@ def test_msbfs_repeated_roots_and_random_graphs(canonical):
             check_row(off, col, r, np_(P[i]), np_(L[i]), p_ref, l_ref, canonical, (trial, i, r))
 
 
+def _three_hub_csr():
+    # hubs 0, 1, 2 with 6000 random neighbours each among 20000 leaves (rows
+    # longer than the batched kernel's 4096-entry threshold), plus random
+    # leaf-leaf edges so that leaves reach the hubs over several levels
+    rng = np.random.default_rng(17)
+    n = 20003
+    e = [np.stack([np.full(6000, h, np.int64), rng.choice(np.arange(3, n), 6000, replace=False)])
+         for h in range(3)]
+    e.append(rng.integers(3, n, size=(2, 20000)).astype(np.int64))
+    off, col = oracle.csr_build(np.concatenate(e, axis=1), (n - 1).bit_length())
+    return off[: n + 1].copy(), col
+
+
+@pytest.mark.parametrize("canonical", [0, 1])
+@pytest.mark.parametrize("mode", list(MS_SWITCHES))
+def test_msbfs_rows_longer_than_the_huge_threshold(mode, canonical):
+    # the first bottom-up level scans rows above 4096 entries one per warp
+    # before the groups of 32; the rows must still equal the oracle's
+    gb.bfs_set_options(canonical_parents=canonical, **MS_SWITCHES[mode])
+    off, col = _three_hub_csr()
+    assert (np.diff(off)[:3] > 4096).all()
+    G = gb.graph_from_csr(torch.as_tensor(off).cuda(), torch.as_tensor(col).cuda())
+    rng = np.random.default_rng(3)
+    roots = [0, 1, 2] + [int(x) for x in rng.integers(3, off.size - 1, size=61)]
+    P, L = gb.bfs_batch(G, roots)
+    for i, r in enumerate(roots):
+        p_ref, l_ref = oracle.bfs(off, col, r)
+        check_row(off, col, r, np_(P[i]), np_(L[i]), p_ref, l_ref, canonical, (i, r))
+    # one graph through the graph-batch path (byte masks, 8 roots)
+    P2, L2 = gb.bfs_multi_graph([G], [roots[:8]])
+    for b, r in enumerate(roots[:8]):
+        p_ref, l_ref = oracle.bfs(off, col, r)
+        check_row(off, col, r, np_(P2[0][b]), np_(L2[0][b]), p_ref, l_ref, canonical, (b, r))
+    G.free()
+
+
 def _path_and_cycle_csr():
     # a 200-vertex path and a 150-vertex cycle: searches 100+ levels deep
     e = [(i, i + 1) for i in range(199)] + [(200 + i, 200 + (i + 1) % 150) for i in range(150)]
