@@ -29,9 +29,19 @@ constexpr int FIN_ITEMS = 16;
 constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;  // 4096 keys
 constexpr int SITE_K1_RANGE = 10;
 
-__global__ void k1_sym_kernel(const int64_t *__restrict__ edges, int64_t m, int scale,
-                              ulonglong2 *__restrict__ keys, DevStatus *st)
+// Both directed keys of every tuple, and the digit counts of the radix
+// sort's passes over them (8-bit digits from bit 0; `passes` of them), so
+// that the sort does not read the keys once more for its histogram.
+constexpr int SYM_THREADS = 256;
+constexpr int SYM_MAX_PASSES = 8;
+__global__ void __launch_bounds__(SYM_THREADS) k1_sym_kernel(const int64_t *__restrict__ edges, int64_t m,
+                                                             int scale, ulonglong2 *__restrict__ keys,
+                                                             int passes, unsigned long long *__restrict__ hist,
+                                                             DevStatus *st)
 {
+    __shared__ unsigned s_h[SYM_MAX_PASSES][256];
+    for (int i = threadIdx.x; i < SYM_MAX_PASSES * 256; i += blockDim.x) (&s_h[0][0])[i] = 0;
+    __syncthreads();
     const int64_t n = int64_t(1) << scale;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
@@ -41,8 +51,18 @@ __global__ void k1_sym_kernel(const int64_t *__restrict__ edges, int64_t m, int 
             record_error(st, GB_ERR_RANGE, SITE_K1_RANGE, (long long)e);
             u = v = 0;  // a self-loop: dropped below
         }
-        keys[e] = make_ulonglong2(((uint64_t)u << scale) | (uint64_t)v,
-                                  ((uint64_t)v << scale) | (uint64_t)u);
+        const uint64_t ka = ((uint64_t)u << scale) | (uint64_t)v;
+        const uint64_t kb = ((uint64_t)v << scale) | (uint64_t)u;
+        keys[e] = make_ulonglong2(ka, kb);
+        for (int q = 0; q < passes; ++q) {  // passes <= SYM_MAX_PASSES (0: no counts)
+            atomicAdd(&s_h[q][(unsigned)(ka >> (8 * q)) & 255u], 1u);
+            atomicAdd(&s_h[q][(unsigned)(kb >> (8 * q)) & 255u], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const unsigned c = (&s_h[0][0])[i];
+        if (c) atomicAdd(&hist[i], (unsigned long long)c);
     }
 }
 
@@ -53,21 +73,31 @@ __device__ __forceinline__ bool k1_keep(const uint64_t *keys, int64_t i, uint64_
     return i == 0 || keys[i - 1] != k;              // first of a run of duplicates
 }
 
+// Warp w of a tile takes keys [t0 + w*WARP_KEYS, +WARP_KEYS) here and in the
+// write pass; the kept keys are counted per warp and per tile.
+constexpr int FIN_WARPS = FIN_THREADS / 32;
+constexpr int WARP_KEYS = FIN_TILE / FIN_WARPS;  // 512
 __global__ void __launch_bounds__(FIN_THREADS) k1_count_kernel(const uint64_t *__restrict__ keys,
                                                                int64_t nk, int scale,
-                                                               unsigned *__restrict__ tile_cnt)
+                                                               unsigned *__restrict__ tile_cnt,
+                                                               unsigned *__restrict__ warp_cnt)
 {
-    __shared__ unsigned s_w[FIN_THREADS / 32];
+    __shared__ unsigned s_w[FIN_WARPS];
     const uint64_t vmask = (uint64_t(1) << scale) - 1;
-    const int64_t t0 = (int64_t)blockIdx.x * FIN_TILE;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t w0 = (int64_t)blockIdx.x * FIN_TILE + (int64_t)warp * WARP_KEYS;
     unsigned c = 0;
 #pragma unroll 4
-    for (int j = 0; j < FIN_ITEMS; ++j) {
-        const int64_t i = t0 + j * FIN_THREADS + threadIdx.x;
+    for (int j = 0; j < WARP_KEYS / 32; ++j) {
+        const int64_t i = w0 + 32 * j + lane;
         if (i < nk) c += k1_keep(keys, i, keys[i], scale, vmask);
     }
     c = warp_sum(c);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    if (lane == 0) {
+        s_w[warp] = c;
+        warp_cnt[(int64_t)blockIdx.x * FIN_WARPS + warp] = c;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned t = 0;
@@ -106,44 +136,35 @@ __global__ void __launch_bounds__(1024) k1_scan_tiles_kernel(const unsigned *__r
     if (tid == blockDim.x - 1) base[ntiles] = run;
 }
 
-// Warp-striped: warp w of the tile takes keys [t0 + w*WARP_KEYS, +WARP_KEYS),
-// lane i of round j the key t0 + w*WARP_KEYS + 32 j + i, so that loads and
-// column stores are coalesced; a key's predecessor comes from the next-lower
-// lane (lane 0: the previous round's lane 31, or memory at the warp's start).
-constexpr int WARP_KEYS = FIN_TILE / (FIN_THREADS / 32);  // 512
+// Warp-striped like the count: lane i of round j takes the key
+// t0 + w*WARP_KEYS + 32 j + i, so that loads and column stores are
+// coalesced; a key's predecessor comes from the next-lower lane (lane 0: the
+// previous round's lane 31, or memory at the warp's start).  The warp's first
+// column position (the tile's base plus the counts of the tile's earlier
+// warps) is loaded together with its keys: one pass, no block barrier.
 __global__ void __launch_bounds__(FIN_THREADS) k1_write_kernel(
     const uint64_t *__restrict__ keys, int64_t nk, int scale,
-    const unsigned long long *__restrict__ tile_base, int64_t n, int64_t *__restrict__ off,
-    int32_t *__restrict__ col, int64_t nnz, DevStatus *st)
+    const unsigned long long *__restrict__ tile_base, const unsigned *__restrict__ warp_cnt,
+    int64_t n, int64_t *__restrict__ off, int32_t *__restrict__ col, int64_t nnz, DevStatus *st)
 {
-    __shared__ unsigned s_w[FIN_THREADS / 32];
     const uint64_t vmask = (uint64_t(1) << scale) - 1;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int64_t w0 = (int64_t)blockIdx.x * FIN_TILE + (int64_t)warp * WARP_KEYS;
     constexpr int ROUNDS = WARP_KEYS / 32;
-    // pass 1: the warp's kept keys (self-loops and repeats dropped)
+    const unsigned wc = lane < warp ? warp_cnt[(int64_t)blockIdx.x * FIN_WARPS + lane] : 0u;
+    const unsigned long long tb = tile_base[blockIdx.x];
     uint64_t k[ROUNDS];
-    unsigned total = 0;
-    uint64_t prev = w0 > 0 && w0 - 1 < nk ? keys[w0 - 1] : ~0ull;  // predecessor of the warp's first key
 #pragma unroll
     for (int j = 0; j < ROUNDS; ++j) {
         const int64_t i = w0 + 32 * j + lane;
         k[j] = i < nk ? keys[i] : 0;
-        uint64_t kp = __shfl_up_sync(kFull, k[j], 1);
-        if (lane == 0) kp = prev;
-        prev = __shfl_sync(kFull, k[j], 31);
-        const bool keep = i < nk && (k[j] >> scale) != (k[j] & vmask) && (i == 0 || kp != k[j]);
-        total += __popc(__ballot_sync(kFull, keep));
     }
-    if (lane == 0) s_w[warp] = total;
-    __syncthreads();
-    unsigned woff = 0;
-    for (int w = 0; w < warp; ++w) woff += s_w[w];
-    int64_t base = (int64_t)tile_base[blockIdx.x] + woff;
-    // pass 2: columns at their positions; every change of row writes the
-    // offsets of the rows it passes (an empty row repeats the offset)
-    prev = w0 > 0 && w0 - 1 < nk ? keys[w0 - 1] : ~0ull;
+    uint64_t prev = w0 > 0 && w0 - 1 < nk ? keys[w0 - 1] : ~0ull;  // predecessor of the warp's first key
+    int64_t base = (int64_t)tb + (int64_t)warp_sum(wc);
+    // columns at their positions (self-loops and repeats dropped); every
+    // change of row writes the offsets of the rows it passes (an empty row
+    // repeats the offset)
 #pragma unroll
     for (int j = 0; j < ROUNDS; ++j) {
         const int64_t i = w0 + 32 * j + lane;
@@ -371,20 +392,21 @@ namespace {
 // Stages 2-4 on the symmetrised keys k0[0..nk) (k1: the sort's second buffer
 // of nk keys; the caller owns both).
 gb_status csr_from_keys(uint64_t *k0, uint64_t *k1, int64_t nk, int scale, gb_graph *g,
-                        cudaStream_t s)
+                        cudaStream_t s, const unsigned long long *hist = nullptr)
 {
     Context *ctx = context();
     const int64_t n = g->n;
     uint64_t *ks = nullptr;
-    gb_status rc = radix_sort(k0, k1, nullptr, nullptr, nk, 0, 2 * scale, &ks, nullptr, s);
+    gb_status rc = radix_sort(k0, k1, nullptr, nullptr, nk, 0, 2 * scale, &ks, nullptr, s, hist);
     if (rc != GB_OK) return rc;
     const int64_t ntiles = (nk + FIN_TILE - 1) / FIN_TILE;
-    unsigned *tcnt = nullptr;
+    unsigned *tcnt = nullptr, *wcnt = nullptr;
     unsigned long long *tbase = nullptr;
     Scratch tmp(s);
     GB_CUDA(tmp.alloc(&tcnt, (size_t)ntiles));
+    GB_CUDA(tmp.alloc(&wcnt, (size_t)ntiles * FIN_WARPS));
     GB_CUDA(tmp.alloc(&tbase, (size_t)ntiles + 1));
-    k1_count_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tcnt);
+    k1_count_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tcnt, wcnt);
     note_launch();
     k1_scan_tiles_kernel<<<1, 1024, 0, s>>>(tcnt, ntiles, tbase);
     note_launch();
@@ -403,8 +425,8 @@ gb_status csr_from_keys(uint64_t *k0, uint64_t *k1, int64_t nk, int scale, gb_gr
     g->nnz = (int64_t)nnz;
     GB_CUDA(gb::dmalloc(&g->off, (n + 1) * sizeof(int64_t)));
     GB_CUDA(gb::dmalloc(&g->col, col_alloc_entries(g->nnz) * sizeof(int32_t)));
-    k1_write_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tbase, n, g->off, g->col,
-                                                             g->nnz, ctx->status);
+    k1_write_kernel<<<(unsigned)ntiles, FIN_THREADS, 0, s>>>(ks, nk, scale, tbase, wcnt, n, g->off,
+                                                             g->col, g->nnz, ctx->status);
     note_launch();
     GB_CUDA(cudaGetLastError());
     return build_graph_aux(g, s);
@@ -436,14 +458,21 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
     GB_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
     if (nk == 0) return empty_csr(g, s);
     uint64_t *k0 = nullptr, *k1 = nullptr;
+    unsigned long long *hist = nullptr;
+    const int sort_passes = (2 * scale + 7) / 8;
+    const int passes = sort_passes <= SYM_MAX_PASSES ? sort_passes : 0;  // 0: the sort counts
     Scratch tmp(s);
     GB_CUDA(tmp.alloc(&k0, (size_t)nk));
     GB_CUDA(tmp.alloc(&k1, (size_t)nk));
-    k1_sym_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(edges, m, scale,
-                                                   reinterpret_cast<ulonglong2 *>(k0), ctx->status);
+    if (passes) {
+        GB_CUDA(tmp.alloc(&hist, (size_t)passes * 256));
+        GB_CUDA(cudaMemsetAsync(hist, 0, (size_t)passes * 256 * sizeof(unsigned long long), s));
+    }
+    k1_sym_kernel<<<ctx->num_sms * 8, SYM_THREADS, 0, s>>>(edges, m, scale, reinterpret_cast<ulonglong2 *>(k0),
+                                                           passes, hist, ctx->status);
     note_launch();
     GB_CUDA(cudaGetLastError());
-    return csr_from_keys(k0, k1, nk, scale, g, s);
+    return csr_from_keys(k0, k1, nk, scale, g, s, hist);
 }
 
 gb_status kron_csr(int scale, int edgefactor, double a, double b, double c, uint64_t seed_gen,

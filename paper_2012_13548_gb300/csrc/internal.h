@@ -121,11 +121,13 @@ class Scratch {
 // Radix sort (sort.cu): ascending LSD sort of uint64 keys by bits
 // [begin_bit, end_bit), optionally carrying uint32 values.  keys/keys_alt
 // (and vals/vals_alt) are two caller buffers of n entries; *keys_out and
-// *vals_out receive whichever buffer holds the result.
+// *vals_out receive whichever buffer holds the result.  hist, if given,
+// holds the digit counts of every pass (8-bit digits from begin_bit,
+// [passes][256]) already counted by the caller; otherwise the sort counts them.
 // ---------------------------------------------------------------------------
 gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                      int64_t n, int begin_bit, int end_bit, uint64_t **keys_out,
-                     uint32_t **vals_out, cudaStream_t s);
+                     uint32_t **vals_out, cudaStream_t s, const unsigned long long *hist = nullptr);
 // Keys per portion of radix_sort (process-wide; 0 restores the default 2^28).
 gb_status set_sort_portion(int64_t keys);
 int64_t sort_portion();

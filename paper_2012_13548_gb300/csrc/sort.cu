@@ -240,7 +240,7 @@ int64_t sort_portion() { return g_portion.load(); }
 
 gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                      int64_t n, int begin_bit, int end_bit, uint64_t **keys_out,
-                     uint32_t **vals_out, cudaStream_t s)
+                     uint32_t **vals_out, cudaStream_t s, const unsigned long long *hist_in)
 {
     *keys_out = keys;
     if (vals_out) *vals_out = vals;
@@ -271,15 +271,17 @@ gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_
     unsigned long long *hist = nullptr, *base = nullptr;
     unsigned *status = nullptr;
     Scratch tmp(s);
-    GB_CUDA(tmp.alloc(&hist, (size_t)passes * 256));
     GB_CUDA(tmp.alloc(&base, (size_t)passes * (portions + 1) * 256));
     GB_CUDA(tmp.alloc(&status, 1 + (size_t)tiles_max * 256));
-    GB_CUDA(cudaMemsetAsync(hist, 0, (size_t)passes * 256 * sizeof(unsigned long long), s));
-
-    const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 4, (n + 511) / 512));
-    rs_hist_kernel<<<hist_blocks, 512, 0, s>>>(keys, n, begin_bit, passes, hist);
-    note_launch();
-    rs_scan_kernel<<<1, 256, 0, s>>>(hist, passes, portions, base);
+    if (!hist_in) {
+        GB_CUDA(tmp.alloc(&hist, (size_t)passes * 256));
+        GB_CUDA(cudaMemsetAsync(hist, 0, (size_t)passes * 256 * sizeof(unsigned long long), s));
+        const int hist_blocks =
+            (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 4, (n + 511) / 512));
+        rs_hist_kernel<<<hist_blocks, 512, 0, s>>>(keys, n, begin_bit, passes, hist);
+        note_launch();
+    }
+    rs_scan_kernel<<<1, 256, 0, s>>>(hist_in ? hist_in : hist, passes, portions, base);
     note_launch();
     GB_CUDA(cudaGetLastError());
 
