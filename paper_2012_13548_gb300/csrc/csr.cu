@@ -30,17 +30,17 @@ constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;  // 4096 keys
 constexpr int SITE_K1_RANGE = 10;
 
 // Both directed keys of every tuple, and the digit counts of the radix
-// sort's passes over them (8-bit digits from bit 0; `passes` of them), so
-// that the sort does not read the keys once more for its histogram.
+// sort's passes over them (plan.passes of them; 0: none), so that the sort
+// does not read the keys once more for its histogram.
 constexpr int SYM_THREADS = 256;
-constexpr int SYM_MAX_PASSES = 8;
 __global__ void __launch_bounds__(SYM_THREADS) k1_sym_kernel(const int64_t *__restrict__ edges, int64_t m,
                                                              int scale, ulonglong2 *__restrict__ keys,
-                                                             int passes, unsigned long long *__restrict__ hist,
+                                                             SortPlan plan, unsigned long long *__restrict__ hist,
                                                              DevStatus *st)
 {
-    __shared__ unsigned s_h[SYM_MAX_PASSES][256];
-    for (int i = threadIdx.x; i < SYM_MAX_PASSES * 256; i += blockDim.x) (&s_h[0][0])[i] = 0;
+    __shared__ unsigned s_h[RS_MAX_PASSES][RS_RADIX_MAX];
+    const int passes = plan.passes;
+    for (int i = threadIdx.x; i < RS_MAX_PASSES * RS_RADIX_MAX; i += blockDim.x) (&s_h[0][0])[i] = 0;
     __syncthreads();
     const int64_t n = int64_t(1) << scale;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -54,13 +54,16 @@ __global__ void __launch_bounds__(SYM_THREADS) k1_sym_kernel(const int64_t *__re
         const uint64_t ka = ((uint64_t)u << scale) | (uint64_t)v;
         const uint64_t kb = ((uint64_t)v << scale) | (uint64_t)u;
         keys[e] = make_ulonglong2(ka, kb);
-        for (int q = 0; q < passes; ++q) {  // passes <= SYM_MAX_PASSES (0: no counts)
-            atomicAdd(&s_h[q][(unsigned)(ka >> (8 * q)) & 255u], 1u);
-            atomicAdd(&s_h[q][(unsigned)(kb >> (8 * q)) & 255u], 1u);
+#pragma unroll
+        for (int q = 0; q < RS_MAX_PASSES; ++q) {  // unrolled: the plan stays in registers
+            if (q >= passes) break;
+            const unsigned dm = (1u << plan.bits[q]) - 1u;
+            atomicAdd(&s_h[q][(unsigned)(ka >> plan.shift[q]) & dm], 1u);
+            atomicAdd(&s_h[q][(unsigned)(kb >> plan.shift[q]) & dm], 1u);
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+    for (int i = threadIdx.x; i < passes * RS_RADIX_MAX; i += blockDim.x) {
         const unsigned c = (&s_h[0][0])[i];
         if (c) atomicAdd(&hist[i], (unsigned long long)c);
     }
@@ -459,17 +462,18 @@ gb_status build_csr(const int64_t *edges, int64_t m, int scale, gb_graph *g, cud
     if (nk == 0) return empty_csr(g, s);
     uint64_t *k0 = nullptr, *k1 = nullptr;
     unsigned long long *hist = nullptr;
-    const int sort_passes = (2 * scale + 7) / 8;
-    const int passes = sort_passes <= SYM_MAX_PASSES ? sort_passes : 0;  // 0: the sort counts
+    SortPlan plan = sort_plan(0, 2 * scale);
     Scratch tmp(s);
     GB_CUDA(tmp.alloc(&k0, (size_t)nk));
     GB_CUDA(tmp.alloc(&k1, (size_t)nk));
-    if (passes) {
-        GB_CUDA(tmp.alloc(&hist, (size_t)passes * 256));
-        GB_CUDA(cudaMemsetAsync(hist, 0, (size_t)passes * 256 * sizeof(unsigned long long), s));
+    if (plan.passes > RS_MAX_PASSES) {
+        plan.passes = 0;  // the sort counts (and rejects) it
+    } else {
+        GB_CUDA(tmp.alloc(&hist, (size_t)plan.passes * RS_RADIX_MAX));
+        GB_CUDA(cudaMemsetAsync(hist, 0, (size_t)plan.passes * RS_RADIX_MAX * sizeof(unsigned long long), s));
     }
     k1_sym_kernel<<<ctx->num_sms * 8, SYM_THREADS, 0, s>>>(edges, m, scale, reinterpret_cast<ulonglong2 *>(k0),
-                                                           passes, hist, ctx->status);
+                                                           plan, hist, ctx->status);
     note_launch();
     GB_CUDA(cudaGetLastError());
     return csr_from_keys(k0, k1, nk, scale, g, s, hist);

@@ -122,12 +122,24 @@ class Scratch {
 // [begin_bit, end_bit), optionally carrying uint32 values.  keys/keys_alt
 // (and vals/vals_alt) are two caller buffers of n entries; *keys_out and
 // *vals_out receive whichever buffer holds the result.  hist, if given,
-// holds the digit counts of every pass (8-bit digits from begin_bit,
-// [passes][256]) already counted by the caller; otherwise the sort counts them.
+// holds the digit counts of every pass of sort_plan(begin_bit, end_bit),
+// already counted by the caller; otherwise the sort counts them.
 // ---------------------------------------------------------------------------
 gb_status radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                      int64_t n, int begin_bit, int end_bit, uint64_t **keys_out,
                      uint32_t **vals_out, cudaStream_t s, const unsigned long long *hist = nullptr);
+// The sort's passes over bits [begin_bit, end_bit): ceil(bits / 9) passes, the
+// first (bits - 8 * passes) of them 9 bits wide and the others 8.  A caller
+// that counts the digits itself fills hist[p * RS_RADIX_MAX + digit].
+constexpr int RS_MAX_PASSES = 8;
+constexpr int RS_MAX_BITS = 9;
+constexpr int RS_RADIX_MAX = 1 << RS_MAX_BITS;
+struct SortPlan {
+    int passes;
+    int shift[RS_MAX_PASSES];
+    int bits[RS_MAX_PASSES];
+};
+SortPlan sort_plan(int begin_bit, int end_bit);
 // Keys per portion of radix_sort (process-wide; 0 restores the default 2^28).
 gb_status set_sort_portion(int64_t keys);
 int64_t sort_portion();
