@@ -184,6 +184,18 @@ gb_status graph_info(const gb_graph *g, int64_t *n, int64_t *nnz);
  * graph_free). */
 gb_status graph_csr_view(const gb_graph *g, const int64_t **off, const int32_t **col);
 
+/* Build g's degree-ordered copy for bfs_batch (a no-op if it exists): the
+ * vertices renumbered by decreasing degree (ties by id), each row keeping its
+ * entry order, so that the frontier masks of the few vertices holding most of
+ * the edge endpoints (Sec. 2.1's skewed degrees) are read from neighbouring
+ * lines.  bfs_batch searches a graph that has the copy on it, with the same
+ * results (levels, and parents as original ids), and builds it by itself for
+ * graphs of 2^25 or more vertices.  It adds 8 (n+1) + 4 nnz + 8 n bytes to the
+ * graph until graph_free; GB_ERR_NOMEM leaves the graph as it was.  Part of
+ * kernel 1 in the sense of Sec. 4.3 (a structure built once per graph), so
+ * not part of the searches' time.  Calls on one graph must not overlap. */
+gb_status graph_prepare_batched(gb_graph *g, gb_stream s);
+
 /* ------------------------------------------------------------------------ */
 /* Sec. 2.3: kernel 2, breadth-first search.                                 */
 /* ------------------------------------------------------------------------ */

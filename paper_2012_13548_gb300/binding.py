@@ -109,6 +109,7 @@ def lib():
             "graph_free": (ctypes.c_int, [_vp]),
             "graph_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
             "graph_csr_view": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+            "graph_prepare_batched": (ctypes.c_int, [_vp, _vp]),
             "bfs_get_options": (ctypes.c_int, [ctypes.POINTER(gb_bfs_options)]),
             "bfs_set_options": (ctypes.c_int, [ctypes.POINTER(gb_bfs_options)]),
             "bfs": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp]),
@@ -157,7 +158,7 @@ def exported_symbols():
             "gb_sort_portion", "gb_debug_fail_allocations", "gb_debug_live_allocations",
             "gb_device_status", "kron_generate",
             "graph_build_csr", "graph_build_csr_counting", "graph_from_csr", "graph_generate_csr",
-            "graph_free", "graph_info", "graph_csr_view",
+            "graph_free", "graph_info", "graph_csr_view", "graph_prepare_batched",
             "bfs_get_options", "bfs_set_options", "bfs", "bfs_batch", "bfs_multi_graph",
             "bfs_last_stats", "bfs_noalloc", "bfs_validate", "kron_weights", "graph_build_csr_weighted",
             "graph_weights_view", "sssp", "sssp_last_stats", "sssp_validate", "server_create",
@@ -226,6 +227,11 @@ class Graph:
         _check(lib().graph_weights_view(self.handle, ctypes.byref(w)))
         dev = torch.cuda.current_device()
         return torch.as_tensor(_DevArray(w.value, (self.nnz,), "<i4", self), device="cuda:%d" % dev)
+
+    def prepare_batched(self, stream=None):
+        """Build the degree-ordered copy bfs_batch searches (graph_prepare_batched)."""
+        _check(lib().graph_prepare_batched(self.handle, _stream(stream)))
+        return self
 
     def free(self):
         if self._h:

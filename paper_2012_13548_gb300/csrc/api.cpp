@@ -78,7 +78,7 @@ SsspDevStats *sssp_stats_buffer()
 // Free every device array of a graph (any may be null) and the graph.
 void destroy_graph(gb_graph *g)
 {
-    void *arrays[] = {g->off, g->col, g->nz, g->hub, g->nzl, g->deg16, g->wgt, g->wadj};
+    void *arrays[] = {g->off, g->col, g->nz, g->hub, g->nzl, g->deg16, g->rl_off, g->rl_col, g->rl_perm, g->rl_inv, g->wgt, g->wadj};
     for (void *p : arrays)
         if (p) gb::dfree(p);
     delete g;
@@ -550,6 +550,15 @@ gb_status graph_free(gb_graph *g)
         cudaDeviceSynchronize();
         destroy_graph(g);
         return GB_OK;
+    });
+}
+
+gb_status graph_prepare_batched(gb_graph *g, gb_stream s)
+{
+    return guarded([&]() -> gb_status {
+        gb_status rc = check_graph(g);
+        if (rc != GB_OK) return rc;
+        return gb::prepare_batched(g, as_stream(s));
     });
 }
 

@@ -344,6 +344,244 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const int64_t *__restr
 
 }  // namespace
 
+namespace {
+
+// ---- The degree-ordered copy of a CSR (for the batched search) -----------
+// Its vertex i is original vertex perm[i], in order of decreasing degree (ties
+// by id: a stable sort), so the masks of the few vertices that hold most of a
+// Kronecker graph's edge endpoints lie together.  Each row keeps its original
+// entry order (entries renamed), so the first neighbour of a row in the copy is
+// still its smallest original id.
+constexpr int RL_THREADS = 512;
+constexpr int RL_ITEMS = 16;
+constexpr int RL_TILE = RL_THREADS * RL_ITEMS;  // offsets per scan tile
+constexpr int64_t RL_LONG = 4096;               // rows copied by a whole block
+
+__global__ void rl_key_kernel(const int64_t *__restrict__ off, int64_t n, uint64_t *__restrict__ key,
+                              uint32_t *__restrict__ val)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t d = off[v + 1] - off[v];
+        key[v] = 0xffffffffull - (uint64_t)(d < 0xffffffffll ? d : 0xffffffffll);  // ascending = by degree, down
+        val[v] = (uint32_t)v;
+    }
+}
+
+// perm and inv from the sorted ids; dnew[i] = degree of perm[i]
+__global__ void rl_perm_kernel(const uint32_t *__restrict__ sorted, const int64_t *__restrict__ off, int64_t n,
+                               int32_t *__restrict__ perm, int32_t *__restrict__ inv, int64_t *__restrict__ dnew)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t v = sorted[i];
+        perm[i] = (int32_t)v;
+        inv[v] = (int32_t)i;
+        dnew[i] = off[v + 1] - off[v];
+    }
+}
+
+// Exclusive scan of dnew into rl_off: tile sums, a scan of the tile sums
+// (one block), then each tile scans itself from its base.
+__global__ void __launch_bounds__(RL_THREADS) rl_tile_sum_kernel(const int64_t *__restrict__ d, int64_t n,
+                                                                 unsigned long long *__restrict__ tsum)
+{
+    __shared__ unsigned long long s_w[RL_THREADS / 32];
+    const int64_t t0 = (int64_t)blockIdx.x * RL_TILE;
+    unsigned long long c = 0;
+    for (int j = 0; j < RL_ITEMS; ++j) {
+        const int64_t i = t0 + (int64_t)j * RL_THREADS + threadIdx.x;
+        if (i < n) c += (unsigned long long)d[i];
+    }
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < RL_THREADS / 32; ++w) t += s_w[w];
+        tsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) rl_tile_scan_kernel(const unsigned long long *__restrict__ tsum,
+                                                            int64_t ntiles, unsigned long long *__restrict__ tbase)
+{
+    __shared__ unsigned long long s_w[32];
+    const int tid = threadIdx.x;
+    const int64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = (int64_t)tid * per < ntiles ? (int64_t)tid * per : ntiles;
+    const int64_t e = b0 + per < ntiles ? b0 + per : ntiles;
+    unsigned long long sum = 0;
+    for (int64_t i = b0; i < e; ++i) sum += tsum[i];
+    const unsigned long long incl = warp_inclusive_scan(sum);
+    if ((tid & 31) == 31) s_w[tid >> 5] = incl;
+    __syncthreads();
+    if (tid < 32) {
+        const unsigned long long w = s_w[tid];
+        s_w[tid] = warp_inclusive_scan(w) - w;
+    }
+    __syncthreads();
+    unsigned long long run = s_w[tid >> 5] + incl - sum;
+    for (int64_t i = b0; i < e; ++i) {
+        tbase[i] = run;
+        run += tsum[i];
+    }
+}
+
+__global__ void __launch_bounds__(RL_THREADS) rl_tile_write_kernel(const int64_t *__restrict__ d, int64_t n,
+                                                                   const unsigned long long *__restrict__ tbase,
+                                                                   int64_t *__restrict__ rl_off)
+{
+    __shared__ unsigned long long s_w[RL_THREADS / 32];
+    // thread t takes RL_ITEMS consecutive entries of the tile
+    const int64_t i0 = (int64_t)blockIdx.x * RL_TILE + (int64_t)threadIdx.x * RL_ITEMS;
+    unsigned long long own = 0;
+    for (int j = 0; j < RL_ITEMS; ++j)
+        if (i0 + j < n) own += (unsigned long long)d[i0 + j];
+    const unsigned long long incl = warp_inclusive_scan(own);
+    if ((threadIdx.x & 31) == 31) s_w[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned long long w = threadIdx.x < RL_THREADS / 32 ? s_w[threadIdx.x] : 0ull;
+        const unsigned long long x = warp_inclusive_scan(w) - w;
+        if (threadIdx.x < RL_THREADS / 32) s_w[threadIdx.x] = x;
+    }
+    __syncthreads();
+    unsigned long long run = tbase[blockIdx.x] + s_w[threadIdx.x >> 5] + incl - own;
+    for (int j = 0; j < RL_ITEMS; ++j)
+        if (i0 + j < n) {
+            rl_off[i0 + j] = (int64_t)run;
+            run += (unsigned long long)d[i0 + j];
+        }
+}
+
+// Rows of at most RL_LONG entries: a warp takes 32 rows and streams their
+// entries as one sequence (lane k of a round copies entry k), renaming each.
+__global__ void rl_copy_rows_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                    const int32_t *__restrict__ perm, const int32_t *__restrict__ inv,
+                                    const int64_t *__restrict__ rl_off, int64_t n, int32_t *__restrict__ rl_col)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = gwarp * 32; r0 < n; r0 += nwarps * 32) {
+        const int64_t r = r0 + lane;
+        int64_t src = 0, dst = 0, d = 0;
+        if (r < n) {
+            dst = rl_off[r];
+            d = rl_off[r + 1] - dst;
+            src = off[perm[r]];
+            if (d > RL_LONG) d = 0;  // copied by rl_copy_long_kernel
+        }
+        const int64_t incl = warp_inclusive_scan(d);
+        const int64_t total = __shfl_sync(kFull, incl, 31);
+        const int64_t excl = incl - d;
+        for (int64_t b = 0; b < total; b += 32) {
+            const int64_t k = b + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int cand = owner + step;
+                if (__shfl_sync(kFull, excl, cand) <= k) owner = cand;
+            }
+            const int64_t so = __shfl_sync(kFull, src, owner);
+            const int64_t doo = __shfl_sync(kFull, dst, owner);
+            const int64_t eo = __shfl_sync(kFull, excl, owner);
+            if (k < total) rl_col[doo + (k - eo)] = inv[col[so + (k - eo)]];
+        }
+    }
+}
+
+// Rows longer than RL_LONG (the first rows of the copy): one block each.
+__global__ void rl_copy_long_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                    const int32_t *__restrict__ perm, const int32_t *__restrict__ inv,
+                                    const int64_t *__restrict__ rl_off, int64_t nlong, int32_t *__restrict__ rl_col)
+{
+    for (int64_t r = blockIdx.x; r < nlong; r += gridDim.x) {
+        const int64_t dst = rl_off[r];
+        const int64_t d = rl_off[r + 1] - dst;
+        if (d <= RL_LONG) continue;
+        const int64_t src = off[perm[r]];
+        for (int64_t k = threadIdx.x; k < d; k += blockDim.x) rl_col[dst + k] = inv[col[src + k]];
+    }
+}
+
+}  // namespace
+
+gb_status build_batched_layout(gb_graph *g, cudaStream_t s)
+{
+    Context *ctx = context();
+    if (!ctx) return GB_ERR_CUDA;
+    const int64_t n = g->n;
+    if (g->rl_col || n == 0) return GB_OK;
+    if (n >= (int64_t(1) << 31)) {
+        set_error("batched layout: more than 2^31 vertices");
+        return GB_ERR_RANGE;
+    }
+    gb_graph tmpg;  // the new arrays, moved into g once all are built
+    Scratch tmp(s);
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr;
+    GB_CUDA(tmp.alloc(&k0, (size_t)n));
+    GB_CUDA(tmp.alloc(&k1, (size_t)n));
+    GB_CUDA(tmp.alloc(&v0, (size_t)n));
+    GB_CUDA(tmp.alloc(&v1, (size_t)n));
+    rl_key_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(g->off, n, k0, v0);
+    note_launch();
+    GB_CUDA(cudaGetLastError());
+    uint64_t *ks = nullptr;
+    uint32_t *vs = nullptr;
+    gb_status rc = radix_sort(k0, k1, v0, v1, n, 0, 32, &ks, &vs, s);
+    if (rc != GB_OK) return rc;
+    int64_t *dnew = reinterpret_cast<int64_t *>(ks == k0 ? k1 : k0);  // the sort's spare buffer
+    auto fail = [&](cudaError_t e) {
+        void *arrays[] = {tmpg.rl_off, tmpg.rl_col, tmpg.rl_perm, tmpg.rl_inv};
+        for (void *p : arrays)
+            if (p) gb::dfree(p);
+        return cuda_fail(e, "batched layout");
+    };
+    cudaError_t e;
+    if ((e = gb::dmalloc(&tmpg.rl_perm, (size_t)n * sizeof(int32_t))) != cudaSuccess ||
+        (e = gb::dmalloc(&tmpg.rl_inv, (size_t)n * sizeof(int32_t))) != cudaSuccess ||
+        (e = gb::dmalloc(&tmpg.rl_off, (size_t)(n + 1) * sizeof(int64_t))) != cudaSuccess ||
+        (e = gb::dmalloc(&tmpg.rl_col, (size_t)col_alloc_entries(g->nnz) * sizeof(int32_t))) != cudaSuccess)
+        return fail(e);
+    rl_perm_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(vs, g->off, n, tmpg.rl_perm, tmpg.rl_inv, dnew);
+    note_launch();
+    const int64_t ntiles = (n + RL_TILE - 1) / RL_TILE;
+    unsigned long long *tsum = nullptr, *tbase = nullptr;
+    if ((e = tmp.alloc(&tsum, (size_t)ntiles)) != cudaSuccess || (e = tmp.alloc(&tbase, (size_t)ntiles)) != cudaSuccess)
+        return fail(e);
+    rl_tile_sum_kernel<<<(unsigned)ntiles, RL_THREADS, 0, s>>>(dnew, n, tsum);
+    note_launch();
+    rl_tile_scan_kernel<<<1, 1024, 0, s>>>(tsum, ntiles, tbase);
+    note_launch();
+    rl_tile_write_kernel<<<(unsigned)ntiles, RL_THREADS, 0, s>>>(dnew, n, tbase, tmpg.rl_off);
+    note_launch();
+    const int64_t nnz = g->nnz;
+    if ((e = cudaMemcpyAsync(tmpg.rl_off + n, &g->nnz, sizeof(int64_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(e);
+    (void)nnz;
+    rl_copy_rows_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(g->off, g->col, tmpg.rl_perm, tmpg.rl_inv, tmpg.rl_off,
+                                                         n, tmpg.rl_col);
+    note_launch();
+    // the long rows are the first ones of the copy; a block per row up to the
+    // first that is not long (each block skips the short ones)
+    rl_copy_long_kernel<<<ctx->num_sms * 4, 512, 0, s>>>(g->off, g->col, tmpg.rl_perm, tmpg.rl_inv, tmpg.rl_off,
+                                                          std::min<int64_t>(n, g->nnz / (RL_LONG + 1) + 1),
+                                                          tmpg.rl_col);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    g->rl_perm = tmpg.rl_perm;
+    g->rl_inv = tmpg.rl_inv;
+    g->rl_off = tmpg.rl_off;
+    g->rl_col = tmpg.rl_col;
+    tmpg.rl_perm = tmpg.rl_inv = nullptr;
+    tmpg.rl_off = nullptr;
+    tmpg.rl_col = nullptr;
+    return GB_OK;
+}
+
 gb_status build_graph_aux(gb_graph *g, cudaStream_t s)
 {
     Context *ctx = context();

@@ -162,6 +162,13 @@ struct gb_graph {
     int64_t nnzv = 0;
     uint32_t *wgt = nullptr; // device [nnz] weights in units of 2^-24 (weighted graphs only)
     uint2 *wadj = nullptr;   // device [nnz] (column, weight) of each row by ascending weight
+    // Degree-ordered copy for the batched search (built by build_batched_layout;
+    // null until then): vertex i of the copy is rl_perm[i], vertices in order of
+    // decreasing degree (ties by id), rows holding their original entry order.
+    int64_t *rl_off = nullptr;   // device [n+1]
+    int32_t *rl_col = nullptr;   // device [nnz] (padded like col), entries relabelled
+    int32_t *rl_perm = nullptr;  // device [n]: copy id -> original id
+    int32_t *rl_inv = nullptr;   // device [n]: original id -> copy id
     int device = -1;
 };
 
@@ -181,6 +188,11 @@ gb_status kron_csr(int scale, int edgefactor, double a, double b, double c, uint
                    uint64_t seed_perm, gb_graph *g, cudaStream_t s);
 // The degree >= 1 bitmap and the hub array of a graph whose CSR is in place (csr.cu).
 gb_status build_graph_aux(gb_graph *g, cudaStream_t s);
+// The degree-ordered copy of g's CSR for the batched search (csr.cu); a no-op
+// if it exists.  Not thread-safe for one graph: the caller serialises.
+gb_status build_batched_layout(gb_graph *g, cudaStream_t s);
+// The same, serialised with the batched search's own builds (msbfs.cu).
+gb_status prepare_batched(gb_graph *g, cudaStream_t s);
 
 // Kernel 1 with the weight row: build_csr, then each entry's least weight (sssp.cu).
 gb_status build_csr_weighted(const int64_t *edges, const float *w, int64_t m, int scale, gb_graph *g,

@@ -49,6 +49,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 namespace gb {
@@ -63,6 +64,10 @@ constexpr int MS_QBUF = 256;  // per-warp staging of newly active vertices
 constexpr int MS_BBUF = 32;   // per-warp staging of newly active big vertices
 constexpr int MS_HIST = 8;    // batch calls: levels whose reached-bit masks are kept
 constexpr int MS_HUGE = 4096; // bottom-up: rows longer than this are scanned first, one per warp
+// batch calls on graphs of at least this many vertices (frontier masks of
+// 256 MB and more, twice the L2) run on the graph's degree-ordered copy; at
+// 2^24 vertices the copy measured slower, at 2^26 faster
+constexpr int64_t MS_LAYOUT_MIN_N = int64_t(1) << 25;
 constexpr int SITE_MS_BAR = 30;
 constexpr int SITE_MS_LEVELS = 31;
 
@@ -77,6 +82,11 @@ struct MsGraph {
     int32_t *pst;  // batch calls: parents staged vertex-major, [n][kst]
     int32_t *lst;  // and levels
     int64_t kst;
+    // the search runs on the graph's degree-ordered copy (off/col above are the
+    // copy's): ids inside the kernel are copy ids, perm maps them back and inv
+    // maps the roots in; both null when the search runs on the graph itself
+    const int32_t *perm;
+    const int32_t *inv;
 };
 
 }  // namespace
@@ -209,10 +219,25 @@ __device__ __forceinline__ int find_graph(const int64_t *s_voff, int ng, int64_t
     return lo;
 }
 
+// The original id of a vertex of the search (the identity unless the search
+// runs on the degree-ordered copy).  The staged outputs (parents, levels, the
+// level masks) are kept by original id, so the final pass reads them in line
+// with its output rows.
+__device__ __forceinline__ int64_t orig_id(const MsGraph &G, int64_t local)
+{
+    return G.perm ? (int64_t)__ldg(&G.perm[local]) : local;
+}
+
+// local: the vertex whose parents these are (already an original id if
+// local_orig); p: the parent, an id of the search.
 template <typename T>
 __device__ __forceinline__ void write_parents(const MsGraph &G, const MsSlots *S, int64_t local,
-                                              T bits, int32_t p)
+                                              T bits, int32_t p, bool local_orig = false)
 {
+    if (!S && G.perm) {  // staged by original id, as an original id
+        if (!local_orig) local = orig_id(G, local);
+        p = (int32_t)orig_id(G, p);
+    }
     while (bits) {
         const int b = __ffsll((unsigned long long)bits) - 1;
         bits &= bits - 1;
@@ -226,11 +251,13 @@ template <typename T>
 __device__ __forceinline__ void write_levels(const MsGraph &G, const MsSlots *S, int64_t local,
                                              T bits, int32_t lvl)
 {
+    if (!S && lvl < MS_HIST) return;  // earlier levels: the mask history
+    if (!S && G.perm) local = orig_id(G, local);
     while (bits) {
         const int b = __ffsll((unsigned long long)bits) - 1;
         bits &= bits - 1;
         if (S) S->lev[b][local] = lvl - S->start[b];
-        else if (lvl >= MS_HIST) G.lst[local * G.kst + b] = lvl;  // earlier levels: the mask history
+        else G.lst[local * G.kst + b] = lvl;
     }
 }
 
@@ -342,8 +369,9 @@ __device__ __forceinline__ void ms_td_edge(bool valid, T f, int64_t gu, int32_t 
     ms_append(first, gu, deg, wb, qn, bn, my_mf, nxt, act_next, bigq_next);
 }
 
-// Rows of a warp (lane i owns one row: graph g, local id lu, adjacency
-// [s, e), missing bits `need`) are scanned together.  Each round deals 4 x 32
+// Rows of a warp (lane i owns one row: graph g, adjacency [s, e), missing
+// bits `need`; lu is the row's vertex as the staged outputs know it, its
+// original id) are scanned together.  Each round deals 4 x 32
 // neighbour slots, an equal share to every row still missing bits, so a row
 // that completes early stops taking slots; the loads of a round are issued
 // together.  Slots are processed in neighbour order: a segmented prefix-OR
@@ -406,7 +434,7 @@ __device__ __forceinline__ T ms_rows(const MsGraph *s_g, const MsSlots *S, const
         for (int t = 0; t < 4; ++t) {
             const T bt = (T)(mine & m[t]);
             if (bt) {
-                write_parents(G, S, luo, bt, c[t]);
+                write_parents(G, S, luo, bt, c[t], true);
                 mine &= (T)~bt;
             }
         }
@@ -419,8 +447,8 @@ __device__ __forceinline__ T ms_rows(const MsGraph *s_g, const MsSlots *S, const
     return found;
 }
 
-// Warp-collective bottom-up scan of one long row [s, e) of graph g (local id
-// lu) for the bits `need`, 128 entries a round: lane i takes entries
+// Warp-collective bottom-up scan of one long row [s, e) of graph g (its vertex
+// lu as an original id, for the staged parents) for the bits `need`, 128 entries a round: lane i takes entries
 // 4i..4i+3 of the round (one 16-byte load when the columns are aligned) and
 // ORs their masks in order; an exclusive prefix-OR over the lanes then gives
 // each bit's first supplier in row order (the smallest-id parent), which the
@@ -469,7 +497,7 @@ __device__ __forceinline__ T ms_row_warp(const MsGraph *s_g, const MsSlots *S, c
         for (int t = 0; t < 4; ++t) {
             const T bt = (T)(mine & m[t]);
             if (bt) {
-                write_parents(G, S, lu, bt, c[t]);
+                write_parents(G, S, lu, bt, c[t], true);
                 mine &= (T)~bt;
             }
         }
@@ -538,7 +566,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             for (int g = 0; g < a.ng; ++g) {
                 const MsGraph G = s_g[g];
                 for (int b = 0; b < a.k; ++b) {
-                    const int64_t r = a.roots[(int64_t)g * a.k + b];
+                    const int64_t r0 = a.roots[(int64_t)g * a.k + b];
+                    const int64_t r = G.inv ? (int64_t)G.inv[r0] : r0;
                     const int64_t gid = G.voff + r;
                     if (a.mbuf[gid] == 0) {
                         a.act[na++] = (int32_t)gid;
@@ -552,8 +581,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                     }
                     a.mbuf[gid] |= (T)((T)1 << b);
                     a.seen[gid] |= (T)((T)1 << b);
-                    a.hist[gid] |= (T)((T)1 << b);  // level 0
-                    G.pst[r * G.kst + b] = (int32_t)r;
+                    a.hist[G.voff + r0] |= (T)((T)1 << b);  // level 0 (staging: original ids)
+                    G.pst[r0 * G.kst + b] = (int32_t)r0;
                 }
             }
             h->ctl[0].na = na;
@@ -703,11 +732,12 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                         re = s_g[g].off[lu + 1];
                     }
                 }
-                if (a.canonical) ms_rows(s_g, S, M, g, lu, rs, re, nw, my_edges);
+                if (a.canonical) ms_rows(s_g, S, M, g, orig_id(s_g[g], lu), rs, re, nw, my_edges);
                 if (i < nn) {
                     if (a.canonical) write_levels(s_g[g], S, lu, nw, l + 1);
                     st_mask(&a.seen[gu], (T)(ld_mask(&a.seen[gu]) | nw));
-                    if (a.hist && l + 1 < MS_HIST) a.hist[(size_t)(l + 1) * a.mstride + gu] = nw;
+                    if (a.hist && l + 1 < MS_HIST)
+                        a.hist[(size_t)(l + 1) * a.mstride + s_g[g].voff + orig_id(s_g[g], lu)] = nw;
                     reached_new += __popcll((unsigned long long)nw);
                     my_any |= nw;
                 }
@@ -726,13 +756,14 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                 T found = 0;
                 if (need) {
                     my_touched += (lane == 0);
-                    found = ms_row_warp(s_g, S, M, 0, gu, rs, re, need, a.vec_col != 0, my_edges);
+                    found = ms_row_warp(s_g, S, M, 0, orig_id(s_g[0], gu), rs, re, need, a.vec_col != 0,
+                                        my_edges);
                 }
                 if (found && lane == 0) {
                     write_levels(s_g[0], S, gu, found, l + 1);
                     st_mask(&a.seen[gu], (T)(sn | found));
                     st_mask(&Mn[gu], found);
-                    if (a.hist && l + 1 < MS_HIST) a.hist[(size_t)(l + 1) * a.mstride + gu] = found;
+                    if (a.hist && l + 1 < MS_HIST) a.hist[(size_t)(l + 1) * a.mstride + orig_id(s_g[0], gu)] = found;
                     reached_new += __popcll((unsigned long long)found);
                     my_any |= found;
                 }
@@ -775,12 +806,14 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
                     re = rs + deg;
                 }
                 my_touched += (need != 0);
-                const T found = ms_rows(s_g, S, M, g, lu, rs, re, need, my_edges);
+                // the row's original id, loaded once (consecutive rows: one load per warp)
+                const T found = ms_rows(s_g, S, M, g, orig_id(s_g[g], lu), rs, re, need, my_edges);
                 if (found) {
                     write_levels(s_g[g], S, lu, found, l + 1);
                     st_mask(&a.seen[gu], (T)(sn | found));
                     st_mask(&Mn[gu], found);
-                    if (a.hist && l + 1 < MS_HIST) a.hist[(size_t)(l + 1) * a.mstride + gu] = found;
+                    if (a.hist && l + 1 < MS_HIST)
+                        a.hist[(size_t)(l + 1) * a.mstride + s_g[g].voff + orig_id(s_g[g], lu)] = found;
                     reached_new += __popcll((unsigned long long)found);
                     my_any |= found;
                 }
@@ -832,8 +865,10 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             if (gv >= ntot) continue;
             const int g = find_graph(s_voff, a.ng, gv);
             const MsGraph &G = s_g[g];
-            const int64_t lu = gv - G.voff;
-            const T sn = ld_mask(&a.seen[gv]);
+            const int64_t lu = gv - G.voff;  // the output's vertex (original id)
+            // the reached bits from the search state (by search id); the
+            // staged parents, levels and level masks are by original id
+            const T sn = ld_mask(&a.seen[G.voff + (G.inv ? (int64_t)G.inv[lu] : lu)]);
             T hm[MS_HIST];
 #pragma unroll
             for (int j = 0; j < MS_HIST; ++j) hm[j] = a.hist[(size_t)j * a.mstride + gv];
@@ -961,14 +996,31 @@ gb_status ms_launch(std::vector<MsGraph> gs, int k, const std::vector<int64_t> &
     return GB_OK;
 }
 
+// Serialises the build of a graph's degree-ordered copy by batched calls.
+std::mutex g_layout_mu;
+
 }  // namespace
+
+gb_status prepare_batched(gb_graph *g, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_layout_mu);
+    return build_batched_layout(g, s);
+}
 
 gb_status msbfs_impl(const gb_graph *g, const int64_t *roots, int k, int32_t *parents,
                      int32_t *levels, BfsDevStats *stats, cudaStream_t s)
 {
+    // A graph whose frontier masks (8 n bytes) outgrow the L2 is searched on its
+    // degree-ordered copy, built at the first batched call if not yet there.
+    if (!g->rl_col && g->n >= MS_LAYOUT_MIN_N) {
+        gb_status rc = prepare_batched(const_cast<gb_graph *>(g), s);
+        if (rc != GB_OK) return rc;
+    }
     MsGraph G;
-    G.off = g->off;
-    G.col = g->col;
+    G.off = g->rl_col ? g->rl_off : g->off;
+    G.col = g->rl_col ? g->rl_col : g->col;
+    G.perm = g->rl_col ? g->rl_perm : nullptr;
+    G.inv = g->rl_col ? g->rl_inv : nullptr;
     G.nz = g->nz;
     G.voff = 0;
     G.n = g->n;
@@ -988,6 +1040,8 @@ gb_status multigraph_impl(const gb_graph *const *gs, int ng, const int64_t *root
         v[i].off = gs[i]->off;
         v[i].col = gs[i]->col;
         v[i].nz = gs[i]->nz;
+        v[i].perm = nullptr;
+        v[i].inv = nullptr;
         v[i].voff = 0;
         v[i].n = gs[i]->n;
         v[i].par = parents[i];
@@ -1112,6 +1166,8 @@ gb_status ms_serve_create(const gb_graph *g, int blocks, MsServe **out, cudaStre
     G.off = g->off;
     G.col = g->col;
     G.nz = g->nz;
+    G.perm = nullptr;  // serving searches the graph itself
+    G.inv = nullptr;
     G.voff = 0;
     G.n = n;
     G.par = nullptr;

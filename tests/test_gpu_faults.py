@@ -128,6 +128,25 @@ def test_server_creation_reports_nomem_without_leaks(graph):
     small.free()
 
 
+def test_batched_layout_reports_nomem_without_leaks(graph):
+    spec, edges, w, g, gw, roots = graph
+    off, col = g.csr()
+
+    def build_and_prepare():
+        G = gb.graph_from_csr(off, col)
+        try:
+            G.prepare_batched()
+        finally:
+            G.free()
+        return None
+
+    assert check_every_allocation_failure("graph_prepare_batched", build_and_prepare) > 0
+    G = gb.graph_from_csr(off, col).prepare_batched()
+    P, L = gb.bfs_batch(G, roots)
+    assert gb.bfs_validate(G, roots[0], P[0], L[0])["code"] == 0
+    G.free()
+
+
 def test_injection_arguments_are_checked():
     with pytest.raises(gb.GbError, match="INVALID"):
         gb.debug_fail_allocations(-1, 1)

@@ -62,7 +62,8 @@ def test_generator_bit_exact(scale):
     assert np.array_equal(np_(e), e_ref)
 
 
-@pytest.mark.parametrize("scale", list(range(1, 13)) + [16, 20])
+# the sort's pass plans: 8-bit digits, 9-bit (SCALE 9, 18) and mixed (13, 17)
+@pytest.mark.parametrize("scale", list(range(1, 14)) + [16, 17, 18, 20])
 def test_csr_bit_exact(scale):
     _, off_ref, col_ref = oracle_graph(scale)
     _, g = gpu_graph(scale)
@@ -435,6 +436,31 @@ def test_msbfs_rows_longer_than_the_huge_threshold(mode, canonical):
         p_ref, l_ref = oracle.bfs(off, col, r)
         check_row(off, col, r, np_(P2[0][b]), np_(L2[0][b]), p_ref, l_ref, canonical, (b, r))
     G.free()
+
+
+@pytest.mark.parametrize("canonical", [0, 1])
+@pytest.mark.parametrize("mode", list(MS_SWITCHES))
+def test_msbfs_on_the_degree_ordered_copy(mode, canonical):
+    # graph_prepare_batched renumbers the vertices by degree for the batched
+    # search (automatic from 2^25 vertices); the rows must still equal the
+    # oracle's, parents given as original ids and, in canonical mode, still the
+    # smallest-id neighbour one level up
+    gb.bfs_set_options(canonical_parents=canonical, **MS_SWITCHES[mode])
+    cases = [_three_hub_csr(), _path_and_cycle_csr()]
+    for scale in (10, 16):
+        _, off_ref, col_ref = oracle_graph(scale)
+        cases.append((off_ref, col_ref))
+    for ci, (off, col) in enumerate(cases):
+        G = gb.graph_from_csr(torch.as_tensor(off).cuda(), torch.as_tensor(col).cuda())
+        G.prepare_batched()
+        G.prepare_batched()   # a second call keeps the copy
+        rng = np.random.default_rng(ci)
+        roots = [int(x) for x in rng.integers(0, off.size - 1, size=64)]
+        P, L = gb.bfs_batch(G, roots)
+        for i, r in enumerate(roots):
+            p_ref, l_ref = oracle.bfs(off, col, r)
+            check_row(off, col, r, np_(P[i]), np_(L[i]), p_ref, l_ref, canonical, (ci, i, r))
+        G.free()
 
 
 def _path_and_cycle_csr():

@@ -69,7 +69,9 @@ def test_generator_with_portions_equals_the_oracle(scale):
         assert np.array_equal(np_(e), e_ref), p
 
 
-@pytest.mark.parametrize("scale", [12, 16, 20])
+# 12, 16, 20: 8-bit digit passes only; 13 (9, 9, 8), 17 (9, 9, 8, 8) and 18
+# (four 9-bit passes) exercise the 512-digit passes and their chained bases.
+@pytest.mark.parametrize("scale", [12, 13, 16, 17, 18, 20])
 def test_kernel1_with_portions_equals_the_oracle(scale):
     spec = W.GraphSpec(scale=scale)
     e_ref, off_ref, col_ref = oracle_graph(scale)
