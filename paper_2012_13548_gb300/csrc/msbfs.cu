@@ -872,15 +872,44 @@ __global__ void __launch_bounds__(MS_THREADS, 2) ms_kernel(MsArgs<T> a)
             T hm[MS_HIST];
 #pragma unroll
             for (int j = 0; j < MS_HIST; ++j) hm[j] = a.hist[(size_t)j * a.mstride + gv];
-            for (int b = 0; b < a.k; ++b) {
-                const bool has = (sn >> b) & 1;
-                int32_t lvl = -1;
+            if ((G.kst & 15) == 0) {
+                // the vertex's staged parents 16 at a time, as four 16-byte loads
+                const int4 *prow = reinterpret_cast<const int4 *>(G.pst + lu * G.kst);
+                for (int b0 = 0; b0 < a.k; b0 += 16) {
+                    int32_t pv[16];
 #pragma unroll
-                for (int j = 0; j < MS_HIST; ++j)
-                    if ((hm[j] >> b) & 1) lvl = j;
-                if (has && lvl < 0) lvl = G.lst[lu * G.kst + b];
-                G.par[(int64_t)b * G.n + lu] = has ? G.pst[lu * G.kst + b] : -1;
-                G.lev[(int64_t)b * G.n + lu] = has ? lvl : -1;
+                    for (int q = 0; q < 4; ++q) {
+                        const int4 x = prow[(b0 >> 2) + q];
+                        pv[4 * q] = x.x;
+                        pv[4 * q + 1] = x.y;
+                        pv[4 * q + 2] = x.z;
+                        pv[4 * q + 3] = x.w;
+                    }
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        const int b = b0 + t;
+                        if (b >= a.k) break;
+                        const bool has = (sn >> b) & 1;
+                        int32_t lvl = -1;
+#pragma unroll
+                        for (int j = 0; j < MS_HIST; ++j)
+                            if ((hm[j] >> b) & 1) lvl = j;
+                        if (has && lvl < 0) lvl = G.lst[lu * G.kst + b];
+                        G.par[(int64_t)b * G.n + lu] = has ? pv[t] : -1;
+                        G.lev[(int64_t)b * G.n + lu] = has ? lvl : -1;
+                    }
+                }
+            } else {
+                for (int b = 0; b < a.k; ++b) {
+                    const bool has = (sn >> b) & 1;
+                    int32_t lvl = -1;
+#pragma unroll
+                    for (int j = 0; j < MS_HIST; ++j)
+                        if ((hm[j] >> b) & 1) lvl = j;
+                    if (has && lvl < 0) lvl = G.lst[lu * G.kst + b];
+                    G.par[(int64_t)b * G.n + lu] = has ? G.pst[lu * G.kst + b] : -1;
+                    G.lev[(int64_t)b * G.n + lu] = has ? lvl : -1;
+                }
             }
         }
     }
