@@ -238,6 +238,22 @@ __device__ __forceinline__ void write_parents(const MsGraph &G, const MsSlots *S
         if (!local_orig) local = orig_id(G, local);
         p = (int32_t)orig_id(G, p);
     }
+    if (!S && (G.kst & 15) == 0) {
+        // an aligned group of 4 bits that all take this parent: one 16-byte store
+        int32_t *row = G.pst + local * G.kst;
+        unsigned long long bb = (unsigned long long)bits;
+        while (bb) {
+            const int b = __ffsll(bb) - 1;
+            if ((b & 3) == 0 && ((bb >> b) & 15ull) == 15ull) {
+                *reinterpret_cast<int4 *>(row + b) = make_int4(p, p, p, p);
+                bb &= ~(15ull << b);
+            } else {
+                row[b] = p;
+                bb &= bb - 1;
+            }
+        }
+        return;
+    }
     while (bits) {
         const int b = __ffsll((unsigned long long)bits) - 1;
         bits &= bits - 1;
