@@ -133,10 +133,10 @@ gb_status kron_generate(int scale, int edgefactor, double a, double b, double c,
  * library-owned graph; free it with graph_free.  Besides the CSR every graph
  * holds four arrays the search reads: a degree >= 1 bitmap (n/8 bytes), the
  * list of the vertices of degree >= 1 in ascending order (4 bytes each; the
- * first bottom-up level walks it), the degrees saturated at 65535 (2 * n
- * bytes; read by the bottom-up list walks) and a hub per vertex (4 * n bytes:
- * a neighbour of largest degree among the first 128 of its row, tested first
- * by the bottom-up step).  The column array is padded to a multiple of 4
+ * first bottom-up level walks it), a hub per vertex (4 * n bytes: a neighbour
+ * of largest degree among the first 128 of its row, tested first by the
+ * bottom-up step) and, for the bottom-up list walks, each hub again beside
+ * the vertex's degree saturated at 65535 (8 * n bytes).  The column array is padded to a multiple of 4
  * entries. */
 gb_status graph_build_csr(const int64_t *edges, int64_t m, int scale, gb_graph **out,
                           gb_stream s);

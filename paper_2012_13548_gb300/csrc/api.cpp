@@ -78,7 +78,7 @@ SsspDevStats *sssp_stats_buffer()
 // Free every device array of a graph (any may be null) and the graph.
 void destroy_graph(gb_graph *g)
 {
-    void *arrays[] = {g->off, g->col, g->nz, g->hub, g->nzl, g->deg16, g->rl_off, g->rl_col, g->rl_perm, g->rl_inv, g->wgt, g->wadj};
+    void *arrays[] = {g->off, g->col, g->nz, g->hub, g->nzl, g->hd, g->rl_off, g->rl_col, g->rl_perm, g->rl_inv, g->wgt, g->wadj};
     for (void *p : arrays)
         if (p) gb::dfree(p);
     delete g;

@@ -107,7 +107,7 @@ struct BfsArgs {
     int32_t *ulist;  // per warp a segment of useg entries: the vertices a bottom-up level left open (or null)
     int64_t useg;
     const int32_t *nzl;  // the vertices of degree >= 1, ascending (or null)
-    const uint16_t *deg16;  // min(degree, 65535) per vertex (set whenever ulist is)
+    const int2 *hd;         // (hub, min(degree, 65535)) per vertex (set whenever ulist is)
     int64_t nnzv;
     BigEnt *bigq;
     int64_t bigcap;
@@ -713,9 +713,10 @@ __global__ void __launch_bounds__(BFS_THREADS, MINB) bfs_kernel(BfsArgs a)
 #pragma unroll
                 for (int t = 0; t < BU_WORDS; ++t) {
                     vw[t] = cand[t] && from_nzl ? ldcg_u32(&a.vis[(unsigned)u[t] >> 5]) : 0u;
-                    // 2 bytes per entry instead of two scattered 8-byte offsets
-                    dg[t] = cand[t] ? (int32_t)__ldg(&a.deg16[u[t]]) : 0;
-                    hb[t] = cand[t] && a.hub ? __ldg(&a.hub[u[t]]) : -1;
+                    // hub and degree in one 8-byte load, not two scattered offsets
+                    const int2 x = cand[t] ? __ldg(&a.hd[u[t]]) : make_int2(-1, 0);
+                    dg[t] = x.y;
+                    hb[t] = a.hub ? x.x : -1;
                 }
 #pragma unroll
                 for (int t = 0; t < BU_WORDS; ++t) {
@@ -1037,7 +1038,7 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
     a.ulist = reinterpret_cast<int32_t *>(ws + Lw.off_ul);
     a.nzl = g->nzl;
     a.nnzv = g->nnzv;
-    a.deg16 = g->deg16;
+    a.hd = g->hd;
     a.bigq = reinterpret_cast<BigEnt *>(ws + off_big);
     a.bigcap = bigcap;
     a.st = ctx->status;
@@ -1056,7 +1057,7 @@ gb_status bfs_impl(const gb_graph *g, int64_t root, int32_t *parent, int32_t *le
                                : (o.blocks_per_sm == 1 ? std::max(1, ctx->bfs_blocks2 / 2) : ctx->bfs_blocks2);
     const int blocks = grid > 0 && grid < full ? grid : full;
     a.useg = open_list_seg(n, (int64_t)blocks * (BFS_THREADS / 32));
-    if (a.useg == 0 || !a.deg16) a.ulist = nullptr;  // the list walks read deg16
+    if (a.useg == 0 || !a.hd) a.ulist = nullptr;  // the list walks read hd
     const void *kern = minb == 2 ? (const void *)bfs_kernel<2> : (const void *)bfs_kernel<3>;
     GB_CUDA(cudaLaunchCooperativeKernel(kern, dim3(blocks),
                                         dim3(BFS_THREADS), args, 0, s));
@@ -1189,7 +1190,7 @@ gb_status bfs_noalloc_impl(const int64_t *off, const int32_t *col, int64_t n, in
     a.useg = 0;
     a.nzl = nullptr;
     a.nnzv = 0;
-    a.deg16 = nullptr;
+    a.hd = nullptr;
     a.bigq = reinterpret_cast<BigEnt *>(ws + kNaBig);
     a.bigcap = kNaBigCap;
     a.st = reinterpret_cast<DevStatus *>(ws + kNaStatus);

@@ -249,14 +249,16 @@ __global__ void __launch_bounds__(NZL_WORDS) nzl_write_kernel(const uint32_t *__
     }
 }
 
-// deg16[v] = min(degree(v), 65535): the bottom-up list walks read 2 bytes per
-// vertex instead of two 8-byte offsets from different sectors.
-__global__ void deg16_kernel(const int64_t *__restrict__ off, int64_t n, uint16_t *__restrict__ d16)
+// hd[v] = (hub[v], min(degree(v), 65535)): the bottom-up list walks read both
+// with one 8-byte load instead of a hub load and two 8-byte offsets from
+// other sectors.
+__global__ void hd_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ hub, int64_t n,
+                          int2 *__restrict__ hd)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const int64_t d = off[v + 1] - off[v];
-        d16[v] = (uint16_t)(d < 65535 ? d : 65535);
+        hd[v] = make_int2(hub[v], (int)(d < 65535 ? d : 65535));
     }
 }
 
@@ -612,10 +614,6 @@ gb_status build_graph_aux(gb_graph *g, cudaStream_t s)
         note_launch();
         GB_CUDA(cudaGetLastError());
     }
-    GB_CUDA(gb::dmalloc(&g->deg16, std::max<int64_t>(g->n, 1) * sizeof(uint16_t)));
-    deg16_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(g->off, g->n, g->deg16);
-    note_launch();
-    GB_CUDA(cudaGetLastError());
     GB_CUDA(gb::dmalloc(&g->hub, std::max<int64_t>(g->n, 1) * sizeof(int32_t)));
     uint8_t *key = nullptr;
     GB_CUDA(tmp.alloc(&key, (size_t)g->n));
@@ -623,6 +621,9 @@ gb_status build_graph_aux(gb_graph *g, cudaStream_t s)
     note_launch();
     hub_kernel<<<ctx->num_sms * 8, HUB_THREADS, 0, s>>>(g->off, g->col, key, g->n, g->nnz, g->hub,
                                                         ctx->status);
+    note_launch();
+    GB_CUDA(gb::dmalloc(&g->hd, std::max<int64_t>(g->n, 1) * sizeof(int2)));
+    hd_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(g->off, g->hub, g->n, g->hd);
     note_launch();
     GB_CUDA(cudaGetLastError());
     return GB_OK;

@@ -157,7 +157,9 @@ struct gb_graph {
     int32_t *col = nullptr;  // device [nnz]
     uint32_t *nz = nullptr;  // device [ceil(n/32)]: bit v set iff degree(v) >= 1
     int32_t *hub = nullptr;  // device [n]: a neighbour of v of largest degree, or -1
-    uint16_t *deg16 = nullptr;  // device [n]: min(degree(v), 65535); 65535 means "read the offsets"
+    // device [n]: (hub[v], min(degree(v), 65535)) side by side, one 8-byte load
+    // for the bottom-up list walks (65535 means "read the offsets")
+    int2 *hd = nullptr;
     int32_t *nzl = nullptr;  // device [nnzv]: the vertices of degree >= 1, ascending
     int64_t nnzv = 0;
     uint32_t *wgt = nullptr; // device [nnz] weights in units of 2^-24 (weighted graphs only)
