@@ -49,7 +49,7 @@ namespace {
 
 constexpr int BFS_THREADS = 512;
 constexpr int BIG_CHUNK = 128;      // edges per chunk of a big frontier vertex (one round)
-constexpr int BU_LANE_FIRST = 4;    // bottom-up: each lane probes this many neighbours itself
+constexpr int BU_LANE_FIRST = 8;    // bottom-up: each lane probes this many neighbours itself
 constexpr int BU_WORDS = 4;         // bottom-up hub pass: visited words per warp iteration
 constexpr int PBUF = 256;           // per-warp ring of vertices left for the row pass
 constexpr int BFS_WARPS = BFS_THREADS / 32;
