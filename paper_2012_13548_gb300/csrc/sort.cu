@@ -127,12 +127,19 @@ __global__ void __launch_bounds__(RS_THREADS, RS_MINB(VALS)) rs_onesweep_kernel(
         k[j] = idx < tend ? kin[idx] : 0ull;
         if (VALS) v[j] = idx < tend ? vin[idx] : 0u;
     }
-    // Warp-level stable ranking by digit (multisplit with match-any).
+    // Warp-level stable ranking by digit (multisplit: the lanes holding the same
+    // digit found with one ballot per digit bit, faster here than match-any).
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         const bool valid = wbase + j * 32 + lane < tend;
         const unsigned dg = valid ? (unsigned)(k[j] >> shift) & DMASK : (unsigned)RADIX;
-        const unsigned peers = __match_any_sync(kFull, dg);
+        // lanes with the same digit: one ballot per digit bit (and the valid bit)
+        unsigned peers = kFull;
+#pragma unroll
+        for (int bit = 0; bit <= DBITS; ++bit) {
+            const unsigned bl = __ballot_sync(kFull, (dg >> bit) & 1u);
+            peers &= ((dg >> bit) & 1u) ? bl : ~bl;
+        }
         const unsigned before = __popc(peers & lanemask_lt());
         unsigned cnt = 0;
         if (valid) cnt = s_whist[warp][dg];
