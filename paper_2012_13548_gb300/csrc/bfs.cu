@@ -50,7 +50,7 @@ namespace {
 constexpr int BFS_THREADS = 512;
 constexpr int BIG_CHUNK = 128;      // edges per chunk of a big frontier vertex (one round)
 constexpr int BU_LANE_FIRST = 8;    // bottom-up: each lane probes this many neighbours itself
-constexpr int BU_WORDS = 4;         // bottom-up hub pass: visited words per warp iteration
+constexpr int BU_WORDS = 2;         // bottom-up hub pass: visited words (or 32-entry list groups) per warp step
 constexpr int PBUF = 256;           // per-warp ring of vertices left for the row pass
 constexpr int BFS_WARPS = BFS_THREADS / 32;
 constexpr int QBUF = 512;           // per-warp buffer of discovered vertices (shared memory)
